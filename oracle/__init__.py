@@ -1,0 +1,155 @@
+"""The ORACLE: a plain FP64 CPU reference of the BCTS / Batch-BFS search.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the bench's CPU
+baseline leg may import this package; the CUDA library never does, and the two
+share no code (the oracle's C source restates the environment, the renderer,
+the Q-network, Eq. 1, Eq. 3, Eq. 7 and Alg. 1's tree order on its own).
+
+This module is the ctypes binding of `bcts_oracle.c` (built by `build()` into
+`liboracle.so` beside it) plus thin numpy marshalling.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bcts_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+STATE_BYTES = 80
+FRAME_BYTES = 4 * 84 * 84
+
+
+def build(force: bool = False) -> str:
+    """Compile bcts_oracle.c with gcc (-O2, OpenMP).  Returns the .so path."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        subprocess.check_call(
+            ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-Wall", "-Wextra",
+             "-o", _LIB_PATH, _SRC, "-lm"])
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        lib.or_env_step.argtypes = [P, ctypes.c_int, P]
+        lib.or_env_step.restype = ctypes.c_int
+        lib.or_render.argtypes = [P, P]
+        lib.or_qnet.argtypes = [P, P, ctypes.c_int, P]
+        lib.or_qnet_batch.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P]
+        lib.or_qnet_numel.argtypes = [ctypes.c_int]
+        lib.or_qnet_numel.restype = ctypes.c_size_t
+        lib.or_bellman_penalty.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+        lib.or_bellman_penalty.restype = ctypes.c_double
+        lib.or_search.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_double, P, P, P]
+        lib.or_search.restype = ctypes.c_int
+        lib.or_replay.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_double, P, P]
+        lib.or_level.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
+                                 ctypes.c_double, P, P]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _state_array(s) -> np.ndarray:
+    a = np.ascontiguousarray(s)
+    assert a.dtype.itemsize == STATE_BYTES
+    return a
+
+
+def env_step(state, a: int):
+    """One environment tick: returns (next_state, reward)."""
+    lib = _load()
+    s = _state_array(state).reshape(1)
+    out = np.zeros_like(s)
+    r = lib.or_env_step(_ptr(s), int(a), _ptr(out))
+    return out[0], int(r)
+
+
+def render(state) -> np.ndarray:
+    """The 4 x 84 x 84 uint8 frame stack of a state."""
+    lib = _load()
+    s = _state_array(state).reshape(1)
+    fr = np.zeros((4, 84, 84), dtype=np.uint8)
+    lib.or_render(_ptr(s), _ptr(fr))
+    return fr
+
+
+def qnet(frames: np.ndarray, weights: np.ndarray, A: int) -> np.ndarray:
+    """FP64 Q-values for a batch of frame stacks [n][4][84][84] -> [n][A]."""
+    lib = _load()
+    fr = np.ascontiguousarray(frames, dtype=np.uint8).reshape(-1, FRAME_BYTES)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    assert w.size == lib.or_qnet_numel(A)
+    q = np.zeros((fr.shape[0], A), dtype=np.float64)
+    lib.or_qnet_batch(_ptr(fr), fr.shape[0], _ptr(w), A, _ptr(q))
+    return q
+
+
+def bellman_penalty(delta_e: float, delta_o: float, A: int, d: int) -> float:
+    """Eq. 7."""
+    return float(_load().or_bellman_penalty(delta_e, delta_o, A, d))
+
+
+def search(roots, weights: np.ndarray, A: int, d: int, gamma: float, correction: float):
+    """Full BCTS search.  Returns dict(action [n], values [n][A], q0, v_uncorrected,
+    delta, r0 [n][A], pi_o, delta_o, delta_e, B [n])."""
+    lib = _load()
+    r = _state_array(roots).reshape(-1)
+    n = r.shape[0]
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    assert w.size == lib.or_qnet_numel(A)
+    act = np.zeros(n, dtype=np.int32)
+    val = np.zeros((n, A), dtype=np.float64)
+    diag = np.zeros((n, 4 * A + 4), dtype=np.float64)
+    rc = lib.or_search(_ptr(r), n, _ptr(w), A, d, float(gamma), float(correction), _ptr(act), _ptr(val),
+                       _ptr(diag))
+    if rc != 0:
+        raise ValueError("oracle search rejected its arguments")
+    return {
+        "action": act, "values": val,
+        "q0": diag[:, 0:A], "v_uncorrected": diag[:, A:2 * A], "delta": diag[:, 2 * A:3 * A],
+        "r0": diag[:, 3 * A:4 * A], "pi_o": diag[:, 4 * A].astype(np.int64),
+        "delta_o": diag[:, 4 * A + 1], "delta_e": diag[:, 4 * A + 2], "B": diag[:, 4 * A + 3],
+    }
+
+
+def replay(root, A: int, depth: int, idx: int, gamma: float):
+    """State and accumulated discounted reward of node `idx` of level `depth`."""
+    lib = _load()
+    r = _state_array(root).reshape(1)
+    out = np.zeros_like(r)
+    R = np.zeros(1, dtype=np.float64)
+    lib.or_replay(_ptr(r), A, depth, int(idx), float(gamma), _ptr(out), _ptr(R))
+    return out[0], float(R[0])
+
+
+def level(root, A: int, depth: int, gamma: float, first: int = 0, count: int | None = None):
+    """States and rewards of nodes [first, first+count) of level `depth` (Alg. 1 order)."""
+    lib = _load()
+    r = _state_array(root).reshape(1)
+    if count is None:
+        count = A ** depth - first
+    out = np.zeros(count, dtype=r.dtype)
+    R = np.zeros(count, dtype=np.float64)
+    lib.or_level(_ptr(r), A, depth, int(first), int(count), float(gamma), _ptr(out), _ptr(R))
+    return out, R
+
+
+def threads() -> int:
+    """OpenMP threads the oracle uses (OMP_NUM_THREADS or all cores)."""
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else (os.cpu_count() or 1)

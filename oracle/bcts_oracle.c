@@ -1,0 +1,338 @@
+/*
+ * bcts_oracle.c -- the ORACLE: plain, slow, obviously correct CPU reference of
+ * the Batch-BFS / BCTS search, in FP64.  TEST INFRASTRUCTURE ONLY: the tests,
+ * the smoke check and the bench's CPU-baseline leg call it; the product path
+ * never does.  It shares no code, header, table or constant with the CUDA
+ * library: every constant below is written here from the environment
+ * definition, independently.
+ *
+ * What it computes (paper: "Improve Agents without Retraining: Parallel Tree
+ * Search with Off-Policy Correction", Hallak et al., NeurIPS 2021):
+ *   - Eq. 1: the d-step Q estimate, max over a_1..a_d of the discounted d-step
+ *     return plus gamma^d Q(s_d, a_d), computed by a recursive depth-first search
+ *     (the max over the tail factorises level by level);
+ *   - Prop. 1 / Sec. 3.3: the Bellman errors delta(a) = Q_1(s,a) - Q_0(s,a) from
+ *     the root and the depth-1 nodes;
+ *   - Eq. 7: the Bellman penalty B(delta_e, delta_o, A, d);
+ *   - Eq. 3 / Eq. 4: the corrected values and the BCTS action.
+ * The environment is the synthetic sprite environment that stands in for the
+ * paper's Atari games (Sec. 4 uses CuLE); the Q-network is Nature-DQN with
+ * seeded weights standing in for the pre-trained Rainbow agent (Sec. 5.1),
+ * fed the 4-frame stack of Sec. 5 (frame stacking).
+ *
+ * Readings of the paper taken here (each listed with its reason in the design
+ * notes): |delta| as the std-dev surrogate; delta_e = arithmetic mean of
+ * |delta(a)| over a != pi_o; natural log in Eq. 7; Eq. 7 applied unchanged for
+ * every d >= 1 (sqrt(d-1) = 0 at d = 1); d = 0 returns pi_o; ties broken to the
+ * lowest index; the correction is scaled by the swept multiplier c (Sec. 5.1).
+ *
+ * Pins: tests/test_oracle_*.py check this file against brute-force enumeration
+ * of all A^d action sequences, torch.nn.functional conv2d/linear in float64,
+ * closed-form returns of hand-built environments, the Lemma 3 form of Eq. 7
+ * and the exact GEV biases of Lemma 2.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- state: 80 bytes, same field order and sizes as the documented layout -- */
+typedef struct {
+    int16_t pos[4][4][2]; /* [history slot][object][x,y]; slot 3 newest */
+    int8_t vel[4][2];     /* object velocities; object 0 = agent, unused */
+    uint32_t tick;
+    uint32_t pad;
+} or_state;
+
+enum { OR_GRID = 21, OR_HIST = 4, OR_NOBJ = 4, OR_PIX = 84 };
+
+/* ---- environment step ---------------------------------------------------- */
+/* Agent move table: action a, direction a mod 9, speed 1 + a / 9. */
+static const int OR_DX[9] = {0, 0, 1, -1, 0, 1, -1, 1, -1};
+static const int OR_DY[9] = {0, -1, 0, 0, 1, -1, -1, 1, 1};
+
+static int or_clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* lowbias32 integer hash (C. Wellons, "hash prospector", 2018). */
+static uint32_t or_hash32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+/* Reflect one coordinate moving by v off the walls at 0 and GRID-1. */
+static void or_reflect(int *p, int *v) {
+    int q = *p + *v;
+    if (q < 0) { q = -q; *v = -*v; }
+    if (q > OR_GRID - 1) { q = 2 * (OR_GRID - 1) - q; *v = -*v; }
+    *p = q;
+}
+
+/* One tick of the deterministic sprite environment (the forward model G of
+ * Alg. 1).  Returns the integer reward in {-1, 0, 1}. */
+int or_env_step(const or_state *s, int a, or_state *out) {
+    or_state n = *s;
+    int ax = s->pos[3][0][0], ay = s->pos[3][0][1];
+    int dir = a % 9, speed = 1 + a / 9;
+    int nax = or_clampi(ax + speed * OR_DX[dir], 0, OR_GRID - 1);
+    int nay = or_clampi(ay + speed * OR_DY[dir], 0, OR_GRID - 1);
+    int px[4], py[4];
+    px[0] = nax;
+    py[0] = nay;
+    for (int k = 1; k < OR_NOBJ; ++k) {
+        int x = s->pos[3][k][0], y = s->pos[3][k][1];
+        int vx = s->vel[k][0], vy = s->vel[k][1];
+        or_reflect(&x, &vx);
+        or_reflect(&y, &vy);
+        px[k] = x;
+        py[k] = y;
+        n.vel[k][0] = (int8_t)vx;
+        n.vel[k][1] = (int8_t)vy;
+    }
+    int reward = 0;
+    for (int k = 1; k < OR_NOBJ; ++k) {
+        if (px[k] == nax && py[k] == nay) {
+            reward += (k == 1) ? 1 : -1;
+            uint32_t key = s->tick * 0x9E3779B1u + (uint32_t)k * 0x85EBCA77u +
+                           (uint32_t)(nax * OR_GRID + nay) * 0xC2B2AE3Du;
+            uint32_t h = or_hash32(key);
+            px[k] = (int)(h % OR_GRID);
+            py[k] = (int)((h >> 16) % OR_GRID);
+        }
+    }
+    if (reward > 1) reward = 1;
+    if (reward < -1) reward = -1;
+    for (int h = 0; h < OR_HIST - 1; ++h) memcpy(n.pos[h], s->pos[h + 1], sizeof n.pos[h]);
+    for (int k = 0; k < OR_NOBJ; ++k) {
+        n.pos[3][k][0] = (int16_t)px[k];
+        n.pos[3][k][1] = (int16_t)py[k];
+    }
+    n.tick = s->tick + 1u;
+    n.pad = 0;
+    *out = n;
+    return reward;
+}
+
+/* ---- renderer: 4 x 84 x 84 uint8 frame stack, channel h = history slot h ---- */
+/* Sprite masks, 4x4, bit (r*4 + c) set = pixel drawn. */
+static const uint16_t OR_SPRITE[4] = {0xFFFF, 0x6FF6, 0x9669, 0xF99F};
+static const uint8_t OR_PALETTE[4] = {240, 192, 128, 64};
+
+void or_render(const or_state *s, uint8_t *frames) {
+    memset(frames, 0, OR_HIST * OR_PIX * OR_PIX);
+    for (int h = 0; h < OR_HIST; ++h) {
+        uint8_t *f = frames + h * OR_PIX * OR_PIX;
+        for (int k = 0; k < OR_NOBJ; ++k) { /* later objects paint over earlier ones */
+            int cx = s->pos[h][k][0], cy = s->pos[h][k][1];
+            for (int r = 0; r < 4; ++r)
+                for (int c = 0; c < 4; ++c)
+                    if ((OR_SPRITE[k] >> (r * 4 + c)) & 1)
+                        f[(cy * 4 + r) * OR_PIX + (cx * 4 + c)] = OR_PALETTE[k];
+        }
+    }
+}
+
+/* ---- Nature-DQN forward in FP64 with direct loops ------------------------- */
+/* Weights: flat float32 in PyTorch parameter order (conv [Cout][Cin][kh][kw],
+ * bias; linear [out][in], bias; fc1 input flattened (C, H, W)).  Input pixels
+ * are scaled by 1/255. */
+static void or_conv_relu(const double *in, int cin, int ih, int iw, const float *w, const float *b,
+                         int cout, int k, int stride, double *out, int oh, int ow) {
+    for (int o = 0; o < cout; ++o)
+        for (int y = 0; y < oh; ++y)
+            for (int x = 0; x < ow; ++x) {
+                double acc = (double)b[o];
+                for (int c = 0; c < cin; ++c)
+                    for (int ky = 0; ky < k; ++ky)
+                        for (int kx = 0; kx < k; ++kx)
+                            acc += (double)w[((o * cin + c) * k + ky) * k + kx] *
+                                   in[(c * ih + (y * stride + ky)) * iw + (x * stride + kx)];
+                out[(o * oh + y) * ow + x] = acc > 0.0 ? acc : 0.0;
+            }
+}
+
+static void or_linear(const double *in, int nin, const float *w, const float *b, int nout, int relu,
+                      double *out) {
+    for (int o = 0; o < nout; ++o) {
+        double acc = (double)b[o];
+        for (int i = 0; i < nin; ++i) acc += (double)w[(size_t)o * nin + i] * in[i];
+        out[o] = (relu && acc < 0.0) ? 0.0 : acc;
+    }
+}
+
+size_t or_qnet_numel(int A) {
+    return (size_t)32 * 4 * 8 * 8 + 32 + 64 * 32 * 4 * 4 + 64 + 64 * 64 * 3 * 3 + 64 +
+           (size_t)512 * 3136 + 512 + (size_t)A * 512 + A;
+}
+
+void or_qnet(const uint8_t *frames, const float *W, int A, double *q) {
+    const float *c1w = W, *c1b = c1w + 32 * 4 * 8 * 8;
+    const float *c2w = c1b + 32, *c2b = c2w + 64 * 32 * 4 * 4;
+    const float *c3w = c2b + 64, *c3b = c3w + 64 * 64 * 3 * 3;
+    const float *f1w = c3b + 64, *f1b = f1w + (size_t)512 * 3136;
+    const float *f2w = f1b + 512, *f2b = f2w + (size_t)A * 512;
+    double *x = malloc(sizeof(double) * 4 * 84 * 84);
+    double *h1 = malloc(sizeof(double) * 32 * 20 * 20);
+    double *h2 = malloc(sizeof(double) * 64 * 9 * 9);
+    double *h3 = malloc(sizeof(double) * 64 * 7 * 7);
+    double *h4 = malloc(sizeof(double) * 512);
+    for (int i = 0; i < 4 * 84 * 84; ++i) x[i] = (double)frames[i] / 255.0;
+    or_conv_relu(x, 4, 84, 84, c1w, c1b, 32, 8, 4, h1, 20, 20);
+    or_conv_relu(h1, 32, 20, 20, c2w, c2b, 64, 4, 2, h2, 9, 9);
+    or_conv_relu(h2, 64, 9, 9, c3w, c3b, 64, 3, 1, h3, 7, 7);
+    or_linear(h3, 3136, f1w, f1b, 512, 1, h4);
+    or_linear(h4, 512, f2w, f2b, A, 0, q);
+    free(x); free(h1); free(h2); free(h3); free(h4);
+}
+
+/* Q-values of a state: render the stack, run the network. */
+static void or_q_of_state(const or_state *s, const float *W, int A, double *q) {
+    uint8_t fr[4 * 84 * 84];
+    or_render(s, fr);
+    or_qnet(fr, W, A, q);
+}
+
+/* Batch of frame stacks -> Q [n][A], parallel over stacks. */
+void or_qnet_batch(const uint8_t *frames, int n, const float *W, int A, double *q) {
+#pragma omp parallel for schedule(dynamic)
+    for (int i = 0; i < n; ++i) or_qnet(frames + (size_t)i * 4 * 84 * 84, W, A, q + (size_t)i * A);
+}
+
+static int or_argmax_lowest(const double *v, int n) {
+    int best = 0;
+    for (int i = 1; i < n; ++i)
+        if (v[i] > v[best]) best = i;
+    return best;
+}
+
+static double or_maxv(const double *v, int n) { return v[or_argmax_lowest(v, n)]; }
+
+/* W_k(s): value of a node at depth k <= d.  At k = d it is max_a Q(s, a)
+ * (Alg. 1's leaf term); above, max over actions of r + gamma * W_{k+1}(s'),
+ * which equals the max over the remaining action sequence in Eq. 1. */
+static double or_node_value(const or_state *s, int k, int d, const float *W, int A, double gamma) {
+    if (k == d) {
+        double q[64];
+        or_q_of_state(s, W, A, q);
+        return or_maxv(q, A);
+    }
+    double best = -INFINITY;
+    for (int a = 0; a < A; ++a) {
+        or_state n;
+        int r = or_env_step(s, a, &n);
+        double v = (double)r + gamma * or_node_value(&n, k + 1, d, W, A, gamma);
+        if (v > best) best = v;
+    }
+    return best;
+}
+
+/* Eq. 7: B = sqrt(log A) (de sqrt(d) - do sqrt(d-1)) - (de - do) / sqrt(8). */
+double or_bellman_penalty(double delta_e, double delta_o, int A, int d) {
+    double dm1 = d >= 1 ? (double)(d - 1) : 0.0;
+    return sqrt(log((double)A)) * (delta_e * sqrt((double)d) - delta_o * sqrt(dm1)) -
+           (delta_e - delta_o) / sqrt(8.0);
+}
+
+/*
+ * Full search from one root.
+ *   values[A]  : corrected root values Q^BCTS_d(s0, a) (Eq. 3); for d = 0, Q_0(s0, a)
+ *   *action    : lowest-index argmax of values (Eq. 4)
+ *   diag (may be NULL), 4*A + 4 doubles:
+ *     [0,A)    Q_0(s0, a)                      root Q-values
+ *     [A,2A)   V_d(s0, a)                      uncorrected Eq. 1 values
+ *     [2A,3A)  delta(a) = r(s0,a) + gamma max Q(s1^a) - Q_0(s0,a)   (Prop. 1)
+ *     [3A,4A)  r(s0, a)
+ *     4A: pi_o, 4A+1: delta_o, 4A+2: delta_e, 4A+3: B (Eq. 7)
+ * Work is split over the A root actions (OpenMP) when `parallel` is set.
+ */
+static void or_search_one(const or_state *root, const float *W, int A, int d, double gamma, double corr,
+                          int parallel, int *action, double *values, double *diag) {
+    double q0[64], V[64], delta[64], r0[64];
+    or_q_of_state(root, W, A, q0);
+    int pi_o = or_argmax_lowest(q0, A);
+    if (d == 0) {
+        for (int a = 0; a < A; ++a) values[a] = q0[a];
+        *action = pi_o;
+        if (diag) {
+            for (int a = 0; a < A; ++a) {
+                diag[a] = q0[a]; diag[A + a] = q0[a]; diag[2 * A + a] = 0.0; diag[3 * A + a] = 0.0;
+            }
+            diag[4 * A] = pi_o; diag[4 * A + 1] = 0; diag[4 * A + 2] = 0; diag[4 * A + 3] = 0;
+        }
+        return;
+    }
+#pragma omp parallel for schedule(dynamic) if (parallel)
+    for (int a = 0; a < A; ++a) {
+        or_state s1;
+        int r = or_env_step(root, a, &s1);
+        double q1[64];
+        or_q_of_state(&s1, W, A, q1);
+        double maxq1 = or_maxv(q1, A);
+        r0[a] = (double)r;
+        delta[a] = (double)r + gamma * maxq1 - q0[a];
+        double tail = (d == 1) ? maxq1 : or_node_value(&s1, 1, d, W, A, gamma);
+        V[a] = (double)r + gamma * tail;
+    }
+    double delta_o = fabs(delta[pi_o]);
+    double delta_e = 0.0;
+    if (A > 1) {
+        for (int a = 0; a < A; ++a)
+            if (a != pi_o) delta_e += fabs(delta[a]);
+        delta_e /= (double)(A - 1);
+    }
+    double B = or_bellman_penalty(delta_e, delta_o, A, d);
+    double gd = pow(gamma, (double)d);
+    for (int a = 0; a < A; ++a) values[a] = (a == pi_o) ? V[a] : V[a] - gd * corr * B;
+    *action = or_argmax_lowest(values, A);
+    if (diag) {
+        for (int a = 0; a < A; ++a) {
+            diag[a] = q0[a]; diag[A + a] = V[a]; diag[2 * A + a] = delta[a]; diag[3 * A + a] = r0[a];
+        }
+        diag[4 * A] = pi_o; diag[4 * A + 1] = delta_o; diag[4 * A + 2] = delta_e; diag[4 * A + 3] = B;
+    }
+}
+
+/* n roots; roots run one after another, each root's A subtrees in parallel. */
+int or_search(const or_state *roots, int n, const float *W, int A, int d, double gamma, double corr,
+              int *actions, double *values, double *diag) {
+    if (A < 1 || A > 64 || d < 0 || n < 0) return -1;
+    for (int i = 0; i < n; ++i)
+        or_search_one(&roots[i], W, A, d, gamma, corr, 1, &actions[i], values + (size_t)i * A,
+                      diag ? diag + (size_t)i * (4 * A + 4) : NULL);
+    return 0;
+}
+
+/* ---- tree enumeration in Alg. 1 order ------------------------------------ */
+/* Replay node `idx` of level `depth` (0 <= idx < A^depth): its actions are the
+ * base-A digits of idx, most significant first (child = parent * A + a).
+ * Returns the state and R = sum_t gamma^t r_t (Alg. 1's accumulated reward). */
+void or_replay(const or_state *root, int A, int depth, long long idx, double gamma, or_state *out,
+               double *R) {
+    int acts[32];
+    long long x = idx;
+    for (int i = depth - 1; i >= 0; --i) {
+        acts[i] = (int)(x % A);
+        x /= A;
+    }
+    or_state s = *root;
+    double acc = 0.0, g = 1.0;
+    for (int i = 0; i < depth; ++i) {
+        or_state n;
+        int r = or_env_step(&s, acts[i], &n);
+        acc += g * (double)r;
+        g *= gamma;
+        s = n;
+    }
+    *out = s;
+    *R = acc;
+}
+
+/* Nodes [first, first+count) of level `depth` below one root. */
+void or_level(const or_state *root, int A, int depth, long long first, long long count, double gamma,
+              or_state *out, double *R) {
+#pragma omp parallel for schedule(static)
+    for (long long i = 0; i < count; ++i) or_replay(root, A, depth, first + i, gamma, &out[i], &R[i]);
+}
