@@ -1,0 +1,353 @@
+"""Benchmark of the Batch-BFS / BCTS search on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload atari|precision] [--precision fp32|bf16|fp8|fp32_simt]
+
+One step = one full search (Alg. 1 expansion, root / depth-1 / leaf Q-network,
+backup with the Eq. 7 correction) over one batch of roots.  Default workload:
+32 roots from seeded synthetic sprite-environment states, |A| = 18, d = 3
+(5,832 leaves per root), gamma = 0.99, correction c = 1, FP32-class arithmetic,
+He-initialised Nature-DQN weights from seed 1234 (synthetic stand-ins for
+Atari states and pre-trained Rainbow weights).
+
+Prints ONE JSON line on rank 0.  `value` = leaf nodes per second over all ranks
+(device time, inputs resident in HBM); `e2e` = the same through bcts_search
+with host buffers (host->device roots and device->host actions + values in the
+timed region).  Under torchrun every rank searches its own 32 roots (weak
+scaling, no collective on the data path; a barrier and a max over ranks of the
+elapsed time only).
+
+--impl reference times the oracle (plain FP64 C, OpenMP) on this host's cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2107_01715_b300 import inputs  # noqa: E402
+
+METRIC = "leaf nodes/sec & decisions/sec (A=18, d=3/4) vs plain FP32; p50/p99 latency, 1 B300"
+WORKLOADS = {
+    "atari": dict(n=32, A=18, d=3, gamma=0.99, c=1.0, precision="fp32",
+                  name="plain Batch-BFS at Atari scale: 32 roots, |A|=18, d=3, FP32, correction on"),
+    "precision": dict(n=8, A=18, d=4, gamma=0.99, c=1.0, precision="bf16",
+                      name="precision form: 8 roots, |A|=18, d=4, leaf Q-net in reduced precision"),
+}
+# Per-leaf Nature-DQN multiply-accumulates (conv1, conv2, conv3, fc1, fc2 at A=18).
+MACS = {"conv1": 400 * 32 * 256, "conv2": 81 * 64 * 512, "conv3": 49 * 64 * 576, "fc1": 512 * 3136,
+        "fc2": 18 * 512}
+L2_BYTES = 126 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="atari", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+            "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, max_mhz):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": max_mhz, "reasons": ["nvidia-smi unavailable"]}
+        sm, reasons, power = [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    max_mhz = float(parts[2])
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max_mhz,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def dist_setup(gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BCTS_BENCH_BACKEND") != "gloo" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float, device):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(W, wl, target_s=15.0):
+    """The oracle as it stands on this host's cores, on a bounded sample: one root
+    (A^d leaves + the root and depth-1 evaluations) of the same workload."""
+    import oracle
+    oracle.build()
+    roots = inputs.root_states([0])
+    t0 = time.perf_counter()
+    oracle.search(roots, W, wl["A"], wl["d"], float(np.float32(wl["gamma"])), wl["c"])
+    dt = time.perf_counter() - t0
+    leaves = wl["A"] ** wl["d"]
+    return {"value": leaves / dt, "unit": "leaf nodes/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"1 root (seed 0) of the workload: {leaves} leaves + {1 + wl['A']} root/depth-1 "
+                      f"Q evaluations, FP64, {dt:.1f} s"}
+
+
+def run_reference(args, wl):
+    world, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    W = inputs.qnet_weights(wl["A"], seed=1234)
+    times = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(W, wl)
+        if i >= args.warmup:
+            times.append(wl["A"] ** wl["d"] / r["value"])
+            cb = r
+    total = sum(times)
+    leaves = wl["A"] ** wl["d"] * len(times)
+    value = leaves / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "leaf nodes/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"] + " (oracle sample: 1 root per step)", "roots_per_step": 1,
+                       "A": wl["A"], "d": wl["d"]},
+            "cpu_baseline": dict(cb, value=value),
+            "e2e": {"value": value, "unit": "leaf nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, wl):
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2107_01715_b300 import bcts
+    precision = args.precision or wl["precision"]
+    n, A, d = wl["n"], wl["A"], wl["d"]
+    W = inputs.qnet_weights(A, seed=1234)
+    ctx = bcts.bcts_create(W, A, d, wl["gamma"], wl["c"], precision=precision)
+    roots = inputs.root_states(range(rank * n, rank * n + n))  # each rank its own roots
+    d_roots = torch.from_numpy(roots.view(np.uint8).copy()).to(dev)
+    d_act = torch.empty(n, dtype=torch.int32, device=dev)
+    d_val = torch.empty(n * A, dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    leaves = n * A ** d
+
+    def step():
+        bcts.bcts_search_device(ctx, d_roots, n, d_act, d_val, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        bcts.bcts_profile(ctx, True)  # reset; record per-kernel events from here
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            t_wall0 = time.perf_counter()
+            for i in range(args.steps):
+                flush.zero_()  # L2 flush between steps, outside the timed events
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+            stream.synchronize()
+            t_wall = time.perf_counter() - t_wall0
+        torch.cuda.synchronize()
+        barrier(world)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    prof_ms, prof_cnt, launches = bcts.bcts_profile(ctx, False)
+    total_s = sum(step_ms) / 1e3
+    total_s = max_over_ranks(world, total_s, dev)
+    value = world * leaves * args.steps / total_s
+    decisions = world * n * args.steps / total_s
+
+    # end to end: host roots in, host actions + values out, every step
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        act, val = bcts.bcts_search(ctx, roots)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_times.append(dt)
+    e2e_total = max_over_ranks(world, sum(e2e_times), dev)
+    e2e_value = world * leaves * args.steps / e2e_total
+
+    if rank != 0:
+        ctx.close()
+        return
+
+    pk, pk_kind = peaks()
+    # dominant kernel class by device time inside the timed region
+    dom = max(prof_ms, key=lambda k: prof_ms[k])
+    roofline = None
+    if dom in MACS and prof_ms[dom] > 0:
+        # every leaf, root and depth-1 node runs the Q-network once per step
+        nodes = args.steps * (leaves + n + n * A) if d >= 2 else args.steps * (n + n * A)
+        macs = MACS[dom] if dom != "fc2" else A * 512
+        flops = 2.0 * macs * nodes
+        achieved = flops / (prof_ms[dom] / 1e3) / 1e12
+        if precision == "fp32_simt":
+            peak = pk.get("sm_max_mhz", 2032.0) * 1e6 * 148 * 128 * 2 / 1e12
+            bound, unit, pnote = "alu", "TFLOP/s", "FP32 FMA: 148 SMs x 128 lanes x 2 FLOP x max SM clock"
+        else:
+            peak = pk["bf16_tflops_sustained"]
+            bound, unit, pnote = "tensor", "TFLOP/s", f"bf16 dense sustained ({pk_kind})"
+        roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak, "traffic": None, "peak_note": pnote,
+                    "avg_launch_ms": prof_ms[dom] / max(prof_cnt[dom], 1)}
+    elif prof_ms[dom] > 0:
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": None, "traffic": None}
+
+    plain = None
+    if not args.no_plain and precision != "fp32_simt":
+        # the plain FP32 method: CUDA-core Q-network, one root per launch
+        pctx = bcts.bcts_create(W, A, d, wl["gamma"], wl["c"], precision="fp32_simt")
+        one = [d_roots[i * 80:(i + 1) * 80] for i in range(n)]
+        with torch.cuda.stream(stream):
+            bcts.bcts_search_device(pctx, one[0], 1, d_act, d_val, stream)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(n):
+                bcts.bcts_search_device(pctx, one[i], 1, d_act[i:i + 1], d_val[i * A:(i + 1) * A], stream)
+            e1.record(stream)
+            stream.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {"value": leaves / (pms / 1e3), "unit": "leaf nodes/s", "ms_per_step": pms,
+                 "how": "FP32 CUDA-core Q-network, one root per bcts_search_device call, same roots"}
+        pctx.close()
+
+    cb = None
+    if not args.no_cpu_baseline:
+        cb = cpu_baseline(W, wl)
+
+    lat = sorted(step_ms)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
+    clocks = clk.summary(pk.get("sm_max_mhz"))
+    line = {
+        "metric": METRIC, "value": value, "unit": "leaf nodes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32 (bf16x3 split products, f32 accumulate)", "bf16": "bf16", "fp8": "e4m3",
+                  "fp32_simt": "f32"}.get(precision, precision),
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "roots_per_step": n, "A": A, "d": d, "gamma": wl["gamma"],
+                   "correction": wl["c"], "leaves_per_step": leaves, "precision": precision,
+                   "l2": "flushed between steps (256 MB write); frames per step "
+                         f"{leaves * 28224 / 1e9:.2f} GB > 126 MB L2"},
+        "decisions_per_s": decisions,
+        "latency_ms": {"p50": p50, "p99": p99, "what": "one search of the 32-root batch, device time"},
+        "e2e": {"value": e2e_value, "unit": "leaf nodes/s", "h2d_bytes_per_step": int(n * 80),
+                "d2h_bytes_per_step": int(n * 4 + n * A * 4),
+                "ms_per_step": 1e3 * e2e_total / args.steps},
+        "gpu_launches": launches,
+        "kernel_ms": prof_ms, "kernel_launches": prof_cnt,
+        "roofline": roofline,
+        "plain_fp32": plain,
+        "speedup_vs_plain_fp32": (value / plain["value"]) if plain else None,
+        "cpu_baseline": cb,
+        "clocks": clocks,
+        "wall_s_timed": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

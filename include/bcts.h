@@ -1,0 +1,210 @@
+/*
+ * bcts.h -- C ABI of the B300 Batch-BFS / BCTS tree-search library (libbcts.so).
+ *
+ * The library implements the data-parallel hot path of "Improve Agents without
+ * Retraining: Parallel Tree Search with Off-Policy Correction" (Hallak et al.,
+ * NeurIPS 2021):
+ *   - Alg. 1 (Batch-BFS): every node of one depth is expanded at once; state and
+ *     accumulated reward are replicated A times, child = parent * A + a, the
+ *     simulator advances all children, R += gamma^i r; at depth d the leaves are
+ *     scored R += gamma^d max_a Q(s_d, a);
+ *   - Eq. 1 / Eq. 2: the d-step Q estimate per root action and its argmax;
+ *   - Prop. 1 and Sec. 3.3: Bellman errors delta(a) from the root and depth-1 Q;
+ *   - Eq. 7: the Bellman penalty B(delta_e, delta_o, A, d), scaled by the swept
+ *     multiplier c of Sec. 5.1;
+ *   - Eq. 3 / Eq. 4: corrected root values and the BCTS action.
+ * The simulator is a synthetic integer sprite environment (stand-in for Atari
+ * via CuLE, Sec. 4) rendered to the 4-frame 84x84 uint8 stack of Sec. 5, and
+ * leaves are scored by a Nature-DQN Q-network (stand-in for Rainbow, Sec. 5.1).
+ *
+ * Conventions for every entry point:
+ *   - returns a status (BCTS_OK = 0, negative = error); never aborts, never
+ *     exits; after an error bcts_last_error(ctx) (or bcts_last_error(NULL) for
+ *     calls without a context) describes it;
+ *   - "host" pointers are caller-owned host memory, "device" pointers are
+ *     caller-owned device memory on the context's device; the library never
+ *     frees caller memory;
+ *   - `stream` arguments are a cudaStream_t passed as void*; NULL means the
+ *     context's own stream (for calls without a context: the legacy default
+ *     stream).  Device-pointer calls are asynchronous on that stream.
+ *   - ties in every argmax are broken towards the lowest index.
+ */
+#ifndef BCTS_H
+#define BCTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BCTS_API __attribute__((visibility("default")))
+#else
+#define BCTS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BCTS_OK = 0,
+    BCTS_PENDING = 1,     /* bcts_poll: request not finished yet */
+    BCTS_EINVAL = -1,     /* bad argument */
+    BCTS_ENOMEM = -2,     /* device or host allocation failed / over budget */
+    BCTS_ECUDA = -3,      /* a CUDA call failed */
+    BCTS_ETIMEOUT = -4,   /* a bounded wait ran out */
+    BCTS_EBUSY = -5,      /* queue full */
+    BCTS_ENOTICKET = -6,  /* unknown or already collected ticket */
+    BCTS_EDEVICE = -7,    /* a kernel reported an error through its error word */
+    BCTS_ENOKERNEL = -8   /* the requested path is not available on this device */
+};
+
+/* Leaf Q-network arithmetic. */
+enum {
+    BCTS_PREC_FP32 = 0,      /* FP32-class: tcgen05 BF16 split (hi+lo) products, FP32 accumulate */
+    BCTS_PREC_BF16 = 1,      /* BF16 operands, FP32 accumulate */
+    BCTS_PREC_FP8 = 2,       /* FP8 E4M3 operands, per-output-channel weight scales, FP32 accumulate */
+    BCTS_PREC_FP32_SIMT = 3  /* plain FP32 on CUDA cores (the unoptimised baseline) */
+};
+
+/* Environment state, 80 bytes, little endian:
+ *   pos[h][k] = (x, y) cell of object k at history slot h (slot 3 = newest),
+ *               0 <= x, y <= 20; object 0 is the agent, 1 the reward, 2-3 hazards;
+ *   vel[k]    = per-tick velocity of object k (object 0 unused, 0);
+ *   tick      = step counter (drives the respawn hash);  pad = 0. */
+typedef struct bcts_state {
+    int16_t pos[4][4][2];
+    int8_t vel[4][2];
+    uint32_t tick;
+    uint32_t pad;
+} bcts_state;
+
+/* Simulator description.  kind 0 = the sprite environment (the only one). */
+typedef struct bcts_env_desc {
+    int kind;
+} bcts_env_desc;
+
+typedef struct bcts_options {
+    int precision;              /* BCTS_PREC_* (default BCTS_PREC_FP32) */
+    size_t frame_budget_bytes;  /* serving admission budget for in-flight leaf work (0 = 8 GiB) */
+    int max_roots;              /* serving: requests fused per pass (0 = 64) */
+    int flags;                  /* reserved, 0 */
+    int leaf_chunk;             /* leaves rendered + scored per pass (0 = automatic) */
+} bcts_options;
+
+typedef struct bcts_ctx bcts_ctx;
+
+/* Number of FP32 Q-network parameters for A actions (PyTorch order, see bcts_create). */
+BCTS_API size_t bcts_qnet_numel(int A);
+
+/*
+ * Create a search context on the current CUDA device.
+ *   env          : NULL or {kind = 0}
+ *   qnet_weights : host, bcts_qnet_numel(A) floats in PyTorch parameter order:
+ *                  conv1.w[32][4][8][8], conv1.b[32], conv2.w[64][32][4][4],
+ *                  conv2.b[64], conv3.w[64][64][3][3], conv3.b[64],
+ *                  fc1.w[512][3136] (input flattened C,H,W), fc1.b[512],
+ *                  fc2.w[A][512], fc2.b[A]; input pixels are scaled by 1/255.
+ *                  Copied at create; the caller may free it afterwards.
+ *   A            : action count, 1..18 (like Atari's full action set): actions
+ *                  0..8 move the agent one cell noop, up, right, left, down,
+ *                  up-right, up-left, down-right, down-left; 9..17 the same two
+ *                  cells at a time
+ *   d            : default search depth, 0..6 (Alg. 1's d; d = 0 returns pi_o)
+ *   gamma        : discount in (0, 1]
+ *   correction   : multiplier c of the Eq. 7 penalty (Sec. 5.1 sweeps it);
+ *                  0 = vanilla tree search (Eq. 2), 1 = Eq. 3 as printed
+ *   opt          : NULL = defaults
+ *   out          : receives the context
+ * Errors: BCTS_EINVAL (bad A, d, gamma, NULL weights/out), BCTS_ENOMEM, BCTS_ECUDA.
+ */
+BCTS_API int bcts_create(const bcts_env_desc *env, const float *qnet_weights, int A, int d, float gamma,
+                float correction, const bcts_options *opt, bcts_ctx **out);
+
+/* Free every resource of the context (waits for its pending work). NULL is a no-op. */
+BCTS_API void bcts_destroy(bcts_ctx *ctx);
+
+/* Message of the last error on this context (or of the last context-free call
+ * on this thread when ctx is NULL).  Valid until the next call on the context. */
+BCTS_API const char *bcts_last_error(const bcts_ctx *ctx);
+
+/*
+ * Search n roots at the context's depth (Alg. 1 + Eq. 3/4), synchronously.
+ *   roots           : host, n states
+ *   out_action      : host, n int32 -- BCTS action per root (Eq. 4)
+ *   out_root_values : host, n*A floats -- corrected d-step values (Eq. 3),
+ *                     row i = root i; for d = 0 the root Q-values
+ * Copies inputs to the device, runs, copies results back, synchronises.
+ * n = 0 is a no-op.  Errors: BCTS_EINVAL, BCTS_ENOMEM, BCTS_ECUDA, BCTS_EDEVICE.
+ */
+BCTS_API int bcts_search(bcts_ctx *ctx, const bcts_state *roots, int n, int32_t *out_action, float *out_root_values);
+
+/* Same as bcts_search with device pointers, asynchronous on `stream`.  The
+ * context's buffers are reused by the next search on the same context, so
+ * searches on one context must not overlap (the library orders them on the
+ * context's stream when stream is NULL). */
+BCTS_API int bcts_search_device(bcts_ctx *ctx, const bcts_state *d_roots, int n, int32_t *d_out_action,
+                       float *d_out_root_values, void *stream);
+
+/*
+ * Batched form: n roots, root i searched at depth d_i in [0, 6] with A_i actions
+ * in [1, context A] (FC2 rows 0..A_i-1 are used).  Host pointers, synchronous.
+ * out_root_values is n * (context A) floats; row i holds A_i values, the rest 0.
+ */
+BCTS_API int bcts_search_mixed(bcts_ctx *ctx, const bcts_state *roots, const int32_t *depths, const int32_t *actions,
+                      int n, int32_t *out_action, float *out_root_values);
+
+/*
+ * Serving form: continuous batching.  bcts_submit queues one decision request
+ * (root, depth d in [0, 6], A in [1, context A]) and returns at once with a
+ * ticket; a scheduler thread admits queued requests while their leaf work fits
+ * the frame budget, runs the admitted requests' levels together on the device,
+ * and completes them independently.  bcts_poll waits up to timeout_us
+ * microseconds (0 = do not wait, <0 = wait without limit) for a ticket:
+ * BCTS_OK with out_action (1 int32) and out_root_values (A floats, host)
+ * filled and the ticket released; BCTS_PENDING if not finished; BCTS_ENOTICKET
+ * for unknown tickets.  Both are thread-safe.
+ */
+BCTS_API int bcts_submit(bcts_ctx *ctx, const bcts_state *root, int d, int A, uint64_t *out_ticket);
+BCTS_API int bcts_poll(bcts_ctx *ctx, uint64_t ticket, int32_t *out_action, float *out_root_values, int timeout_us);
+
+/* ---- step-level entry points (device pointers; Alg. 1's individual steps) ---- */
+
+/*
+ * Alg. 1 replicate + advance + accumulate: child c = p * A + a of parent p gets
+ * state G(parent p, action a) and R[c] = R[p] + gamma_pow * r  (gamma_pow = gamma^i
+ * at depth i).  parents: n_parents states; parent_R: n_parents floats (NULL =
+ * zeros); children: n_parents*A states; child_R: n_parents*A floats (may be NULL);
+ * child_reward: n_parents*A int8 rewards (may be NULL).  No context needed.
+ */
+BCTS_API int bcts_expand(const bcts_state *d_parents, const float *d_parent_R, int64_t n_parents, int A, float gamma_pow,
+                bcts_state *d_children, float *d_child_R, int8_t *d_child_reward, void *stream);
+
+/* Render n states to n frame stacks, uint8 [n][4][84][84], channel h = history slot h. */
+BCTS_API int bcts_render(const bcts_state *d_states, int64_t n, uint8_t *d_frames, void *stream);
+
+/* ---- measurement ------------------------------------------------------------ */
+/* Kernel classes timed by bcts_profile. */
+enum {
+    BCTS_KERN_EXPAND = 0, BCTS_KERN_RENDER, BCTS_KERN_CONV1, BCTS_KERN_CONV2, BCTS_KERN_CONV3,
+    BCTS_KERN_FC1, BCTS_KERN_FC2, BCTS_KERN_BACKUP, BCTS_KERN_COUNT
+};
+
+/*
+ * Per-kernel-class device time of this context's searches.  enable = 1 starts
+ * recording (a CUDA event pair on the launching stream around every kernel),
+ * 0 stops.  On each call the totals since the previous call are returned and
+ * reset: out_ms[BCTS_KERN_COUNT] milliseconds and out_launches[BCTS_KERN_COUNT]
+ * launches per class (either may be NULL); *out_total_launches (may be NULL)
+ * counts every kernel launch of the context, recorded or not.  Synchronises
+ * the context's pending work.  Not for use while a search runs on another thread.
+ */
+BCTS_API int bcts_profile(bcts_ctx *ctx, int enable, double *out_ms, int64_t *out_launches,
+                          int64_t *out_total_launches);
+
+/* Score n frame stacks with the context's Q-network in its precision: q [n][A] floats. */
+BCTS_API int bcts_qnet(bcts_ctx *ctx, const uint8_t *d_frames, int64_t n, float *d_q, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BCTS_H */

@@ -1,0 +1,230 @@
+// env.cu -- the simulator and the renderer of Alg. 1 on the GPU.
+//
+//   expand_kernel : Alg. 1's loop body for one depth: every child c = p * A + a of
+//                   every frontier parent p is produced at once (replicate state
+//                   and reward A times, advance the simulator with action a,
+//                   R += gamma^i r).  One thread per child; integer arithmetic only.
+//   render_kernel : the 4 x 84 x 84 uint8 frame stack of a state (Sec. 5 frame
+//                   stacking), one thread per 16 output bytes, 16-byte stores.
+//
+// The sprite environment (agent + reward + two hazards on a 21 x 21 grid) is the
+// stand-in for the Atari emulator the paper runs on the GPU (Sec. 4).
+#include <cstdio>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bcts {
+
+namespace {
+
+// Action direction table (noop, up, right, left, down, up-right, up-left,
+// down-right, down-left), packed 2 bits per entry as (delta + 1) so that a warp
+// holding many different actions reads it from a register, not a table.
+constexpr int kDX[9] = {0, 0, 1, -1, 0, 1, -1, 1, -1};
+constexpr int kDY[9] = {0, -1, 0, 0, 1, -1, -1, 1, 1};
+constexpr uint32_t pack_dirs(const int (&v)[9]) {
+  uint32_t p = 0;
+  for (int i = 0; i < 9; ++i) p |= uint32_t(v[i] + 1) << (2 * i);
+  return p;
+}
+constexpr uint32_t kDXP = pack_dirs(kDX);
+constexpr uint32_t kDYP = pack_dirs(kDY);
+
+// Sprite masks (4x4, bit r*4+c) and palette of objects 0..3, packed.
+constexpr uint64_t kSprites = 0xF99F96696FF6FFFFull;  // agent block, diamond, X, ring
+constexpr uint32_t kPalette = 0x4080C0F0u;            // 240, 192, 128, 64
+
+union StateRegs {
+  uint4 v[5];
+  bcts_state s;
+};
+
+__device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
+  // C. Wellons' lowbias32 integer hash.
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+__device__ __forceinline__ void bounce(int &p, int &v) {
+  int q = p + v;
+  if (q < 0) {
+    q = -q;
+    v = -v;
+  }
+  if (q > kGrid - 1) {
+    q = 2 * (kGrid - 1) - q;
+    v = -v;
+  }
+  p = q;
+}
+
+// One tick: agent moves by the action and clamps, objects move and reflect,
+// contact (same cell) pays +1 / -1 and respawns the object at a hashed cell;
+// the history slots shift by one.  Returns the reward clipped to [-1, 1].
+__device__ __forceinline__ int sprite_step(const bcts_state &s, int a, bcts_state &n) {
+  const int dir = a % 9, speed = 1 + a / 9;
+  const int dx = int((kDXP >> (2 * dir)) & 3u) - 1;
+  const int dy = int((kDYP >> (2 * dir)) & 3u) - 1;
+  const int ax = min(max(s.pos[3][0][0] + speed * dx, 0), kGrid - 1);
+  const int ay = min(max(s.pos[3][0][1] + speed * dy, 0), kGrid - 1);
+#pragma unroll
+  for (int h = 0; h < kHist - 1; ++h)
+#pragma unroll
+    for (int k = 0; k < kObj; ++k) {
+      n.pos[h][k][0] = s.pos[h + 1][k][0];
+      n.pos[h][k][1] = s.pos[h + 1][k][1];
+    }
+  n.pos[3][0][0] = (int16_t)ax;
+  n.pos[3][0][1] = (int16_t)ay;
+  n.vel[0][0] = s.vel[0][0];
+  n.vel[0][1] = s.vel[0][1];
+  int reward = 0;
+#pragma unroll
+  for (int k = 1; k < kObj; ++k) {
+    int x = s.pos[3][k][0], y = s.pos[3][k][1];
+    int vx = s.vel[k][0], vy = s.vel[k][1];
+    bounce(x, vx);
+    bounce(y, vy);
+    if (x == ax && y == ay) {
+      reward += (k == 1) ? 1 : -1;
+      const uint32_t key = s.tick * 0x9E3779B1u + uint32_t(k) * 0x85EBCA77u +
+                           uint32_t(ax * kGrid + ay) * 0xC2B2AE3Du;
+      const uint32_t hsh = lowbias32(key);
+      x = int(hsh % kGrid);
+      y = int((hsh >> 16) % kGrid);
+    }
+    n.pos[3][k][0] = (int16_t)x;
+    n.pos[3][k][1] = (int16_t)y;
+    n.vel[k][0] = (int8_t)vx;
+    n.vel[k][1] = (int8_t)vy;
+  }
+  n.tick = s.tick + 1u;
+  n.pad = 0u;
+  return max(-1, min(1, reward));
+}
+
+__global__ void __launch_bounds__(256) expand_kernel(const uint4 *__restrict__ parents,
+                                                     const float *__restrict__ parent_R, uint32_t n_child,
+                                                     int A, float gamma_pow, uint4 *__restrict__ children,
+                                                     float *__restrict__ child_R,
+                                                     int8_t *__restrict__ child_reward) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_child) return;
+  const uint32_t p = c / uint32_t(A);
+  const int a = int(c - p * uint32_t(A));
+  StateRegs in, out;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) in.v[i] = __ldg(parents + size_t(p) * 5 + i);
+  const int r = sprite_step(in.s, a, out.s);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) children[size_t(c) * 5 + i] = out.v[i];
+  if (child_R) {
+    const float base = parent_R ? __ldg(parent_R + p) : 0.0f;
+    child_R[c] = base + gamma_pow * float(r);
+  }
+  if (child_reward) child_reward[c] = (int8_t)r;
+}
+
+// Frame layout per state: [4 slots][84 rows][21 words]; word (h, y, cx) holds the
+// 4 pixels of cell cx in pixel row y.  A 16-byte chunk is 4 consecutive words.
+__global__ void __launch_bounds__(256) render_kernel(const uint4 *__restrict__ states, uint64_t n_chunks,
+                                                     uint4 *__restrict__ frames) {
+  constexpr uint32_t kChunksPerSlot = kPix * kPix / 16;  // 441
+  constexpr uint32_t kChunksPerState = kHist * kChunksPerSlot;
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n_chunks;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t st = q / kChunksPerState;
+    const uint32_t j = uint32_t(q - st * kChunksPerState);
+    const uint32_t h = j / kChunksPerSlot;
+    const uint32_t w0 = (j - h * kChunksPerSlot) * 4;  // first word in the slot
+    const uint4 P = __ldg(states + st * 5 + h);        // pos[h][0..3][x,y], 16 bytes
+    int ox[4], oy[4];
+    const uint32_t pw[4] = {P.x, P.y, P.z, P.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ox[k] = int(int16_t(pw[k] & 0xFFFFu));
+      oy[k] = int(int16_t(pw[k] >> 16));
+    }
+    uint32_t word[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t w = w0 + i;
+      const int y = int(w / kGrid), cx = int(w - uint32_t(y) * kGrid);
+      const int cy = y >> 2, sr = y & 3;
+      uint32_t v = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (ox[k] == cx && oy[k] == cy) {
+          const uint32_t bits = uint32_t(kSprites >> (16 * k + 4 * sr)) & 0xFu;
+          const uint32_t bytemask = ((bits * 0x00204081u) & 0x01010101u) * 0xFFu;
+          const uint32_t pal = ((kPalette >> (8 * k)) & 0xFFu) * 0x01010101u;
+          v = (v & ~bytemask) | (pal & bytemask);
+        }
+      }
+      word[i] = v;
+    }
+    frames[q] = make_uint4(word[0], word[1], word[2], word[3]);
+  }
+}
+
+}  // namespace
+
+int launch_expand(const bcts_state *parents, const float *parent_R, int64_t n_parents, int A, float gamma_pow,
+                  bcts_state *children, float *child_R, int8_t *child_reward, cudaStream_t stream) {
+  const int64_t n_child = n_parents * A;
+  if (n_child <= 0) return BCTS_OK;
+  if (n_child > 0x7FFFFFFFLL) return BCTS_EINVAL;
+  const int threads = 256;
+  const unsigned blocks = unsigned((n_child + threads - 1) / threads);
+  ProfScope ps(K_EXPAND, stream);
+  expand_kernel<<<blocks, threads, 0, stream>>>(reinterpret_cast<const uint4 *>(parents), parent_R,
+                                                uint32_t(n_child), A, gamma_pow,
+                                                reinterpret_cast<uint4 *>(children), child_R, child_reward);
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
+
+int launch_render(const bcts_state *states, int64_t n, uint8_t *frames, cudaStream_t stream) {
+  if (n <= 0) return BCTS_OK;
+  const uint64_t n_chunks = uint64_t(n) * (kFrameBytes / 16);
+  const int threads = 256;
+  int sms = 148;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t want = (n_chunks + threads - 1) / threads;
+  const uint64_t cap = uint64_t(sms) * 8 * 16;  // grid-stride beyond 16 waves
+  const unsigned blocks = unsigned(want < cap ? want : cap);
+  ProfScope ps(K_RENDER, stream);
+  render_kernel<<<blocks, threads, 0, stream>>>(reinterpret_cast<const uint4 *>(states), n_chunks,
+                                                reinterpret_cast<uint4 *>(frames));
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
+
+}  // namespace bcts
+
+extern "C" int bcts_expand(const bcts_state *d_parents, const float *d_parent_R, int64_t n_parents, int A,
+                           float gamma_pow, bcts_state *d_children, float *d_child_R, int8_t *d_child_reward,
+                           void *stream) {
+  if (!d_parents || !d_children || n_parents < 0 || A < 1 || A > bcts::kMaxA) {
+    bcts::set_thread_error("bcts_expand: invalid argument");
+    return BCTS_EINVAL;
+  }
+  const int rc = bcts::launch_expand(d_parents, d_parent_R, n_parents, A, gamma_pow, d_children, d_child_R,
+                                     d_child_reward, (cudaStream_t)stream);
+  if (rc != BCTS_OK) bcts::set_thread_error("bcts_expand: launch failed");
+  return rc;
+}
+
+extern "C" int bcts_render(const bcts_state *d_states, int64_t n, uint8_t *d_frames, void *stream) {
+  if (!d_states || !d_frames || n < 0) {
+    bcts::set_thread_error("bcts_render: invalid argument");
+    return BCTS_EINVAL;
+  }
+  const int rc = bcts::launch_render(d_states, n, d_frames, (cudaStream_t)stream);
+  if (rc != BCTS_OK) bcts::set_thread_error("bcts_render: launch failed");
+  return rc;
+}

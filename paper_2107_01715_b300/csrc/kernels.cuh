@@ -1,0 +1,46 @@
+// kernels.cuh -- internal launchers shared by the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace bcts {
+
+// env.cu
+int launch_expand(const bcts_state *parents, const float *parent_R, int64_t n_parents, int A, float gamma_pow,
+                  bcts_state *children, float *child_R, int8_t *child_reward, cudaStream_t stream);
+int launch_render(const bcts_state *states, int64_t n, uint8_t *frames, cudaStream_t stream);
+
+// Weights of the plain FP32 CUDA-core Q-network, in the layouts its kernels read:
+//   c1w [32][256]  k = c*64 + ky*8 + kx, pre-scaled by 1/255
+//   c2w [64][512]  k = (ky*4 + kx)*32 + c      (input NHWC)
+//   c3w [64][576]  k = (ky*3 + kx)*64 + c
+//   f1w [512][3136] k = (y*7 + x)*64 + c        (conv3 map NHWC-flattened)
+//   f2w [A][512]
+struct SimtWeights {
+  const float *c1w, *c1b, *c2w, *c2b, *c3w, *c3b, *f1w, *f1b, *f2w, *f2b;
+  int A;
+};
+
+// Scratch the plain path needs per chunk of `chunk` leaves (bytes).
+size_t simt_scratch_bytes(int64_t chunk);
+
+// Q-network on n frame stacks: q [n][A] (may be NULL), maxq [n] (may be NULL).
+int simt_qnet_forward(const SimtWeights &w, const uint8_t *frames, int64_t n, float *q, float *maxq,
+                      void *scratch, cudaStream_t stream);
+
+// qnet_tc.cu (tensor-core paths)
+struct TcWeights;  // defined in qnet_tc.cu
+size_t tc_scratch_bytes(int64_t chunk, int precision);
+int tc_weights_create(const float *host_weights, int A, int precision, TcWeights **out, std::string &err);
+void tc_weights_destroy(TcWeights *w);
+int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
+                    float *maxq, void *scratch, cudaStream_t stream, int *d_err);
+
+// search.cu backup kernels
+int launch_segment_max(const float *R, const float *maxq, int64_t n_seg, int64_t seg_len, float gamma_pow,
+                       float *V, cudaStream_t stream);
+int launch_finalize(const float *q0, const float *maxq1, const float *r1, const float *V, int n, int A,
+                    int depth, int A_stride, float gamma, float gamma_d, float corr, int32_t *action,
+                    float *values, cudaStream_t stream);
+
+}  // namespace bcts

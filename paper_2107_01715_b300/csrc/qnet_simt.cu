@@ -1,0 +1,208 @@
+// qnet_simt.cu -- plain FP32 Nature-DQN on CUDA cores: the unoptimised baseline
+// the tensor-core paths are measured against (and the reference for "plain FP32"
+// one-root-per-launch search).
+//
+// Each layer is one register-blocked implicit GEMM  out[M][N] = relu(A[M][K] W[N][K]^T + b)
+// whose A operand is gathered on the fly from the previous activation map
+// (no im2col buffer): M = nodes * output pixels, K = Cin * kh * kw.  Activations
+// are stored NHWC, so a GEMM row-major output is already the next layer's input.
+// FC2 and the max over actions (Alg. 1's leaf term max_a Q) run in one warp per node.
+#include <cstdio>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bcts {
+namespace {
+
+struct GeoConv1 {  // frames uint8 [n][4][84][84] -> [n][400][32]
+  using In = uint8_t;
+  static constexpr int K = kK1, N = kC1, MPL = kP1;
+  __device__ static __forceinline__ float load(const In *in, int m, int k) {
+    const int leaf = m / MPL, p = m - leaf * MPL;
+    const int oy = p / 20, ox = p - oy * 20;
+    const int c = k >> 6, ky = (k >> 3) & 7, kx = k & 7;
+    return float(__ldg(in + size_t(leaf) * kFrameBytes + c * 7056 + (oy * 4 + ky) * 84 + ox * 4 + kx));
+  }
+};
+struct GeoConv2 {  // [n][20][20][32] -> [n][81][64]
+  using In = float;
+  static constexpr int K = kK2, N = kC2, MPL = kP2;
+  __device__ static __forceinline__ float load(const In *in, int m, int k) {
+    const int leaf = m / MPL, p = m - leaf * MPL;
+    const int oy = p / 9, ox = p - oy * 9;
+    const int kk = k >> 5, c = k & 31, ky = kk >> 2, kx = kk & 3;
+    return __ldg(in + size_t(leaf) * (kP1 * kC1) + ((oy * 2 + ky) * 20 + ox * 2 + kx) * kC1 + c);
+  }
+};
+struct GeoConv3 {  // [n][9][9][64] -> [n][49][64]
+  using In = float;
+  static constexpr int K = kK3, N = kC3, MPL = kP3;
+  __device__ static __forceinline__ float load(const In *in, int m, int k) {
+    const int leaf = m / MPL, p = m - leaf * MPL;
+    const int oy = p / 7, ox = p - oy * 7;
+    const int kk = k >> 6, c = k & 63, ky = kk / 3, kx = kk - ky * 3;
+    return __ldg(in + size_t(leaf) * (kP2 * kC2) + ((oy + ky) * 9 + ox + kx) * kC2 + c);
+  }
+};
+struct GeoFc1 {  // [n][3136] -> [n][512]
+  using In = float;
+  static constexpr int K = kKF, N = kF1, MPL = 1;
+  __device__ static __forceinline__ float load(const In *in, int m, int k) {
+    return __ldg(in + size_t(m) * kKF + k);
+  }
+};
+
+// Block tile BM x BN, K step BK; each thread owns TM x TN outputs.
+template <class Geo, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    simt_gemm(const typename Geo::In *__restrict__ in, const float *__restrict__ W,
+              const float *__restrict__ bias, float *__restrict__ out, int M) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int K = Geo::K, N = Geo::N;
+  static_assert(K % BK == 0 && N % BN == 0, "tile");
+  static_assert((BM * BK) % NT == 0 && (BN * BK) % NT == 0, "loads");
+  __shared__ float As[BK][BM + 4];
+  __shared__ float Bs[BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  constexpr int AL = BM * BK / NT, BL = BN * BK / NT;
+  float ra[AL], rb[BL];
+  auto load_tiles = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < AL; ++i) {
+      const int e = tid + i * NT, ki = e % BK, mi = e / BK;
+      const int m = m0 + mi;
+      ra[i] = (m < M) ? Geo::load(in, m, k0 + ki) : 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < BL; ++i) {
+      const int e = tid + i * NT, ki = e % BK, ni = e / BK;
+      rb[i] = __ldg(W + size_t(n0 + ni) * K + k0 + ki);
+    }
+  };
+  load_tiles(0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < AL; ++i) {
+      const int e = tid + i * NT;
+      As[e % BK][e / BK] = ra[i];
+    }
+#pragma unroll
+    for (int i = 0; i < BL; ++i) {
+      const int e = tid + i * NT;
+      Bs[e % BK][e / BK] = rb[i];
+    }
+    __syncthreads();
+    if (k0 + BK < K) load_tiles(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int m = m0 + ty * TM + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int n = n0 + tx * TN + j;
+      const float v = acc[i][j] + __ldg(bias + n);
+      out[size_t(m) * N + n] = v > 0.f ? v : 0.f;
+    }
+  }
+}
+
+// FC2 + max over actions: one warp per node.  q = W2 h + b2; maxq = max_a q[a]
+// (first maximum on ties).
+__global__ void __launch_bounds__(256) fc2_max_kernel(const float *__restrict__ h, const float *__restrict__ W2,
+                                                      const float *__restrict__ b2, int A, int64_t n,
+                                                      float *__restrict__ q, float *__restrict__ maxq) {
+  __shared__ float w[kMaxA * kF1];
+  for (int i = threadIdx.x; i < A * kF1; i += blockDim.x) w[i] = W2[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t node = int64_t(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (node >= n) return;
+  float x[16];
+  const float4 *hv = reinterpret_cast<const float4 *>(h + node * kF1);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float4 t = __ldg(hv + lane + 32 * j);
+    x[4 * j] = t.x;
+    x[4 * j + 1] = t.y;
+    x[4 * j + 2] = t.z;
+    x[4 * j + 3] = t.w;
+  }
+  float best = 0.f;
+  for (int a = 0; a < A; ++a) {
+    const float *wa = w + a * kF1;
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int base = 4 * (lane + 32 * j);
+      s = fmaf(x[4 * j], wa[base], s);
+      s = fmaf(x[4 * j + 1], wa[base + 1], s);
+      s = fmaf(x[4 * j + 2], wa[base + 2], s);
+      s = fmaf(x[4 * j + 3], wa[base + 3], s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    s += __ldg(b2 + a);
+    if (q && lane == 0) q[node * A + a] = s;
+    if (a == 0 || s > best) best = s;
+  }
+  if (maxq && lane == 0) maxq[node] = best;
+}
+
+template <class Geo, int BM, int BN, int TM, int TN>
+int run_gemm(int kind, const typename Geo::In *in, const float *W, const float *b, float *out, int64_t nodes,
+             cudaStream_t st) {
+  const int64_t M = nodes * Geo::MPL;
+  if (M > 0x7FFFFFFFLL) return BCTS_EINVAL;
+  dim3 grid(unsigned((M + BM - 1) / BM), Geo::N / BN);
+  ProfScope ps(kind, st);
+  simt_gemm<Geo, BM, BN, 16, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(in, W, b, out, int(M));
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
+
+}  // namespace
+
+size_t simt_scratch_bytes(int64_t chunk) {
+  return size_t(chunk) * sizeof(float) * (kP1 * kC1 + kP2 * kC2 + kP3 * kC3 + kF1) + 4096;
+}
+
+int simt_qnet_forward(const SimtWeights &w, const uint8_t *frames, int64_t n, float *q, float *maxq,
+                      void *scratch, cudaStream_t st) {
+  if (n <= 0) return BCTS_OK;
+  float *a1 = static_cast<float *>(scratch);
+  float *a2 = a1 + size_t(n) * kP1 * kC1;
+  float *a3 = a2 + size_t(n) * kP2 * kC2;
+  float *a4 = a3 + size_t(n) * kP3 * kC3;
+  int rc;
+  if ((rc = run_gemm<GeoConv1, 128, 32, 8, 2>(K_CONV1, frames, w.c1w, w.c1b, a1, n, st)) != BCTS_OK) return rc;
+  if ((rc = run_gemm<GeoConv2, 128, 64, 8, 4>(K_CONV2, a1, w.c2w, w.c2b, a2, n, st)) != BCTS_OK) return rc;
+  if ((rc = run_gemm<GeoConv3, 128, 64, 8, 4>(K_CONV3, a2, w.c3w, w.c3b, a3, n, st)) != BCTS_OK) return rc;
+  if ((rc = run_gemm<GeoFc1, 128, 64, 8, 4>(K_FC1, a3, w.f1w, w.f1b, a4, n, st)) != BCTS_OK) return rc;
+  const int warps = 8;
+  ProfScope ps(K_FC2, st);
+  fc2_max_kernel<<<unsigned((n + warps - 1) / warps), warps * 32, 0, st>>>(a4, w.f2w, w.f2b, w.A, n, q, maxq);
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
+
+}  // namespace bcts

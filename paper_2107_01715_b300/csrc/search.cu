@@ -1,0 +1,516 @@
+// search.cu -- the search context, the level-synchronous Batch-BFS driver
+// (Alg. 1), the backup kernels (Eq. 1 max over each root action's sub-tree,
+// Prop. 1 Bellman errors, Eq. 7 penalty, Eq. 3 correction, Eq. 4 argmax) and the
+// C-ABI entry points that run them.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "search.cuh"
+
+namespace bcts {
+
+namespace {
+thread_local std::string g_thread_err;
+}
+
+void set_thread_error(const std::string &msg) { g_thread_err = msg; }
+const char *thread_error() { return g_thread_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// Backup kernels
+// ---------------------------------------------------------------------------
+namespace {
+
+// V[s] = max over the seg_len consecutive leaves of segment s of R + gamma^d maxq
+// (Alg. 1's leaf term; Eq. 1's max over a_1..a_d for root action s mod A).
+__global__ void __launch_bounds__(128) segment_max_kernel(const float *__restrict__ R,
+                                                          const float *__restrict__ maxq, int64_t seg_len,
+                                                          float gamma_pow, float *__restrict__ V) {
+  const int64_t s = blockIdx.x;
+  const int64_t base = s * seg_len;
+  float best = -INFINITY;
+  for (int64_t i = threadIdx.x; i < seg_len; i += blockDim.x) {
+    const float v = __ldg(R + base + i) + gamma_pow * __ldg(maxq + base + i);
+    best = fmaxf(best, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  __shared__ float part[4];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = part[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, part[w]);
+    V[s] = b;
+  }
+}
+
+// One thread per root: pi_o = argmax Q_0 (Sec. 3.3), delta(a) from depths 0
+// and 1 (Prop. 1), delta_o = |delta(pi_o)|, delta_e = mean |delta(a)| over
+// a != pi_o, B by Eq. 7, corrected values (Eq. 3, scaled by c), action (Eq. 4).
+__global__ void finalize_kernel(const float *__restrict__ q0, const float *__restrict__ maxq1,
+                                const float *__restrict__ r1, const float *__restrict__ V, int n, int A,
+                                int depth, int A_stride, float gamma, float gamma_d, float corr,
+                                int32_t *__restrict__ action, float *__restrict__ values) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float *q = q0 + size_t(i) * A;
+  int pi_o = 0;
+  for (int a = 1; a < A; ++a)
+    if (q[a] > q[pi_o]) pi_o = a;
+  float *out = values + size_t(i) * A_stride;
+  if (depth == 0) {
+    for (int a = 0; a < A; ++a) out[a] = q[a];
+    for (int a = A; a < A_stride; ++a) out[a] = 0.f;
+    action[i] = pi_o;
+    return;
+  }
+  float d_o = 0.f, d_e = 0.f;
+  for (int a = 0; a < A; ++a) {
+    const float delta = r1[size_t(i) * A + a] + gamma * maxq1[size_t(i) * A + a] - q[a];
+    if (a == pi_o)
+      d_o = fabsf(delta);
+    else
+      d_e += fabsf(delta);
+  }
+  if (A > 1) d_e /= float(A - 1);
+  const float B = sqrtf(logf(float(A))) * (d_e * sqrtf(float(depth)) - d_o * sqrtf(float(depth - 1))) -
+                  (d_e - d_o) * 0.35355339059327373f;  // 1 / sqrt(8)
+  const float pen = gamma_d * corr * B;
+  int best = 0;
+  float bestv = -INFINITY;
+  for (int a = 0; a < A; ++a) {
+    const float v = V[size_t(i) * A + a] - (a == pi_o ? 0.f : pen);
+    out[a] = v;
+    if (a == 0 || v > bestv) {
+      bestv = v;
+      best = a;
+    }
+  }
+  for (int a = A; a < A_stride; ++a) out[a] = 0.f;
+  action[i] = best;
+}
+
+}  // namespace
+
+int launch_segment_max(const float *R, const float *maxq, int64_t n_seg, int64_t seg_len, float gamma_pow,
+                       float *V, cudaStream_t st) {
+  if (n_seg <= 0) return BCTS_OK;
+  ProfScope ps(K_BACKUP, st);
+  segment_max_kernel<<<unsigned(n_seg), 128, 0, st>>>(R, maxq, seg_len, gamma_pow, V);
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
+
+int launch_finalize(const float *q0, const float *maxq1, const float *r1, const float *V, int n, int A, int depth,
+                    int A_stride, float gamma, float gamma_d, float corr, int32_t *action, float *values,
+                    cudaStream_t st) {
+  if (n <= 0) return BCTS_OK;
+  ProfScope ps(K_BACKUP, st);
+  finalize_kernel<<<unsigned((n + 127) / 128), 128, 0, st>>>(q0, maxq1, r1, V, n, A, depth, A_stride, gamma,
+                                                              gamma_d, corr, action, values);
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Context helpers
+// ---------------------------------------------------------------------------
+int Ctx::fail(int code, const std::string &msg) {
+  err = msg;
+  set_thread_error(msg);
+  return code;
+}
+
+int Ctx::ensure(DevBuf &b, size_t bytes) {
+  if (bytes <= b.cap) return BCTS_OK;
+  if (b.p) {
+    cudaStreamSynchronize(stream);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  const size_t want = (bytes + 255) & ~size_t(255);
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BCTS_ENOMEM, "device allocation of " + std::to_string(want) + " bytes failed");
+  }
+  b.cap = want;
+  return BCTS_OK;
+}
+
+int Ctx::ensure_host(HostBuf &b, size_t bytes) {
+  if (bytes <= b.cap) return BCTS_OK;
+  if (b.p) {
+    cudaStreamSynchronize(stream);
+    cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  const size_t want = (bytes + 255) & ~size_t(255);
+  if (cudaHostAlloc(&b.p, want, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BCTS_ENOMEM, "pinned host allocation failed");
+  }
+  b.cap = want;
+  return BCTS_OK;
+}
+
+int64_t Ctx::chunk_nodes() const {
+  if (opt.leaf_chunk > 0) return opt.leaf_chunk;
+  return precision == BCTS_PREC_FP32_SIMT ? 16384 : 32768;
+}
+
+// Score `count` nodes: render + Q-network, chunked.  q (count x A) and maxq
+// (count) may each be NULL.
+int Ctx::eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st) {
+  const int64_t chunk = chunk_nodes();
+  int rc;
+  for (int64_t off = 0; off < count; off += chunk) {
+    const int64_t cnt = count - off < chunk ? count - off : chunk;
+    if ((rc = qnet_nodes(states + off, nullptr, cnt, q ? q + off * A : nullptr, maxq ? maxq + off : nullptr,
+                         st)) != BCTS_OK)
+      return rc;
+  }
+  return BCTS_OK;
+}
+
+// Q-network on at most one chunk of nodes, given either states (rendered here)
+// or frames.
+int Ctx::qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
+                    cudaStream_t st) {
+  int rc;
+  if (precision == BCTS_PREC_FP32_SIMT) {
+    if (states) {
+      if ((rc = ensure(frames_buf, size_t(cnt) * kFrameBytes)) != BCTS_OK) return rc;
+      if ((rc = launch_render(states, cnt, static_cast<uint8_t *>(frames_buf.p), st)) != BCTS_OK)
+        return fail(rc, "render launch failed");
+      frames = static_cast<const uint8_t *>(frames_buf.p);
+    }
+    if ((rc = ensure(scratch_buf, simt_scratch_bytes(cnt))) != BCTS_OK) return rc;
+    SimtWeights w = simt;
+    w.A = A;  // FC2 rows 0..A-1
+    if ((rc = simt_qnet_forward(w, frames, cnt, q, maxq, scratch_buf.p, st)) != BCTS_OK)
+      return fail(rc, "Q-network launch failed");
+    return BCTS_OK;
+  }
+  if (states && !tc_fused_render) {
+    if ((rc = ensure(frames_buf, size_t(cnt) * kFrameBytes)) != BCTS_OK) return rc;
+    if ((rc = launch_render(states, cnt, static_cast<uint8_t *>(frames_buf.p), st)) != BCTS_OK)
+      return fail(rc, "render launch failed");
+    frames = static_cast<const uint8_t *>(frames_buf.p);
+    states = nullptr;
+  }
+  if ((rc = ensure(scratch_buf, tc_scratch_bytes(cnt, precision))) != BCTS_OK) return rc;
+  rc = tc_qnet_forward(tc, A, frames, states, cnt, q, maxq, scratch_buf.p, st, d_err);
+  if (rc != BCTS_OK) return fail(rc, "tensor-core Q-network launch failed");
+  return BCTS_OK;
+}
+
+// Alg. 1 for n roots sharing (A_, d_): level-synchronous expansion, root and
+// depth-1 evaluation for the Bellman errors, leaf scoring, backup.
+int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d_action, float *d_values,
+                    int A_stride, cudaStream_t st) {
+  if (n <= 0) return BCTS_OK;
+  ProfilerGuard pg(prof);
+  std::vector<int64_t> N(d_ + 1);
+  N[0] = n;
+  for (int i = 1; i <= d_; ++i) N[i] = N[i - 1] * A_;
+  if (N[d_] > 0x7FFFFFFFLL) return fail(BCTS_EINVAL, "tree too large: n * A^d exceeds 2^31 - 1");
+  const int saved_A = A;
+  A = A_;  // eval_nodes writes q rows of A_ entries
+  int rc = BCTS_OK;
+  const size_t lvl_bytes = size_t(d_ >= 1 ? N[d_] : 1) * kStateBytes;
+  const size_t r_bytes = size_t(d_ >= 1 ? N[d_] : 1) * sizeof(float);
+  do {
+    if ((rc = ensure(q0_buf, size_t(n) * A_ * sizeof(float))) != BCTS_OK) break;
+    if ((rc = ensure(maxq1_buf, size_t(n) * A_ * sizeof(float))) != BCTS_OK) break;
+    if ((rc = ensure(V_buf, size_t(n) * A_ * sizeof(float))) != BCTS_OK) break;
+    float *q0 = static_cast<float *>(q0_buf.p);
+    float *maxq1 = static_cast<float *>(maxq1_buf.p);
+    float *V = static_cast<float *>(V_buf.p);
+    // a1: root evaluation, pi_o
+    if ((rc = eval_nodes(d_roots, n, q0, nullptr, st)) != BCTS_OK) break;
+    if (d_ == 0) {
+      rc = launch_finalize(q0, nullptr, nullptr, nullptr, n, A_, 0, A_stride, gamma, 1.f, corr, d_action,
+                           d_values, st);
+      break;
+    }
+    for (int b = 0; b < 2; ++b) {
+      if ((rc = ensure(lvl_buf[b], lvl_bytes)) != BCTS_OK) break;
+      if ((rc = ensure(R_buf[b], r_bytes)) != BCTS_OK) break;
+    }
+    if (rc != BCTS_OK) break;
+    if ((rc = ensure(r1_buf, size_t(n) * A_ * sizeof(float))) != BCTS_OK) break;
+    // a2 at depth 0 -> 1; R_1 = r(s_0, a) (kept for the Bellman errors)
+    bcts_state *L1 = static_cast<bcts_state *>(lvl_buf[1].p);
+    float *r1 = static_cast<float *>(r1_buf.p);
+    if ((rc = launch_expand(d_roots, nullptr, n, A_, 1.f, L1, r1, nullptr, st)) != BCTS_OK) {
+      rc = fail(rc, "expand launch failed");
+      break;
+    }
+    // a3: depth-1 evaluation (for d = 1 these are the leaves)
+    if ((rc = eval_nodes(L1, N[1], nullptr, maxq1, st)) != BCTS_OK) break;
+    const float *leafR = r1;
+    const float *leafMax = maxq1;
+    if (d_ >= 2) {
+      // a2 for depths 1 .. d-1 (ping-pong level buffers; level 1 lives in buffer 1)
+      const bcts_state *cur = L1;
+      const float *curR = r1;
+      double gp = 1.0;
+      for (int i = 1; i < d_; ++i) {
+        gp *= double(gamma);
+        bcts_state *nxt = static_cast<bcts_state *>(lvl_buf[(i + 1) & 1].p);
+        float *nxtR = static_cast<float *>(R_buf[(i + 1) & 1].p);
+        if ((rc = launch_expand(cur, curR, N[i], A_, float(gp), nxt, nxtR, nullptr, st)) != BCTS_OK) {
+          rc = fail(rc, "expand launch failed");
+          break;
+        }
+        cur = nxt;
+        curR = nxtR;
+      }
+      if (rc != BCTS_OK) break;
+      // a4 + a5: leaf render and Q-network, max over actions
+      if ((rc = ensure(leafmax_buf, size_t(N[d_]) * sizeof(float))) != BCTS_OK) break;
+      if ((rc = eval_nodes(cur, N[d_], nullptr, static_cast<float *>(leafmax_buf.p), st)) != BCTS_OK) break;
+      leafR = curR;
+      leafMax = static_cast<float *>(leafmax_buf.p);
+    }
+    // a6: backup
+    double gd = 1.0;
+    for (int i = 0; i < d_; ++i) gd *= double(gamma);
+    int64_t seg = 1;
+    for (int i = 1; i < d_; ++i) seg *= A_;
+    if ((rc = launch_segment_max(leafR, leafMax, int64_t(n) * A_, seg, float(gd), V, st)) != BCTS_OK) {
+      rc = fail(rc, "backup launch failed");
+      break;
+    }
+    if ((rc = launch_finalize(q0, maxq1, r1, V, n, A_, d_, A_stride, gamma, float(gd), corr, d_action, d_values,
+                              st)) != BCTS_OK) {
+      rc = fail(rc, "finalize launch failed");
+      break;
+    }
+  } while (0);
+  A = saved_A;
+  return rc;
+}
+
+Ctx::~Ctx() {
+  if (stream) cudaStreamSynchronize(stream);
+  DevBuf *bufs[] = {&frames_buf, &scratch_buf, &q0_buf, &maxq1_buf, &V_buf, &r1_buf, &leafmax_buf,
+                    &lvl_buf[0], &lvl_buf[1], &R_buf[0], &R_buf[1], &io_roots, &io_action, &io_values,
+                    &simt_w, &mixed_buf};
+  for (DevBuf *b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (host_stage.p) cudaFreeHost(host_stage.p);
+  if (d_err) cudaFree(d_err);
+  if (tc) tc_weights_destroy(tc);
+  if (prof) profiler_destroy(prof);
+  if (stream) cudaStreamDestroy(stream);
+}
+
+}  // namespace bcts
+
+using bcts::Ctx;
+
+extern "C" size_t bcts_qnet_numel(int A) {
+  if (A < 1) return 0;
+  return size_t(32) * 256 + 32 + size_t(64) * 512 + 64 + size_t(64) * 576 + 64 + size_t(512) * 3136 + 512 +
+         size_t(A) * 512 + A;
+}
+
+extern "C" int bcts_create(const bcts_env_desc *env, const float *w, int A, int d, float gamma, float correction,
+                           const bcts_options *opt, bcts_ctx **out) {
+  using namespace bcts;
+  if (!out || !w || A < 1 || A > kMaxA || d < 0 || d > kMaxDepth || !(gamma > 0.f && gamma <= 1.f) ||
+      !std::isfinite(correction) || (env && env->kind != 0)) {
+    set_thread_error("bcts_create: invalid argument");
+    return BCTS_EINVAL;
+  }
+  *out = nullptr;
+  Ctx *c = new Ctx();
+  c->prof = profiler_create();
+  c->A = c->A_create = A;
+  c->d = d;
+  c->gamma = gamma;
+  c->corr = correction;
+  if (opt) c->opt = *opt;
+  c->precision = c->opt.precision;
+  if (c->precision < BCTS_PREC_FP32 || c->precision > BCTS_PREC_FP32_SIMT) {
+    delete c;
+    set_thread_error("bcts_create: unknown precision");
+    return BCTS_EINVAL;
+  }
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    set_thread_error("bcts_create: no usable CUDA device");
+    return BCTS_ECUDA;
+  }
+  if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    set_thread_error("bcts_create: device allocation failed");
+    return BCTS_ENOMEM;
+  }
+  // Plain FP32 weights in the CUDA-core kernels' layouts.
+  const size_t nw = bcts_qnet_numel(A);
+  std::vector<float> hw(nw);
+  const float *c1w = w, *c1b = c1w + 32 * 256, *c2w = c1b + 32, *c2b = c2w + 64 * 512, *c3w = c2b + 64,
+              *c3b = c3w + 64 * 576, *f1w = c3b + 64, *f1b = f1w + size_t(512) * 3136, *f2w = f1b + 512,
+              *f2b = f2w + size_t(A) * 512;
+  float *o = hw.data();
+  for (int i = 0; i < 32 * 256; ++i) o[i] = float(double(c1w[i]) / 255.0);
+  o += 32 * 256;
+  std::memcpy(o, c1b, 32 * sizeof(float));
+  o += 32;
+  for (int oc = 0; oc < 64; ++oc)
+    for (int c = 0; c < 32; ++c)
+      for (int ky = 0; ky < 4; ++ky)
+        for (int kx = 0; kx < 4; ++kx) o[oc * 512 + (ky * 4 + kx) * 32 + c] = c2w[((oc * 32 + c) * 4 + ky) * 4 + kx];
+  o += 64 * 512;
+  std::memcpy(o, c2b, 64 * sizeof(float));
+  o += 64;
+  for (int oc = 0; oc < 64; ++oc)
+    for (int c = 0; c < 64; ++c)
+      for (int ky = 0; ky < 3; ++ky)
+        for (int kx = 0; kx < 3; ++kx) o[oc * 576 + (ky * 3 + kx) * 64 + c] = c3w[((oc * 64 + c) * 3 + ky) * 3 + kx];
+  o += 64 * 576;
+  std::memcpy(o, c3b, 64 * sizeof(float));
+  o += 64;
+  for (int oc = 0; oc < 512; ++oc)
+    for (int c = 0; c < 64; ++c)
+      for (int p = 0; p < 49; ++p) o[size_t(oc) * 3136 + p * 64 + c] = f1w[size_t(oc) * 3136 + c * 49 + p];
+  o += size_t(512) * 3136;
+  std::memcpy(o, f1b, 512 * sizeof(float));
+  o += 512;
+  std::memcpy(o, f2w, size_t(A) * 512 * sizeof(float));
+  o += size_t(A) * 512;
+  std::memcpy(o, f2b, A * sizeof(float));
+  if (c->ensure(c->simt_w, nw * sizeof(float)) != BCTS_OK ||
+      cudaMemcpy(c->simt_w.p, hw.data(), nw * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    set_thread_error("bcts_create: weight upload failed");
+    return BCTS_ENOMEM;
+  }
+  const float *b = static_cast<const float *>(c->simt_w.p);
+  c->simt.c1w = b;
+  c->simt.c1b = b + 32 * 256;
+  c->simt.c2w = c->simt.c1b + 32;
+  c->simt.c2b = c->simt.c2w + 64 * 512;
+  c->simt.c3w = c->simt.c2b + 64;
+  c->simt.c3b = c->simt.c3w + 64 * 576;
+  c->simt.f1w = c->simt.c3b + 64;
+  c->simt.f1b = c->simt.f1w + size_t(512) * 3136;
+  c->simt.f2w = c->simt.f1b + 512;
+  c->simt.f2b = c->simt.f2w + size_t(A) * 512;
+  c->simt.A = A;
+  if (c->precision != BCTS_PREC_FP32_SIMT) {
+    std::string e;
+    const int rc = tc_weights_create(w, A, c->precision, &c->tc, e);
+    if (rc != BCTS_OK) {
+      delete c;
+      set_thread_error("bcts_create: " + e);
+      return rc;
+    }
+  }
+  *out = reinterpret_cast<bcts_ctx *>(c);
+  return BCTS_OK;
+}
+
+extern "C" void bcts_destroy(bcts_ctx *ctx) {
+  if (!ctx) return;
+  bcts::serve_shutdown(reinterpret_cast<Ctx *>(ctx));
+  delete reinterpret_cast<Ctx *>(ctx);
+}
+
+extern "C" const char *bcts_last_error(const bcts_ctx *ctx) {
+  if (!ctx) return bcts::thread_error();
+  return reinterpret_cast<const Ctx *>(ctx)->err.c_str();
+}
+
+extern "C" int bcts_search_device(bcts_ctx *ctx, const bcts_state *d_roots, int n, int32_t *d_action,
+                                  float *d_values, void *stream) {
+  if (!ctx) return BCTS_EINVAL;
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (n < 0 || (n > 0 && (!d_roots || !d_action || !d_values)))
+    return c->fail(BCTS_EINVAL, "bcts_search_device: invalid argument");
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  return c->run_search(d_roots, n, c->A_create, c->d, d_action, d_values, c->A_create, st);
+}
+
+extern "C" int bcts_search(bcts_ctx *ctx, const bcts_state *roots, int n, int32_t *out_action, float *out_values) {
+  if (!ctx) return BCTS_EINVAL;
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (n < 0 || (n > 0 && (!roots || !out_action || !out_values)))
+    return c->fail(BCTS_EINVAL, "bcts_search: invalid argument");
+  if (n == 0) return BCTS_OK;
+  return c->search_host(roots, n, nullptr, nullptr, out_action, out_values);
+}
+
+namespace bcts {
+
+// Host-pointer search: stage through pinned memory, run, copy back, check the
+// device error word, synchronise.  With depths/actions set, roots are grouped by
+// (A, d) (the batched form); otherwise all use the context's A and d.
+int Ctx::search_host(const bcts_state *roots, int n, const int32_t *depths, const int32_t *actions,
+                     int32_t *out_action, float *out_values) {
+  const int As = A_create;
+  int rc;
+  const size_t in_b = size_t(n) * kStateBytes, act_b = size_t(n) * 4, val_b = size_t(n) * As * 4;
+  if ((rc = ensure(io_roots, in_b)) != BCTS_OK) return rc;
+  if ((rc = ensure(io_action, act_b)) != BCTS_OK) return rc;
+  if ((rc = ensure(io_values, val_b)) != BCTS_OK) return rc;
+  if ((rc = ensure_host(host_stage, in_b + act_b + val_b + 64)) != BCTS_OK) return rc;
+  char *hs = static_cast<char *>(host_stage.p);
+  std::memcpy(hs, roots, in_b);
+  BCTS_CUDA_TRY(cudaMemcpyAsync(io_roots.p, hs, in_b, cudaMemcpyHostToDevice, stream), err);
+  const bcts_state *dr = static_cast<const bcts_state *>(io_roots.p);
+  int32_t *da = static_cast<int32_t *>(io_action.p);
+  float *dv = static_cast<float *>(io_values.p);
+  if (!depths) {
+    rc = run_search(dr, n, As, d, da, dv, As, stream);
+  } else {
+    rc = run_mixed(dr, roots, depths, actions, n, da, dv);
+  }
+  if (rc != BCTS_OK) {
+    cudaStreamSynchronize(stream);
+    return rc;
+  }
+  int *herr = reinterpret_cast<int *>(hs + in_b + act_b + val_b);
+  BCTS_CUDA_TRY(cudaMemcpyAsync(hs + in_b, da, act_b, cudaMemcpyDeviceToHost, stream), err);
+  BCTS_CUDA_TRY(cudaMemcpyAsync(hs + in_b + act_b, dv, val_b, cudaMemcpyDeviceToHost, stream), err);
+  BCTS_CUDA_TRY(cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream), err);
+  BCTS_CUDA_TRY(cudaStreamSynchronize(stream), err);
+  if (*herr != 0) {
+    cudaMemsetAsync(d_err, 0, sizeof(int), stream);
+    cudaStreamSynchronize(stream);
+    return fail(BCTS_EDEVICE, "a kernel reported error code " + std::to_string(*herr));
+  }
+  std::memcpy(out_action, hs + in_b, act_b);
+  std::memcpy(out_values, hs + in_b + act_b, val_b);
+  return BCTS_OK;
+}
+
+}  // namespace bcts
+
+extern "C" int bcts_qnet(bcts_ctx *ctx, const uint8_t *d_frames, int64_t n, float *d_q, void *stream) {
+  if (!ctx) return BCTS_EINVAL;
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (n < 0 || (n > 0 && (!d_frames || !d_q))) return c->fail(BCTS_EINVAL, "bcts_qnet: invalid argument");
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  bcts::ProfilerGuard pg(c->prof);
+  const int64_t chunk = c->chunk_nodes();
+  for (int64_t off = 0; off < n; off += chunk) {
+    const int64_t cnt = n - off < chunk ? n - off : chunk;
+    const int rc =
+        c->qnet_nodes(nullptr, d_frames + off * bcts::kFrameBytes, cnt, d_q + off * c->A_create, nullptr, st);
+    if (rc != BCTS_OK) return rc;
+  }
+  return BCTS_OK;
+}

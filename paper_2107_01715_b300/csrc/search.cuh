@@ -1,0 +1,67 @@
+// search.cuh -- the search context shared by search.cu, mixed.cu and serve.cu.
+#pragma once
+
+#include <string>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bcts {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+struct HostBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+struct ServeState;  // serve.cu
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int A = 0;          // action count of the search being run
+  int A_create = 0;   // action count the context was created with (FC2 rows)
+  int d = 0;
+  float gamma = 0.99f;
+  float corr = 1.0f;
+  int precision = BCTS_PREC_FP32;
+  bcts_options opt{};
+  std::string err;
+
+  SimtWeights simt{};
+  TcWeights *tc = nullptr;
+  bool tc_fused_render = false;
+  int *d_err = nullptr;
+
+  DevBuf simt_w, frames_buf, scratch_buf, q0_buf, maxq1_buf, V_buf, r1_buf, leafmax_buf;
+  DevBuf lvl_buf[2], R_buf[2];
+  DevBuf io_roots, io_action, io_values, mixed_buf;
+  HostBuf host_stage;
+
+  ServeState *serve = nullptr;
+  Profiler *prof = nullptr;
+
+  ~Ctx();
+  int fail(int code, const std::string &msg);
+  int ensure(DevBuf &b, size_t bytes);
+  int ensure_host(HostBuf &b, size_t bytes);
+  int64_t chunk_nodes() const;
+  int eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st);
+  int qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
+                 cudaStream_t st);
+  int run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d_action, float *d_values,
+                 int A_stride, cudaStream_t st);
+  int run_mixed(const bcts_state *d_roots, const bcts_state *h_roots, const int32_t *depths,
+                const int32_t *actions, int n, int32_t *d_action, float *d_values);
+  int search_host(const bcts_state *roots, int n, const int32_t *depths, const int32_t *actions,
+                  int32_t *out_action, float *out_values);
+};
+
+void serve_shutdown(Ctx *c);
+Profiler *profiler_create();
+void profiler_destroy(Profiler *p);
+
+}  // namespace bcts

@@ -1,0 +1,38 @@
+"""Helpers shared by the GPU parity tests (no method arithmetic here)."""
+import numpy as np
+
+# Root values: |gpu - oracle| <= TOL * max(|oracle|, 1) per precision.
+# FP32-class paths hold 1e-4; BF16 / FP8 leaf Q-networks carry their operand
+# rounding (8 / 4 significant bits) through four layers.
+TOL = {"fp32_simt": 1e-4, "fp32": 1e-4, "bf16": 2e-2, "fp8": 8e-2}
+
+
+def value_close(gpu, ref, tol):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return np.abs(gpu - ref) <= tol * np.maximum(np.abs(ref), 1.0)
+
+
+def check_actions(gpu_actions, ref_values, tol):
+    """Where the oracle's top-2 margin exceeds the tolerance the action is unique
+    and must match; elsewhere the GPU's action must be within tolerance of the
+    oracle's best value.  Returns the number of roots with a unique action."""
+    ref_values = np.asarray(ref_values, dtype=np.float64)
+    unique = 0
+    for i, a in enumerate(np.asarray(gpu_actions)):
+        v = ref_values[i]
+        order = np.argsort(-v, kind="stable")
+        best = v[order[0]]
+        margin = best - v[order[1]] if v.size > 1 else np.inf
+        thr = 2 * tol * max(abs(best), 1.0)
+        if margin > thr:
+            unique += 1
+            assert a == order[0], (i, a, order[0], margin)
+        else:
+            assert best - v[a] <= thr, (i, a, best, v[a])
+    return unique
+
+
+def as_state_bytes(tensor_u8, n):
+    from paper_2107_01715_b300.inputs import STATE_DTYPE
+    return tensor_u8.cpu().numpy().view(STATE_DTYPE).reshape(n)

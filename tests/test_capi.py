@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library loads without a GPU, exports every
+symbol include/bcts.h declares, and rejects bad arguments before touching CUDA."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bcts.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"BCTS_API\s+[\w\s\*]*?\b(bcts_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def binding():
+    from paper_2107_01715_b300 import build
+    build.build()
+    from paper_2107_01715_b300 import bcts
+    return bcts
+
+
+def test_header_declares_entry_points():
+    syms = declared_symbols()
+    for s in ("bcts_create", "bcts_search", "bcts_submit", "bcts_poll", "bcts_destroy", "bcts_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(binding):
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (bcts_\w+)", out))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    for s in declared_symbols():
+        assert hasattr(binding.lib, s)
+    assert set(binding.EXPORTED) <= exported
+
+
+def test_library_does_not_need_a_driver_to_load(binding):
+    out = subprocess.run(["ldd", binding.LIB_PATH], capture_output=True, text=True).stdout
+    assert "libcuda.so" not in out  # driver API is reached through the runtime's entry-point query
+
+
+def test_qnet_numel(binding):
+    from paper_2107_01715_b300 import inputs
+    for A in (1, 6, 18):
+        assert binding.bcts_qnet_numel(A) == inputs.qnet_numel(A)
+    assert binding.bcts_qnet_numel(18) == 1693362
+
+
+def test_create_rejects_bad_arguments_without_cuda(binding):
+    lib = binding.lib
+    h = ctypes.c_void_p()
+    w = np.zeros(binding.bcts_qnet_numel(6), dtype=np.float32)
+    assert lib.bcts_create(None, None, 6, 2, 0.99, 1.0, None, ctypes.byref(h)) == binding.BCTS_EINVAL
+    assert lib.bcts_create(None, w.ctypes.data, 0, 2, 0.99, 1.0, None, ctypes.byref(h)) == binding.BCTS_EINVAL
+    assert lib.bcts_create(None, w.ctypes.data, 19, 2, 0.99, 1.0, None, ctypes.byref(h)) == binding.BCTS_EINVAL
+    assert lib.bcts_create(None, w.ctypes.data, 6, 7, 0.99, 1.0, None, ctypes.byref(h)) == binding.BCTS_EINVAL
+    assert lib.bcts_create(None, w.ctypes.data, 6, 2, 1.5, 1.0, None, ctypes.byref(h)) == binding.BCTS_EINVAL
+    assert lib.bcts_create(None, w.ctypes.data, 6, 2, 0.0, 1.0, None, ctypes.byref(h)) == binding.BCTS_EINVAL
+    assert b"invalid" in lib.bcts_last_error(None)
+    assert lib.bcts_expand(None, None, 4, 6, 1.0, None, None, None, None) == binding.BCTS_EINVAL
+    assert lib.bcts_render(None, 4, None, None) == binding.BCTS_EINVAL
+    assert lib.bcts_search(None, None, 0, None, None) == binding.BCTS_EINVAL
+    lib.bcts_destroy(None)  # no-op
+
+
+def test_binding_refuses_wrong_weight_count(binding):
+    with pytest.raises(ValueError):
+        binding.bcts_create(np.zeros(10, dtype=np.float32), 6, 2, 0.99, 1.0)

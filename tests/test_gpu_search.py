@@ -1,0 +1,125 @@
+"""GPU parity of the leaf Q-network and of the full search (Alg. 1 + Eq. 3/4/7)
+against the FP64 oracle, through the C ABI, per precision."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2107_01715_b300 import inputs
+from tests._util import TOL, check_actions, value_close
+
+pytestmark = pytest.mark.gpu
+
+PRECISIONS = [p for p in os.environ.get("BCTS_TEST_PRECISIONS", "fp32_simt,fp32,bf16,fp8").split(",") if p]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_01715_b300 import bcts
+    return torch, bcts
+
+
+def _ctx(bcts, A, d, gamma, c, precision, **kw):
+    W = inputs.qnet_weights(A, seed=1234)
+    try:
+        return bcts.bcts_create(W, A, d, gamma, c, precision=precision, **kw), W
+    except bcts.BctsError as e:
+        if e.code == bcts.BCTS_ENOKERNEL:
+            pytest.skip(f"{precision} path not available: {e}")
+        raise
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("n", [1, 37, 300])
+def test_qnet_matches_oracle(oracle_lib, dev, precision, n):
+    torch, bcts = dev
+    A = 18
+    ctx, W = _ctx(bcts, A, 1, 0.99, 1.0, precision)
+    states = inputs.root_states(range(n))
+    for i in range(n):
+        for a in (i % 18, (5 * i + 3) % 18, (7 * i) % 18):
+            states[i], _ = oracle_lib.env_step(states[i], a)
+    frames = np.stack([oracle_lib.render(s) for s in states])
+    ref = oracle_lib.qnet(frames, W, A)
+    dfr = torch.from_numpy(frames.reshape(-1)).cuda()
+    dq = torch.empty(n * A, dtype=torch.float32, device="cuda")
+    bcts.bcts_qnet(ctx, dfr, n, dq)
+    torch.cuda.synchronize()
+    q = dq.cpu().numpy().reshape(n, A)
+    ok = value_close(q, ref, TOL[precision])
+    assert ok.all(), (precision, np.abs(q - ref).max(), np.abs(ref).max())
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("A,d,n,c", [(6, 2, 1, 0.0), (6, 2, 1, 1.0), (6, 2, 5, 2.0), (4, 3, 3, 1.0),
+                                     (9, 1, 4, 1.0), (18, 0, 6, 1.0), (1, 2, 2, 1.0), (18, 2, 2, 0.5)])
+def test_search_matches_oracle(oracle_lib, dev, precision, A, d, n, c):
+    torch, bcts = dev
+    gamma = 0.99
+    ctx, W = _ctx(bcts, A, d, gamma, c, precision)
+    roots = inputs.root_states(range(n))
+    act, val = bcts.bcts_search(ctx, roots)
+    ref = oracle_lib.search(roots, W, A, d, float(np.float32(gamma)), c)
+    tol = TOL[precision]
+    ok = value_close(val, ref["values"], tol)
+    assert ok.all(), (np.abs(val - ref["values"]).max(), val, ref["values"])
+    check_actions(act, ref["values"], tol)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_search_ragged_chunks(oracle_lib, dev, precision):
+    """Leaf chunk smaller than the leaf count and not dividing it: 3 roots x 6^2
+    leaves = 108 leaves in chunks of 40."""
+    torch, bcts = dev
+    A, d, gamma, c = 6, 2, 0.99, 1.0
+    ctx, W = _ctx(bcts, A, d, gamma, c, precision, leaf_chunk=40)
+    roots = inputs.root_states(range(50, 53))
+    act, val = bcts.bcts_search(ctx, roots)
+    ref = oracle_lib.search(roots, W, A, d, float(np.float32(gamma)), c)
+    assert value_close(val, ref["values"], TOL[precision]).all()
+    check_actions(act, ref["values"], TOL[precision])
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_search_empty_and_device_entry(oracle_lib, dev, precision):
+    torch, bcts = dev
+    A, d = 6, 2
+    ctx, W = _ctx(bcts, A, d, 0.99, 1.0, precision)
+    act, val = bcts.bcts_search(ctx, inputs.root_states([]))
+    assert act.shape == (0,)
+    roots = inputs.root_states(range(3))
+    droots = torch.from_numpy(roots.view(np.uint8).copy()).cuda()
+    dact = torch.full((3,), -1, dtype=torch.int32, device="cuda")
+    dval = torch.zeros(3 * A, dtype=torch.float32, device="cuda")
+    bcts.bcts_search_device(ctx, droots, 3, dact, dval)
+    torch.cuda.synchronize()
+    h_act, h_val = bcts.bcts_search(ctx, roots)
+    assert np.array_equal(dact.cpu().numpy(), h_act)
+    assert np.array_equal(dval.cpu().numpy().reshape(3, A), h_val)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [p for p in PRECISIONS if p in ("fp32", "fp32_simt")])
+def test_atari_scale_sampled_roots(oracle_lib, dev, precision):
+    """The bench workload (32 roots, A = 18, d = 3, c = 1, FP32) in the bench's
+    launch configuration; three roots checked against the oracle."""
+    torch, bcts = dev
+    A, d, gamma, c = 18, 3, 0.99, 1.0
+    ctx, W = _ctx(bcts, A, d, gamma, c, precision)
+    roots = inputs.root_states(range(32))
+    act, val = bcts.bcts_search(ctx, roots)
+    sample = [0, 17, 31]
+    ref = oracle_lib.search(roots[sample], W, A, d, float(np.float32(gamma)), c)
+    tol = TOL[precision]
+    ok = value_close(val[sample], ref["values"], tol)
+    assert ok.all(), np.abs(val[sample] - ref["values"]).max()
+    check_actions(act[sample], ref["values"], tol)
+    # every root: actions are valid and values finite
+    assert np.isfinite(val).all() and ((act >= 0) & (act < A)).all()
+    ctx.close()
