@@ -204,6 +204,35 @@ BCTS_API int bcts_profile(bcts_ctx *ctx, int enable, double *out_ms, int64_t *ou
 /* Score n frame stacks with the context's Q-network in its precision: q [n][A] floats. */
 BCTS_API int bcts_qnet(bcts_ctx *ctx, const uint8_t *d_frames, int64_t n, float *d_q, void *stream);
 
+/* ---- allocation-free Q-network evaluation ------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory (code running inside an allocator or memory-pool
+ * callback, engines that reserve the whole device before loading this library,
+ * hosts that forbid cudaMalloc after start-up).  It needs no context.
+ *
+ * bcts_qnet_static scores n <= BCTS_STATIC_MAX_NODES frame stacks with the plain
+ * FP32 Q-network (the same kernels as a context created with
+ * BCTS_PREC_FP32_SIMT) and calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Its scratch -- the weights in the kernels' layout and the activation
+ * maps -- is one static device array of about 18 MB that every GPU loading the
+ * library holds until the process exits.
+ *   d_qnet_weights : device, bcts_qnet_numel(A) floats, PyTorch order (as in bcts_create)
+ *   A              : 1..18
+ *   d_frames       : device, uint8 [n][4][84][84]
+ *   n              : 0..BCTS_STATIC_MAX_NODES; larger n returns BCTS_EINVAL
+ *   d_q            : device, n * A floats
+ *   stream         : cudaStream_t as void*, NULL = legacy default stream
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call on a device shares the one array and leaves
+ * its contents behind; each call overwrites all of it that it reads, so nothing
+ * needs clearing, but calls whose execution overlaps on the GPU (different
+ * streams, or different host threads) race on the array and must be serialised
+ * by the caller.  Errors: BCTS_EINVAL, BCTS_ECUDA (message in bcts_last_error(NULL)). */
+#define BCTS_STATIC_MAX_NODES 128
+BCTS_API int bcts_qnet_static(const float *d_qnet_weights, int A, const uint8_t *d_frames, int64_t n, float *d_q,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

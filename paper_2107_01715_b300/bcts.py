@@ -31,7 +31,8 @@ PRECISIONS = {"fp32": BCTS_PREC_FP32, "bf16": BCTS_PREC_BF16, "fp8": BCTS_PREC_F
 
 EXPORTED = ["bcts_qnet_numel", "bcts_create", "bcts_destroy", "bcts_last_error", "bcts_search",
             "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll", "bcts_expand",
-            "bcts_render", "bcts_qnet", "bcts_profile"]
+            "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static"]
+BCTS_STATIC_MAX_NODES = 128
 KERNEL_CLASSES = ["expand", "render", "conv1", "conv2", "conv3", "fc1", "fc2", "backup"]
 
 
@@ -64,8 +65,9 @@ lib.bcts_expand.argtypes = [_P, _P, _I64, _I, ctypes.c_float, _P, _P, _P, _P]
 lib.bcts_render.argtypes = [_P, _I64, _P, _P]
 lib.bcts_qnet.argtypes = [_P, _P, _I64, _P, _P]
 lib.bcts_profile.argtypes = [_P, _I, _P, _P, _P]
+lib.bcts_qnet_static.argtypes = [_P, _I, _P, _I64, _P, _P]
 for _f in ("bcts_search", "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll",
-           "bcts_expand", "bcts_render", "bcts_qnet", "bcts_profile"):
+           "bcts_expand", "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static"):
     getattr(lib, _f).restype = _I
 
 
@@ -227,3 +229,8 @@ def bcts_profile(ctx: Context, enable: bool):
     tot = np.zeros(1, dtype=np.int64)
     _check(lib.bcts_profile(ctx.handle, 1 if enable else 0, ms.ctypes.data, cnt.ctypes.data, tot.ctypes.data), ctx)
     return dict(zip(KERNEL_CLASSES, ms.tolist())), dict(zip(KERNEL_CLASSES, cnt.tolist())), int(tot[0])
+
+
+def bcts_qnet_static(d_qnet_weights, A: int, d_frames, n: int, d_q, stream=None) -> int:
+    """Allocation-free Q-network on n <= BCTS_STATIC_MAX_NODES stacks (device pointers)."""
+    return _check(lib.bcts_qnet_static(_addr(d_qnet_weights), A, _addr(d_frames), n, _addr(d_q), _stream(stream)))
