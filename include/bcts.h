@@ -87,9 +87,15 @@ typedef struct bcts_options {
     int precision;              /* BCTS_PREC_* (default BCTS_PREC_FP32) */
     size_t frame_budget_bytes;  /* serving admission budget for in-flight leaf work (0 = 8 GiB) */
     int max_roots;              /* serving: requests fused per pass (0 = 64) */
-    int flags;                  /* reserved, 0 */
+    int flags;                  /* BCTS_FLAG_* bits, 0 = defaults */
     int leaf_chunk;             /* leaves rendered + scored per pass (0 = automatic) */
 } bcts_options;
+
+/* Option flags.  BCTS_FLAG_FRAMES: tensor-core precisions write every node's
+ * frame stack to device memory and read it back in conv1 (by default conv1
+ * renders its operand tiles from the node states on the fly and the frames of
+ * the searched nodes never reach device memory). */
+#define BCTS_FLAG_FRAMES 1
 
 typedef struct bcts_ctx bcts_ctx;
 

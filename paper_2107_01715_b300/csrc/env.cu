@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "render.cuh"
 
 namespace bcts {
 
@@ -30,10 +31,6 @@ constexpr uint32_t pack_dirs(const int (&v)[9]) {
 }
 constexpr uint32_t kDXP = pack_dirs(kDX);
 constexpr uint32_t kDYP = pack_dirs(kDY);
-
-// Sprite masks (4x4, bit r*4+c) and palette of objects 0..3, packed.
-constexpr uint64_t kSprites = 0xF99F96696FF6FFFFull;  // agent block, diamond, X, ring
-constexpr uint32_t kPalette = 0x4080C0F0u;            // 240, 192, 128, 64
 
 union StateRegs {
   uint4 v[5];
@@ -144,29 +141,13 @@ __global__ void __launch_bounds__(256) render_kernel(const uint4 *__restrict__ s
     const uint32_t w0 = (j - h * kChunksPerSlot) * 4;  // first word in the slot
     const uint4 P = __ldg(states + st * 5 + h);        // pos[h][0..3][x,y], 16 bytes
     int ox[4], oy[4];
-    const uint32_t pw[4] = {P.x, P.y, P.z, P.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      ox[k] = int(int16_t(pw[k] & 0xFFFFu));
-      oy[k] = int(int16_t(pw[k] >> 16));
-    }
+    unpack_slot(P, ox, oy);
     uint32_t word[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const uint32_t w = w0 + i;
       const int y = int(w / kGrid), cx = int(w - uint32_t(y) * kGrid);
-      const int cy = y >> 2, sr = y & 3;
-      uint32_t v = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (ox[k] == cx && oy[k] == cy) {
-          const uint32_t bits = uint32_t(kSprites >> (16 * k + 4 * sr)) & 0xFu;
-          const uint32_t bytemask = ((bits * 0x00204081u) & 0x01010101u) * 0xFFu;
-          const uint32_t pal = ((kPalette >> (8 * k)) & 0xFFu) * 0x01010101u;
-          v = (v & ~bytemask) | (pal & bytemask);
-        }
-      }
-      word[i] = v;
+      word[i] = render_word(ox, oy, cx, y);
     }
     frames[q] = make_uint4(word[0], word[1], word[2], word[3]);
   }

@@ -28,6 +28,10 @@ size_t simt_scratch_bytes(int64_t chunk);
 int simt_qnet_forward(const SimtWeights &w, const uint8_t *frames, int64_t n, float *q, float *maxq,
                       void *scratch, cudaStream_t stream);
 
+// FC2 + max over actions on FP32 fc1 activations h [n][512] (one warp per node).
+int launch_fc2_max(const float *h, const float *W2, const float *b2, int A, int64_t n, float *q, float *maxq,
+                   cudaStream_t st);
+
 // qnet_tc.cu (tensor-core paths)
 struct TcWeights;  // defined in qnet_tc.cu
 size_t tc_scratch_bytes(int64_t chunk, int precision);

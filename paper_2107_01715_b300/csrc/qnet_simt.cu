@@ -199,9 +199,15 @@ int simt_qnet_forward(const SimtWeights &w, const uint8_t *frames, int64_t n, fl
   if ((rc = run_gemm<GeoConv2, 128, 64, 8, 4>(K_CONV2, a1, w.c2w, w.c2b, a2, n, st)) != BCTS_OK) return rc;
   if ((rc = run_gemm<GeoConv3, 128, 64, 8, 4>(K_CONV3, a2, w.c3w, w.c3b, a3, n, st)) != BCTS_OK) return rc;
   if ((rc = run_gemm<GeoFc1, 128, 64, 8, 4>(K_FC1, a3, w.f1w, w.f1b, a4, n, st)) != BCTS_OK) return rc;
+  return launch_fc2_max(a4, w.f2w, w.f2b, w.A, n, q, maxq, st);
+}
+
+int launch_fc2_max(const float *h, const float *W2, const float *b2, int A, int64_t n, float *q, float *maxq,
+                   cudaStream_t st) {
+  if (n <= 0) return BCTS_OK;
   const int warps = 8;
   ProfScope ps(K_FC2, st);
-  fc2_max_kernel<<<unsigned((n + warps - 1) / warps), warps * 32, 0, st>>>(a4, w.f2w, w.f2b, w.A, n, q, maxq);
+  fc2_max_kernel<<<unsigned((n + warps - 1) / warps), warps * 32, 0, st>>>(h, W2, b2, A, n, q, maxq);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 

@@ -1,27 +1,726 @@
-// qnet_tc.cu -- tensor-core (tcgen05) Q-network paths.
+// qnet_tc.cu -- the leaf Q-network (Nature-DQN) on B300's 5th-generation tensor
+// cores: tcgen05.mma with FP32 accumulators in tensor memory (TMEM).
+//
+// Every layer (conv1, conv2, conv3, fc1) is one persistent, warp-specialised
+// implicit GEMM  out[M][N] = relu(A[M][K] W[N][K]^T + b), M = nodes x output
+// pixels, K = Cin x kh x kw:
+//   warps 0-3  producers: gather the A tile (im2col rows of the NHWC activation
+//              map, or for conv1 the frame pixels -- read from the frame stacks
+//              or rendered on the fly from the node states) and the weight tile
+//              into 128-byte-swizzled shared memory (cp.async, or st.shared
+//              after the uint8 -> bf16 conversion), then signal a full barrier;
+//   warp 8     allocates TMEM and, from one lane, issues tcgen05.mma (M = 128,
+//              K = 16 per instruction) over the K blocks, committing each stage
+//              back to its producer barrier and each finished tile to the
+//              epilogue;
+//   warps 4-7  epilogue: tcgen05.ld the accumulator (one TMEM lane per thread),
+//              add bias, ReLU, round to bf16 (and, in the FP32-class mode, the
+//              bf16 remainder) and store NHWC; two accumulators alternate so the
+//              next tile's MMAs overlap this tile's epilogue.
+// Precision modes: BF16 (one MMA per K step) and FP32-class "split" mode, where
+// every operand x is carried as hi = bf16(x), lo = bf16(x - hi) and the product
+// is hi*hi + hi*lo + lo*hi (three MMAs; two for conv1, whose integer pixels are
+// exact in bf16), accumulated in FP32.  FC2 and the max over actions run in
+// FP32 on CUDA cores (9,216 MACs per node, 0.1 % of the network).
+//
+// Every wait is bounded: a wait that runs out sets the context's device error
+// word and an abort flag, every role leaves its loop, in-flight copies and MMAs
+// are drained and TMEM is freed before the kernel returns.
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.cuh"
+#include "render.cuh"
 
 namespace bcts {
+namespace tc {
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void st_shared16(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, 128-byte rows, 128-byte
+// swizzle, 8-row groups 1024 bytes apart (the tile base is 1024-byte aligned).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= uint64_t(1) << 16;                  // leading-dimension offset (unused for this layout)
+  d |= uint64_t(1024 >> 4) << 32;          // stride between 8-row groups
+  d |= uint64_t(1) << 46;                  // descriptor version
+  d |= uint64_t(2) << 61;                  // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: bf16 A and B, FP32 accumulator, both
+// K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+}
+
+// Byte offset of 16-byte chunk `ch` of row `r` in a 128-byte-swizzled tile.
+__device__ __forceinline__ uint32_t sw128_off(int r, int ch) {
+  return uint32_t(r) * 128u + (uint32_t(ch ^ (r & 7)) << 4);
+}
+
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
+
+// Bounded mbarrier wait.  On time-out: error code into the device error word,
+// abort flag for the whole CTA, returns false.
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *d_err,
+                                         int code) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  int spins = 0;
+  while (!mbar_try(bar, parity)) {
+    if (*abort_flag) return false;
+    if (++spins > 16) __nanosleep(64);
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      if (d_err) atomicCAS(d_err, 0, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Layer geometry
+// ---------------------------------------------------------------------------
+// LAYER 1: conv1 32@8x8/4, K = c*64 + ky*8 + kx (the PyTorch order), one K block
+//          per input channel; A from uint8 frames or rendered from states.
+// LAYER 2: conv2 64@4x4/2 on [20][20][32], K = (ky*4 + kx)*32 + c.
+// LAYER 3: conv3 64@3x3/1 on [9][9][64],  K = (ky*3 + kx)*64 + c.
+// LAYER 4: fc1 512 on the NHWC-flattened [7][7][64] map, N tiled by 256.
+template <int LAYER>
+struct Geo;
+template <>
+struct Geo<1> {
+  static constexpr int BN = 32, KB = 4, P = 400, NTOT = 32, K = 256;
+};
+template <>
+struct Geo<2> {
+  static constexpr int BN = 64, KB = 8, P = 81, NTOT = 64, K = 512;
+};
+template <>
+struct Geo<3> {
+  static constexpr int BN = 64, KB = 9, P = 49, NTOT = 64, K = 576;
+};
+template <>
+struct Geo<4> {
+  static constexpr int BN = 256, KB = 49, P = 1, NTOT = 512, K = 3136;
+};
+
+template <int LAYER, bool SPLIT>
+struct Cfg {
+  using G = Geo<LAYER>;
+  static constexpr bool A_LO = SPLIT && LAYER != 1;  // conv1's integer pixels are exact in bf16
+  static constexpr int A_BYTES = 128 * 128;
+  static constexpr int B_BYTES = G::BN * 128;
+  static constexpr int STAGE_BYTES = A_BYTES * (A_LO ? 2 : 1) + B_BYTES * (SPLIT ? 2 : 1);
+  static constexpr int STAGES_RAW = (192 * 1024) / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr uint32_t TMEM_COLS = 2 * G::BN < 32 ? 32 : 2 * G::BN;
+  static_assert(STAGES >= 2, "pipeline depth");
+  static_assert(SMEM <= 232448, "shared memory");
+};
+
+struct GemmParams {
+  const void *a_hi;  // bf16 activations, uint8 frames or node states
+  const void *a_lo;  // bf16 activation remainders (split mode, layers 2-4)
+  const __nv_bfloat16 *b_hi;
+  const __nv_bfloat16 *b_lo;
+  const float *bias;
+  void *out_hi;  // bf16 NHWC (layers 1-3) or FP32 [M][512] (layer 4)
+  void *out_lo;  // bf16 remainders (split mode, layers 1-3)
+  long long M;
+  int num_tiles;
+  int *d_err;
+};
+
+constexpr int kThreads = 288;  // 9 warps
+
+template <int LAYER, bool SPLIT, bool FUSED>
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
+  using C = Cfg<LAYER, SPLIT>;
+  using G = Geo<LAYER>;
+  constexpr int BN = G::BN, KB = G::KB, S = C::STAGES;
+  constexpr int NT = G::NTOT / BN;  // N tiles per M tile
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t *gbase = smem_raw + (base - raw);
+  // barriers and bookkeeping after the stages
+  const uint32_t bar0 = base + S * C::STAGE_BYTES;
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * S + a); };
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * S + 2 + a); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * S + 4);
+  uint8_t *meta = gbase + S * C::STAGE_BYTES + 8 * (2 * S + 5);
+  volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(meta);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(meta + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full_bar(s), 128);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 4);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) tmem_alloc(smem_u32((const void *)tmem_slot), C::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp < 4) {
+    // ------------------------------------------------------------ producers
+    const int pt = threadIdx.x;  // 0..127
+    const int ch = pt & 7, r0 = pt >> 3;
+    int g = 0, pending = -1;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+      const long long m0 = (long long)(t / NT) * 128;
+      const int n0 = (t % NT) * BN;
+      // per-row source offsets for this tile (rows r0 + 16 i)
+      long long rowoff[8];
+      int rowx[8], rowy[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        long long m = m0 + r0 + 16 * i;
+        if (m > p.M - 1) m = p.M - 1;
+        const long long leaf = m / G::P;
+        const int px = int(m - leaf * G::P);
+        if (LAYER == 1) {
+          const int oy = px / 20, ox = px - oy * 20;
+          rowx[i] = ox;
+          rowy[i] = oy;
+          rowoff[i] = FUSED ? leaf : leaf * kFrameBytes + (4 * oy) * 84 + 4 * ox;
+        } else if (LAYER == 2) {
+          const int oy = px / 9, ox = px - oy * 9;
+          rowoff[i] = leaf * (kP1 * kC1) + (2 * oy * 20 + 2 * ox) * kC1;
+        } else if (LAYER == 3) {
+          const int oy = px / 7, ox = px - oy * 7;
+          rowoff[i] = leaf * (kP2 * kC2) + (oy * 9 + ox) * kC2;
+        } else {
+          rowoff[i] = m * kKF;
+        }
+      }
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = g % S;
+        const uint32_t round = uint32_t(g / S);
+        if (!wait_bar(empty_bar(s), (round & 1u) ^ 1u, abort_flag, p.d_err, 1)) {
+          ok = false;
+          break;
+        }
+        const uint32_t sA = base + s * C::STAGE_BYTES;
+        const uint32_t sAlo = sA + C::A_BYTES;
+        const uint32_t sB = sA + C::A_BYTES * (C::A_LO ? 2 : 1);
+        const uint32_t sBlo = sB + C::B_BYTES;
+        // A tile
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int r = r0 + 16 * i;
+          const uint32_t off = sw128_off(r, ch);
+          if (LAYER == 1) {
+            uint32_t w0, w1;
+            if (FUSED) {
+              const uint4 P = __ldg(reinterpret_cast<const uint4 *>(p.a_hi) + rowoff[i] * 5 + kb);
+              int ox[4], oy[4];
+              unpack_slot(P, ox, oy);
+              const int y = 4 * rowy[i] + ch;
+              w0 = render_word(ox, oy, rowx[i], y);
+              w1 = render_word(ox, oy, rowx[i] + 1, y);
+            } else {
+              const uint8_t *src = static_cast<const uint8_t *>(p.a_hi) + rowoff[i] + kb * 7056 + ch * 84;
+              w0 = __ldg(reinterpret_cast<const uint32_t *>(src));
+              w1 = __ldg(reinterpret_cast<const uint32_t *>(src + 4));
+            }
+            // 8 pixels -> 8 bf16 (integers below 256 are exact in bf16)
+            uint32_t o[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const uint32_t wsrc = h < 2 ? w0 : w1;
+              const uint32_t b0 = (wsrc >> (16 * (h & 1))) & 0xFFu;
+              const uint32_t b1 = (wsrc >> (16 * (h & 1) + 8)) & 0xFFu;
+              o[h] = (__float_as_uint(float(b0)) >> 16) | (__float_as_uint(float(b1)) & 0xFFFF0000u);
+            }
+            st_shared16(sA + off, make_uint4(o[0], o[1], o[2], o[3]));
+          } else {
+            long long e;
+            if (LAYER == 2) {
+              const int pos = 2 * kb + (ch >> 2), ky = pos >> 2, kx = pos & 3;
+              e = rowoff[i] + (ky * 20 + kx) * kC1 + (ch & 3) * 8;
+            } else if (LAYER == 3) {
+              const int ky = kb / 3, kx = kb - 3 * (kb / 3);
+              e = rowoff[i] + (ky * 9 + kx) * kC2 + ch * 8;
+            } else {
+              e = rowoff[i] + kb * 64 + ch * 8;
+            }
+            cp_async16(sA + off, static_cast<const __nv_bfloat16 *>(p.a_hi) + e);
+            if (C::A_LO) cp_async16(sAlo + off, static_cast<const __nv_bfloat16 *>(p.a_lo) + e);
+          }
+        }
+        // B tile (weights, [NTOT][K] K-major)
+#pragma unroll
+        for (int i = 0; i < BN / 16; ++i) {
+          const int r = r0 + 16 * i;
+          const uint32_t off = sw128_off(r, ch);
+          const long long e = (long long)(n0 + r) * G::K + kb * 64 + ch * 8;
+          cp_async16(sB + off, p.b_hi + e);
+          if (SPLIT) cp_async16(sBlo + off, p.b_lo + e);
+        }
+        cp_commit();
+        if (pending >= 0) {
+          cp_wait<1>();
+          fence_proxy_async();
+          mbar_arrive(full_bar(pending));
+        }
+        pending = s;
+        ++g;
+      }
+    }
+    cp_wait<0>();
+    fence_proxy_async();
+    if (pending >= 0) mbar_arrive(full_bar(pending));
+  } else if (warp == 8) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(BN);
+      int g = 0, it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x, ++it) {
+        const int acc = it & 1;
+        if (!wait_bar(tempty_bar(acc), (uint32_t((it >> 1) & 1)) ^ 1u, abort_flag, p.d_err, 2)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + uint32_t(acc * BN);
+        for (int kb = 0; kb < KB; ++kb) {
+          const int s = g % S;
+          const uint32_t round = uint32_t(g / S);
+          if (!wait_bar(full_bar(s), round & 1u, abort_flag, p.d_err, 3)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sA = base + s * C::STAGE_BYTES;
+          const uint32_t sAlo = sA + C::A_BYTES;
+          const uint32_t sB = sA + C::A_BYTES * (C::A_LO ? 2 : 1);
+          const uint32_t sBlo = sB + C::B_BYTES;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {  // K = 16 bf16 = 32 bytes per instruction
+            const uint32_t first = (kb | j) != 0;
+            const uint64_t a = sw128_desc(sA) + uint64_t(2 * j);
+            const uint64_t b = sw128_desc(sB) + uint64_t(2 * j);
+            mma_bf16(d, a, b, idesc, first);
+            if (SPLIT) {
+              mma_bf16(d, a, sw128_desc(sBlo) + uint64_t(2 * j), idesc, 1u);
+              if (C::A_LO) mma_bf16(d, sw128_desc(sAlo) + uint64_t(2 * j), b, idesc, 1u);
+            }
+          }
+          mma_commit(empty_bar(s));  // stage free once these MMAs have read it
+          ++g;
+        }
+        if (!ok) break;
+        mma_commit(tfull_bar(acc));
+      }
+      // drain: this commit completes once every MMA issued above has finished
+      // (also after an abort), so TMEM and shared memory can be released
+      mma_commit(drain_bar);
+      const long long t0 = clock64();
+      while (!mbar_try(drain_bar, 0)) {
+        __nanosleep(64);
+        if (clock64() - t0 > kWaitCycles) {
+          if (p.d_err) atomicCAS(p.d_err, 0, 5);
+          break;
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int it = 0;
+    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++it) {
+      const int acc = it & 1;
+      if (!wait_bar(tfull_bar(acc), uint32_t((it >> 1) & 1), abort_flag, p.d_err, 4)) break;
+      tc_fence_after();
+      const long long m = (long long)(t / NT) * 128 + row;
+      const int n0 = (t % NT) * BN;
+      const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * BN);
+#pragma unroll 1
+      for (int j = 0; j < BN / 16; ++j) {
+        uint32_t r[16];
+        tmem_ld16(tbase + uint32_t(j * 16), r);
+        tmem_wait_ld();
+        float v[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const float x = __uint_as_float(r[e]) + __ldg(p.bias + n0 + j * 16 + e);
+          v[e] = x > 0.f ? x : 0.f;
+        }
+        if (m < p.M) {
+          if (LAYER == 4) {
+            float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(p.out_hi) + m * G::NTOT + n0 + j * 16);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+          } else {
+            uint32_t hi[8], lo[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]), h1 = __float2bfloat16_rn(v[2 * e + 1]);
+              hi[e] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
+              if (SPLIT) {
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
+                lo[e] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+              }
+            }
+            const long long o = m * G::NTOT + n0 + j * 16;
+            uint4 *dh = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(p.out_hi) + o);
+            dh[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            dh[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+            if (SPLIT) {
+              uint4 *dl = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(p.out_lo) + o);
+              dl[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+              dl[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(acc));
+    }
+  }
+  // teardown: every role has left its loop (all waits are bounded)
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 8) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+int num_sms() {
+  static int sms = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
+  });
+  return sms;
+}
+
+template <int LAYER, bool SPLIT, bool FUSED>
+int launch(const GemmParams &p0, long long M, int kind, cudaStream_t st) {
+  using C = Cfg<LAYER, SPLIT>;
+  if (M <= 0) return BCTS_OK;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(tc_gemm<LAYER, SPLIT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    C::SMEM);
+  });
+  if (attr_err != cudaSuccess) return BCTS_ECUDA;
+  GemmParams p = p0;
+  p.M = M;
+  const long long mt = (M + 127) / 128;
+  const long long tiles = mt * (Geo<LAYER>::NTOT / Geo<LAYER>::BN);
+  if (tiles > 0x7FFFFFFFLL) return BCTS_EINVAL;
+  p.num_tiles = int(tiles);
+  const int grid = int(tiles < num_sms() ? tiles : num_sms());
+  ProfScope ps(kind, st);
+  tc_gemm<LAYER, SPLIT, FUSED><<<grid, kThreads, C::SMEM, st>>>(p);
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
+
+uint16_t f2bf(float f) {  // round to nearest even
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7FFFFFFFu) > 0x7F800000u) return 0x7FC0;
+  const uint32_t r = 0x7FFFu + ((u >> 16) & 1u);
+  return uint16_t((u + r) >> 16);
+}
+float bf2f(uint16_t h) {
+  const uint32_t u = uint32_t(h) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+}  // namespace tc
 
 struct TcWeights {
   int A = 0;
   int precision = 0;
+  void *blob = nullptr;
+  const __nv_bfloat16 *w_hi[4] = {};  // conv1, conv2, conv3, fc1
+  const __nv_bfloat16 *w_lo[4] = {};
+  const float *bias[4] = {};
+  const float *f2w = nullptr, *f2b = nullptr;
 };
 
-size_t tc_scratch_bytes(int64_t, int) { return 256; }
+namespace {
+constexpr int kWRows[4] = {32, 64, 64, 512};
+constexpr int kWK[4] = {256, 512, 576, 3136};
 
-int tc_weights_create(const float *, int, int, TcWeights **out, std::string &err) {
-  *out = nullptr;
-  err = "tensor-core Q-network not built yet";
-  return BCTS_ENOKERNEL;
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+}  // namespace
+
+size_t tc_scratch_bytes(int64_t chunk, int precision) {
+  const size_t lo = precision == BCTS_PREC_FP32 ? 2 : 1;
+  return lo * (align256(size_t(chunk) * kP1 * kC1 * 2) + align256(size_t(chunk) * kP2 * kC2 * 2) +
+               align256(size_t(chunk) * kP3 * kC3 * 2)) +
+         align256(size_t(chunk) * kF1 * 4) + 4096;
 }
 
-void tc_weights_destroy(TcWeights *w) { delete w; }
+// `w` holds the weights in the CUDA-core layouts (conv1 pre-scaled by 1/255,
+// conv2/conv3 K = (ky, kx, c), fc1 columns NHWC); the same orders serve here.
+int tc_weights_create(const float *w, int A, int precision, TcWeights **out, std::string &err) {
+  *out = nullptr;
+  if (precision != BCTS_PREC_FP32 && precision != BCTS_PREC_BF16) {
+    err = "precision not available on the tensor-core path";
+    return BCTS_ENOKERNEL;
+  }
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3) {
+    cudaGetLastError();
+    err = "tensor-core Q-network needs an sm_103 (B300) device";
+    return BCTS_ENOKERNEL;
+  }
+  const float *src[4];
+  const float *bsrc[4];
+  src[0] = w;
+  bsrc[0] = src[0] + 32 * 256;
+  src[1] = bsrc[0] + 32;
+  bsrc[1] = src[1] + 64 * 512;
+  src[2] = bsrc[1] + 64;
+  bsrc[2] = src[2] + 64 * 576;
+  src[3] = bsrc[2] + 64;
+  bsrc[3] = src[3] + size_t(512) * 3136;
+  const float *f2w = bsrc[3] + 512;
+  const float *f2b = f2w + size_t(A) * 512;
+  // blob: [hi, lo] bf16 per layer, then FP32 biases, fc2 weights and biases
+  std::vector<size_t> off;
+  size_t total = 0;
+  for (int l = 0; l < 4; ++l) {
+    off.push_back(total);
+    total += align256(size_t(kWRows[l]) * kWK[l] * 2);
+    off.push_back(total);
+    total += align256(size_t(kWRows[l]) * kWK[l] * 2);
+  }
+  for (int l = 0; l < 4; ++l) {
+    off.push_back(total);
+    total += align256(size_t(kWRows[l]) * 4);
+  }
+  const size_t off_f2w = total;
+  total += align256(size_t(A) * 512 * 4);
+  const size_t off_f2b = total;
+  total += align256(size_t(A) * 4);
+  std::vector<uint8_t> h(total, 0);
+  for (int l = 0; l < 4; ++l) {
+    uint16_t *hi = reinterpret_cast<uint16_t *>(h.data() + off[2 * l]);
+    uint16_t *lo = reinterpret_cast<uint16_t *>(h.data() + off[2 * l + 1]);
+    const size_t n = size_t(kWRows[l]) * kWK[l];
+    for (size_t i = 0; i < n; ++i) {
+      hi[i] = tc::f2bf(src[l][i]);
+      lo[i] = tc::f2bf(src[l][i] - tc::bf2f(hi[i]));
+    }
+    std::memcpy(h.data() + off[8 + l], bsrc[l], size_t(kWRows[l]) * 4);
+  }
+  std::memcpy(h.data() + off_f2w, f2w, size_t(A) * 512 * 4);
+  std::memcpy(h.data() + off_f2b, f2b, size_t(A) * 4);
+  TcWeights *t = new TcWeights();
+  t->A = A;
+  t->precision = precision;
+  if (cudaMalloc(&t->blob, total) != cudaSuccess ||
+      cudaMemcpy(t->blob, h.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    if (t->blob) cudaFree(t->blob);
+    delete t;
+    err = "tensor-core weight upload failed";
+    return BCTS_ENOMEM;
+  }
+  uint8_t *b = static_cast<uint8_t *>(t->blob);
+  for (int l = 0; l < 4; ++l) {
+    t->w_hi[l] = reinterpret_cast<const __nv_bfloat16 *>(b + off[2 * l]);
+    t->w_lo[l] = reinterpret_cast<const __nv_bfloat16 *>(b + off[2 * l + 1]);
+    t->bias[l] = reinterpret_cast<const float *>(b + off[8 + l]);
+  }
+  t->f2w = reinterpret_cast<const float *>(b + off_f2w);
+  t->f2b = reinterpret_cast<const float *>(b + off_f2b);
+  *out = t;
+  return BCTS_OK;
+}
 
-int tc_qnet_forward(const TcWeights *, int, const uint8_t *, const bcts_state *, int64_t, float *, float *, void *,
-                    cudaStream_t, int *) {
-  return BCTS_ENOKERNEL;
+void tc_weights_destroy(TcWeights *w) {
+  if (!w) return;
+  if (w->blob) cudaFree(w->blob);
+  delete w;
+}
+
+namespace {
+template <bool SPLIT>
+int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n,
+                    float *q, float *maxq, void *scratch, cudaStream_t st, int *d_err) {
+  const size_t lo = SPLIT ? 2 : 1;
+  uint8_t *s = static_cast<uint8_t *>(scratch);
+  auto take = [&](size_t bytes) {
+    uint8_t *r = s;
+    s += align256(bytes);
+    return r;
+  };
+  __nv_bfloat16 *a1 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP1 * kC1 * 2));
+  __nv_bfloat16 *a1l = SPLIT ? reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP1 * kC1 * 2)) : nullptr;
+  __nv_bfloat16 *a2 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP2 * kC2 * 2));
+  __nv_bfloat16 *a2l = SPLIT ? reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP2 * kC2 * 2)) : nullptr;
+  __nv_bfloat16 *a3 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP3 * kC3 * 2));
+  __nv_bfloat16 *a3l = SPLIT ? reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP3 * kC3 * 2)) : nullptr;
+  float *h = reinterpret_cast<float *>(take(size_t(n) * kF1 * 4));
+  (void)lo;
+  int rc;
+  tc::GemmParams p{};
+  p.d_err = d_err;
+  // conv1
+  p.a_hi = states ? static_cast<const void *>(states) : static_cast<const void *>(frames);
+  p.a_lo = nullptr;
+  p.b_hi = w->w_hi[0];
+  p.b_lo = w->w_lo[0];
+  p.bias = w->bias[0];
+  p.out_hi = a1;
+  p.out_lo = a1l;
+  rc = states ? tc::launch<1, SPLIT, true>(p, (long long)n * kP1, K_CONV1, st)
+              : tc::launch<1, SPLIT, false>(p, (long long)n * kP1, K_CONV1, st);
+  if (rc != BCTS_OK) return rc;
+  // conv2
+  p.a_hi = a1;
+  p.a_lo = a1l;
+  p.b_hi = w->w_hi[1];
+  p.b_lo = w->w_lo[1];
+  p.bias = w->bias[1];
+  p.out_hi = a2;
+  p.out_lo = a2l;
+  if ((rc = tc::launch<2, SPLIT, false>(p, (long long)n * kP2, K_CONV2, st)) != BCTS_OK) return rc;
+  // conv3
+  p.a_hi = a2;
+  p.a_lo = a2l;
+  p.b_hi = w->w_hi[2];
+  p.b_lo = w->w_lo[2];
+  p.bias = w->bias[2];
+  p.out_hi = a3;
+  p.out_lo = a3l;
+  if ((rc = tc::launch<3, SPLIT, false>(p, (long long)n * kP3, K_CONV3, st)) != BCTS_OK) return rc;
+  // fc1 (FP32 output for FC2)
+  p.a_hi = a3;
+  p.a_lo = a3l;
+  p.b_hi = w->w_hi[3];
+  p.b_lo = w->w_lo[3];
+  p.bias = w->bias[3];
+  p.out_hi = h;
+  p.out_lo = nullptr;
+  if ((rc = tc::launch<4, SPLIT, false>(p, (long long)n, K_FC1, st)) != BCTS_OK) return rc;
+  return launch_fc2_max(h, w->f2w, w->f2b, A, n, q, maxq, st);
+}
+}  // namespace
+
+int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
+                    float *maxq, void *scratch, cudaStream_t st, int *d_err) {
+  if (n <= 0) return BCTS_OK;
+  if (w->precision == BCTS_PREC_FP32)
+    return tc_forward_impl<true>(w, A, frames, states, n, q, maxq, scratch, st, d_err);
+  return tc_forward_impl<false>(w, A, frames, states, n, q, maxq, scratch, st, d_err);
 }
 
 }  // namespace bcts

@@ -339,6 +339,7 @@ extern "C" int bcts_create(const bcts_env_desc *env, const float *w, int A, int 
   c->corr = correction;
   if (opt) c->opt = *opt;
   c->precision = c->opt.precision;
+  c->tc_fused_render = (c->opt.flags & BCTS_FLAG_FRAMES) == 0;
   if (c->precision < BCTS_PREC_FP32 || c->precision > BCTS_PREC_FP32_SIMT) {
     delete c;
     set_thread_error("bcts_create: unknown precision");
@@ -412,7 +413,7 @@ extern "C" int bcts_create(const bcts_env_desc *env, const float *w, int A, int 
   c->simt.A = A;
   if (c->precision != BCTS_PREC_FP32_SIMT) {
     std::string e;
-    const int rc = tc_weights_create(w, A, c->precision, &c->tc, e);
+    const int rc = tc_weights_create(hw.data(), A, c->precision, &c->tc, e);
     if (rc != BCTS_OK) {
       delete c;
       set_thread_error("bcts_create: " + e);
