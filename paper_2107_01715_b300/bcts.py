@@ -33,6 +33,7 @@ EXPORTED = ["bcts_qnet_numel", "bcts_create", "bcts_destroy", "bcts_last_error",
             "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll", "bcts_expand",
             "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static"]
 BCTS_STATIC_MAX_NODES = 128
+BCTS_FLAG_FRAMES = 1
 KERNEL_CLASSES = ["expand", "render", "conv1", "conv2", "conv3", "fc1", "fc2", "backup"]
 
 
@@ -135,12 +136,12 @@ def bcts_qnet_numel(A: int) -> int:
 
 def bcts_create(qnet_weights: np.ndarray, A: int, d: int, gamma: float, correction: float,
                 precision="fp32", leaf_chunk: int = 0, frame_budget_bytes: int = 0, max_roots: int = 0,
-                env_kind: int = 0) -> Context:
+                env_kind: int = 0, flags: int = 0) -> Context:
     w = np.ascontiguousarray(qnet_weights, dtype=np.float32)
     if w.size != bcts_qnet_numel(A):
         raise ValueError(f"expected {bcts_qnet_numel(A)} weights for A={A}, got {w.size}")
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    opt = bcts_options(prec, frame_budget_bytes, max_roots, 0, leaf_chunk)
+    opt = bcts_options(prec, frame_budget_bytes, max_roots, flags, leaf_chunk)
     env = bcts_env_desc(env_kind)
     h = _P()
     rc = lib.bcts_create(ctypes.byref(env), w.ctypes.data, A, d, gamma, correction, ctypes.byref(opt),

@@ -4,19 +4,19 @@
 // Every layer (conv1, conv2, conv3, fc1) is one persistent, warp-specialised
 // implicit GEMM  out[M][N] = relu(A[M][K] W[N][K]^T + b), M = nodes x output
 // pixels, K = Cin x kh x kw:
-//   warps 0-3  producers: gather the A tile (im2col rows of the NHWC activation
+//   warps 0-7  producers: gather the A tile (im2col rows of the NHWC activation
 //              map, or for conv1 the frame pixels -- read from the frame stacks
 //              or rendered on the fly from the node states) and the weight tile
 //              into 128-byte-swizzled shared memory (cp.async, or st.shared
 //              after the uint8 -> bf16 conversion), then signal a full barrier;
-//   warp 8     allocates TMEM and, from one lane, issues tcgen05.mma (M = 128,
+//   warp 12    allocates TMEM and, from one lane, issues tcgen05.mma (M = 128,
 //              K = 16 per instruction) over the K blocks, committing each stage
 //              back to its producer barrier and each finished tile to the
 //              epilogue;
-//   warps 4-7  epilogue: tcgen05.ld the accumulator (one TMEM lane per thread),
+//   warps 8-11 epilogue: tcgen05.ld the accumulator (one TMEM lane per thread),
 //              add bias, ReLU, round to bf16 (and, in the FP32-class mode, the
-//              bf16 remainder) and store NHWC; two accumulators alternate so the
-//              next tile's MMAs overlap this tile's epilogue.
+//              bf16 remainder) and store NHWC; up to four accumulators rotate so
+//              the next tiles' MMAs overlap this tile's epilogue.
 // Precision modes: BF16 (one MMA per K step) and FP32-class "split" mode, where
 // every operand x is carried as hi = bf16(x), lo = bf16(x - hi) and the product
 // is hi*hi + hi*lo + lo*hi (three MMAs; two for conv1, whose integer pixels are
@@ -105,6 +105,11 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+// Arrive on `bar` (counted in its expected arrivals) once every cp.async this
+// thread issued before has landed in shared memory.
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -113,6 +118,26 @@ __device__ __forceinline__ void cp_wait() {
 __device__ __forceinline__ void st_shared16(uint32_t addr, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                : "memory");
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// 8 uint8 pixels (two little-endian words) -> 8 bf16.  A pixel b becomes the
+// float 2^23 + b by byte permutation, minus 2^23 gives b exactly (integers
+// below 256 have at most 8 significant bits, so the bf16 is the top half).
+__device__ __forceinline__ uint4 pixels8_to_bf16(uint32_t w0, uint32_t w1) {
+  uint32_t o[4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const uint32_t w = h < 2 ? w0 : w1;
+    const uint32_t j = 2 * (h & 1);
+    const float f0 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + j)) - 8388608.0f;
+    const float f1 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + j + 1)) - 8388608.0f;
+    o[h] = (__float_as_uint(f0) >> 16) | (__float_as_uint(f1) & 0xFFFF0000u);
+  }
+  return make_uint4(o[0], o[1], o[2], o[3]);
 }
 
 // Shared-memory matrix descriptor: K-major tile, 128-byte rows, 128-byte
@@ -149,7 +174,7 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
   int spins = 0;
   while (!mbar_try(bar, parity)) {
     if (*abort_flag) return false;
-    if (++spins > 16) __nanosleep(64);
+    if (++spins > 4096) __nanosleep(32);
     if (clock64() - t0 > kWaitCycles) {
       *abort_flag = 1;
       if (d_err) atomicCAS(d_err, 0, code);
@@ -190,14 +215,29 @@ template <int LAYER, bool SPLIT>
 struct Cfg {
   using G = Geo<LAYER>;
   static constexpr bool A_LO = SPLIT && LAYER != 1;  // conv1's integer pixels are exact in bf16
+  static constexpr bool B_RES = LAYER == 1;          // conv1's weights (16 / 32 KB) stay in shared memory
+  // Split mode stores the weight tile as [hi rows; lo rows] so that one MMA of
+  // twice the width gives A_hi*B_hi and A_hi*B_lo side by side in TMEM (the
+  // epilogue adds the halves); fc1's 256-wide tiles keep separate MMAs.
+  static constexpr bool B_CAT = SPLIT && LAYER != 4;
   static constexpr int A_BYTES = 128 * 128;
-  static constexpr int B_BYTES = G::BN * 128;
-  static constexpr int STAGE_BYTES = A_BYTES * (A_LO ? 2 : 1) + B_BYTES * (SPLIT ? 2 : 1);
-  static constexpr int STAGES_RAW = (192 * 1024) / STAGE_BYTES;
-  static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
-  static constexpr uint32_t TMEM_COLS = 2 * G::BN < 32 ? 32 : 2 * G::BN;
+  static constexpr int B_ROWS = G::BN * (SPLIT ? 2 : 1);
+  static constexpr int B_BYTES = G::BN * 128;            // one of hi / lo
+  static constexpr int ACC_N = B_CAT ? 2 * G::BN : G::BN;  // accumulator columns per tile
+  static constexpr int RES_BYTES = B_RES ? G::KB * B_ROWS * 128 : 0;
+  static constexpr int STAGE_BYTES = A_BYTES * (A_LO ? 2 : 1) + (B_RES ? 0 : B_ROWS * 128);
+  static constexpr int STAGES_RAW = (192 * 1024 - RES_BYTES) / STAGE_BYTES;
+  static constexpr int STAGES = B_RES ? 2 * G::KB : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
+  // fused conv1: re-zero lists (2 tiles x 4 slots x 256 threads) + node-state ring (2 tiles x 2 nodes)
+  static constexpr int DIRTY_BYTES = B_RES ? 2 * 4 * 256 * 4 + 2 * 2 * 80 : 0;
+  static constexpr int SMEM = RES_BYTES + STAGES * STAGE_BYTES + 1024 + 256 + DIRTY_BYTES + G::NTOT * 4;
+  // as many accumulators (up to 4) as TMEM's 512 columns hold, so the MMAs run
+  // ahead of the two epilogue warpgroups
+  static constexpr int NUM_ACC = (4 * ACC_N <= 512) ? 4 : 2;
+  static constexpr uint32_t TMEM_COLS = NUM_ACC * ACC_N < 32 ? 32 : NUM_ACC * ACC_N;
   static_assert(STAGES >= 2, "pipeline depth");
+  static_assert(RES_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0, "1024-byte aligned tiles");
+  static_assert(ACC_N <= 256 && TMEM_COLS <= 512, "accumulator");
   static_assert(SMEM <= 232448, "shared memory");
 };
 
@@ -209,12 +249,17 @@ struct GemmParams {
   const float *bias;
   void *out_hi;  // bf16 NHWC (layers 1-3) or FP32 [M][512] (layer 4)
   void *out_lo;  // bf16 remainders (split mode, layers 1-3)
-  long long M;
+  uint32_t M;  // rows, < 2^31 (checked by the launcher)
   int num_tiles;
   int *d_err;
 };
 
-constexpr int kThreads = 288;  // 9 warps
+// warps 0-7 producers, 8-11 epilogue, 12 MMA
+constexpr int kProdWarps = 8;
+constexpr int kProd = 32 * kProdWarps;  // producer threads
+constexpr int kEpiWarp0 = 8;
+constexpr int kMmaWarp = 12;
+constexpr int kThreads = 32 * (kMmaWarp + 1);
 
 template <int LAYER, bool SPLIT, bool FUSED>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
@@ -226,111 +271,203 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t *gbase = smem_raw + (base - raw);
-  // barriers and bookkeeping after the stages
-  const uint32_t bar0 = base + S * C::STAGE_BYTES;
+  // layout: [resident weights][stages][barriers + meta (256 B)][re-zero lists]
+  const uint32_t res = base;
+  const uint32_t stage0 = base + C::RES_BYTES;
+  const uint32_t bar0 = stage0 + S * C::STAGE_BYTES;
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
+  constexpr int NA = C::NUM_ACC;
   auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * S + a); };
-  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * S + 2 + a); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * S + 4);
-  uint8_t *meta = gbase + S * C::STAGE_BYTES + 8 * (2 * S + 5);
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * S + NA + a); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * S + 2 * NA);
+  const uint32_t wready_bar = bar0 + 8u * (2 * S + 2 * NA + 1);
+  uint8_t *meta = gbase + C::RES_BYTES + S * C::STAGE_BYTES + 8 * (2 * S + 2 * NA + 2);
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(meta);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(meta + 4);
+  uint32_t *dirty = reinterpret_cast<uint32_t *>(gbase + C::RES_BYTES + S * C::STAGE_BYTES + 256);
+  float *bias_s = reinterpret_cast<float *>(gbase + C::RES_BYTES + S * C::STAGE_BYTES + 256 + C::DIRTY_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto sA_of = [&](int s) { return stage0 + uint32_t(s) * C::STAGE_BYTES; };
+  auto sB_of = [&](int s) { return sA_of(s) + C::A_BYTES * (C::A_LO ? 2 : 1); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(full_bar(s), 128);
+      mbar_init(full_bar(s), kProd);
       mbar_init(empty_bar(s), 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < NA; ++a) {
       mbar_init(tfull_bar(a), 1);
       mbar_init(tempty_bar(a), 4);
     }
     mbar_init(drain_bar, 1);
+    mbar_init(wready_bar, kProd);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) tmem_alloc(smem_u32((const void *)tmem_slot), C::TMEM_COLS);
+  if (warp == kMmaWarp) tmem_alloc(smem_u32((const void *)tmem_slot), C::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp < 4) {
+  if (warp < kProdWarps) {
     // ------------------------------------------------------------ producers
-    const int pt = threadIdx.x;  // 0..127
-    const int ch = pt & 7, r0 = pt >> 3;
-    int g = 0, pending = -1;
-    bool ok = true;
-    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-      const long long m0 = (long long)(t / NT) * 128;
-      const int n0 = (t % NT) * BN;
-      // per-row source offsets for this tile (rows r0 + 16 i)
-      long long rowoff[8];
-      int rowx[8], rowy[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        long long m = m0 + r0 + 16 * i;
-        if (m > p.M - 1) m = p.M - 1;
-        const long long leaf = m / G::P;
-        const int px = int(m - leaf * G::P);
-        if (LAYER == 1) {
-          const int oy = px / 20, ox = px - oy * 20;
-          rowx[i] = ox;
-          rowy[i] = oy;
-          rowoff[i] = FUSED ? leaf : leaf * kFrameBytes + (4 * oy) * 84 + 4 * ox;
-        } else if (LAYER == 2) {
-          const int oy = px / 9, ox = px - oy * 9;
-          rowoff[i] = leaf * (kP1 * kC1) + (2 * oy * 20 + 2 * ox) * kC1;
-        } else if (LAYER == 3) {
-          const int oy = px / 7, ox = px - oy * 7;
-          rowoff[i] = leaf * (kP2 * kC2) + (oy * 9 + ox) * kC2;
-        } else {
-          rowoff[i] = m * kKF;
-        }
+    const int pt = threadIdx.x;  // 0..255
+    const int ch = pt & 7, r0 = pt >> 3;  // 16-byte chunk ch of rows r0 + 32 i
+    if (C::B_RES) {
+      // resident weights: KB k-blocks of [B_ROWS x 64] (hi rows, then lo rows)
+      for (int idx = pt; idx < KB * C::B_ROWS * 8; idx += kProd) {
+        const int kb = idx / (C::B_ROWS * 8), rem = idx - kb * (C::B_ROWS * 8), r = rem >> 3, c = rem & 7;
+        const uint32_t off = uint32_t(kb) * (C::B_ROWS * 128) + sw128_off(r, c);
+        const __nv_bfloat16 *src = r < BN ? p.b_hi : p.b_lo;
+        cp_async16(res + off, src + (long long)(r % BN) * G::K + kb * 64 + c * 8);
       }
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = g % S;
-        const uint32_t round = uint32_t(g / S);
-        if (!wait_bar(empty_bar(s), (round & 1u) ^ 1u, abort_flag, p.d_err, 1)) {
-          ok = false;
-          break;
+      cp_commit();
+      cp_wait<0>();
+      fence_proxy_async();
+      mbar_arrive(wready_bar);
+    }
+    if (LAYER == 1 && FUSED) {
+      // conv1 operand rendered from node states (channel kb = history slot kb),
+      // all KB stages of a tile at once.  An im2col row is zero unless one of
+      // the 2 x 2 cells its 8 x 8 patch covers holds an object, so the tiles
+      // stay zero and only the rows next to the <= 4 objects of the <= 2 nodes
+      // a tile's 128 rows touch are rendered.  Candidate = (slot kb, node li,
+      // object k, patch offset dy dx, 16-byte chunk cc): this thread owns
+      // (li, k, dy, dx, cc) = its index and the 4 slots; duplicates write
+      // identical bytes.  What a thread wrote into a stage is re-zeroed when
+      // the stage next comes round (S = 2 KB: every other tile).
+      static_assert(!(LAYER == 1 && FUSED) || S == 2 * KB, "ring of two tiles");
+      for (int idx = pt; idx < S * (C::STAGE_BYTES / 16); idx += kProd)
+        st_shared16(stage0 + uint32_t(idx) * 16u, make_uint4(0u, 0u, 0u, 0u));
+      for (int j = 0; j < 8; ++j) dirty[j * kProd + pt] = 0u;
+      const int li = pt >> 7, k = (pt >> 5) & 3, dy = (pt >> 4) & 1, dx = (pt >> 3) & 1, cc = pt & 7;
+      // node states of a tile's <= 2 nodes, fetched one tile ahead into a ring
+      const uint32_t ring = smem_u32(dirty + 8 * kProd);
+      auto prefetch_states = [&](int t, int slot) {
+        if (pt < 10) {
+          const uint32_t m0 = uint32_t(t) * 128u;
+          const uint32_t mlast = (m0 + 127u < p.M - 1u) ? m0 + 127u : p.M - 1u;
+          const uint32_t leaf0 = m0 / uint32_t(kP1), leaf_last = mlast / uint32_t(kP1);
+          const uint32_t l = (leaf0 + uint32_t(pt / 5) <= leaf_last) ? leaf0 + uint32_t(pt / 5) : leaf_last;
+          cp_async16(ring + uint32_t(slot * 160 + pt * 16),
+                     reinterpret_cast<const uint4 *>(p.a_hi) + size_t(l) * 5 + (pt % 5));
         }
-        const uint32_t sA = base + s * C::STAGE_BYTES;
-        const uint32_t sAlo = sA + C::A_BYTES;
-        const uint32_t sB = sA + C::A_BYTES * (C::A_LO ? 2 : 1);
-        const uint32_t sBlo = sB + C::B_BYTES;
-        // A tile
+        cp_commit();
+      };
+      if (int(blockIdx.x) < p.num_tiles) prefetch_states(blockIdx.x, 0);
+      int c = 0;
+      for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++c) {
+        const int g = c * KB;
+        {
+          // the MMA thread commits once per tile, to the tile's last stage: its
+          // completion frees all KB stages
+          const int s = (g + KB - 1) % S;
+          const uint32_t round = uint32_t((g + KB - 1) / S);
+          wait_bar(empty_bar(s), (round & 1u) ^ 1u, abort_flag, p.d_err, 1);
+        }
+        named_bar_sync(1, kProd);  // every producer decides together
+        if (*abort_flag) break;
+        cp_wait<0>();  // this tile's node states (fetched during the previous tile)
+        uint32_t *dj = dirty + (c & 1) * (4 * kProd);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int r = r0 + 16 * i;
-          const uint32_t off = sw128_off(r, ch);
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t a = dj[j * kProd + pt];
+          if (a) st_shared16(a, make_uint4(0u, 0u, 0u, 0u));
+        }
+        named_bar_sync(1, kProd);  // states visible, re-zeroing done
+        const int tn = t + int(gridDim.x);
+        if (tn < p.num_tiles) prefetch_states(tn, (c + 1) & 1);
+        uint4 P[4];
+        const uint4 *Ps = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(dirty + 8 * kProd) +
+                                                          (c & 1) * 160 + li * 80);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) P[j] = Ps[j];
+        const uint32_t m0 = uint32_t(t) * 128u;
+        const uint32_t mlast = (m0 + 127u < p.M - 1u) ? m0 + 127u : p.M - 1u;
+        const uint32_t leaf0 = m0 / uint32_t(kP1), leaf_last = mlast / uint32_t(kP1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {  // slot (= K block) j
+          uint32_t wrote = 0u;
+          const uint32_t leaf = leaf0 + uint32_t(li);
+          const uint32_t wk = (k & 2) ? ((k & 1) ? P[j].w : P[j].z) : ((k & 1) ? P[j].y : P[j].x);
+          const int ox = int(int16_t(wk & 0xFFFFu)) - dx, oy = int(int16_t(wk >> 16)) - dy;
+          const uint32_t m = leaf * uint32_t(kP1) + uint32_t(oy * 20 + ox);
+          if (leaf <= leaf_last && ox >= 0 && ox <= 19 && oy >= 0 && oy <= 19 && m >= m0 && m <= mlast) {
+            int oxs[4], oys[4];
+            unpack_slot(P[j], oxs, oys);
+            const int y = 4 * oy + cc;
+            const uint32_t w0 = render_word(oxs, oys, ox, y);
+            const uint32_t w1 = render_word(oxs, oys, ox + 1, y);
+            wrote = sA_of((g + j) % S) + sw128_off(int(m - m0), cc);
+            st_shared16(wrote, pixels8_to_bf16(w0, w1));
+          }
+          dj[j * kProd + pt] = wrote;
+        }
+        fence_proxy_async();
+#pragma unroll
+        for (int kb = 0; kb < KB; ++kb) mbar_arrive(full_bar((g + kb) % S));
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    } else {
+      // every stage's copies stay in flight until they land; the full barrier
+      // counts one hardware arrival per producer thread at that moment
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+        const uint32_t m0 = uint32_t(t / NT) * 128u;
+        const int n0 = (t % NT) * BN;
+        // per-row source offsets for this tile (rows r0 + 32 i)
+        long long rowoff[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          uint32_t m = m0 + uint32_t(r0 + 32 * i);
+          if (m > p.M - 1u) m = p.M - 1u;
+          const uint32_t leaf = m / uint32_t(G::P);
+          const int px = int(m - leaf * uint32_t(G::P));
           if (LAYER == 1) {
-            uint32_t w0, w1;
-            if (FUSED) {
-              const uint4 P = __ldg(reinterpret_cast<const uint4 *>(p.a_hi) + rowoff[i] * 5 + kb);
-              int ox[4], oy[4];
-              unpack_slot(P, ox, oy);
-              const int y = 4 * rowy[i] + ch;
-              w0 = render_word(ox, oy, rowx[i], y);
-              w1 = render_word(ox, oy, rowx[i] + 1, y);
-            } else {
-              const uint8_t *src = static_cast<const uint8_t *>(p.a_hi) + rowoff[i] + kb * 7056 + ch * 84;
-              w0 = __ldg(reinterpret_cast<const uint32_t *>(src));
-              w1 = __ldg(reinterpret_cast<const uint32_t *>(src + 4));
-            }
-            // 8 pixels -> 8 bf16 (integers below 256 are exact in bf16)
-            uint32_t o[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const uint32_t wsrc = h < 2 ? w0 : w1;
-              const uint32_t b0 = (wsrc >> (16 * (h & 1))) & 0xFFu;
-              const uint32_t b1 = (wsrc >> (16 * (h & 1) + 8)) & 0xFFu;
-              o[h] = (__float_as_uint(float(b0)) >> 16) | (__float_as_uint(float(b1)) & 0xFFFF0000u);
-            }
-            st_shared16(sA + off, make_uint4(o[0], o[1], o[2], o[3]));
+            const int oy = px / 20, ox = px - oy * 20;
+            rowoff[i] = (long long)leaf * kFrameBytes + (4 * oy) * 84 + 4 * ox;
+          } else if (LAYER == 2) {
+            const int oy = px / 9, ox = px - oy * 9;
+            rowoff[i] = (long long)leaf * (kP1 * kC1) + (2 * oy * 20 + 2 * ox) * kC1;
+          } else if (LAYER == 3) {
+            const int oy = px / 7, ox = px - oy * 7;
+            rowoff[i] = (long long)leaf * (kP2 * kC2) + (oy * 9 + ox) * kC2;
           } else {
+            rowoff[i] = (long long)m * kKF;
+          }
+        }
+        for (int kb = 0; kb < KB; ++kb) {
+          const int s = g % S;
+          const uint32_t round = uint32_t(g / S);
+          if (!wait_bar(empty_bar(s), (round & 1u) ^ 1u, abort_flag, p.d_err, 1)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sA = sA_of(s);
+          const uint32_t sAlo = sA + C::A_BYTES;
+          const uint32_t sB = sB_of(s);
+          const uint32_t sBlo = sB + C::B_BYTES;
+          if (LAYER == 1) {
+            // conv1 from uint8 frame stacks: 8 pixels of kernel row ch, converted
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const uint8_t *src = static_cast<const uint8_t *>(p.a_hi) + rowoff[i] + kb * 7056 + ch * 84;
+              const uint32_t w0 = __ldg(reinterpret_cast<const uint32_t *>(src));
+              const uint32_t w1 = __ldg(reinterpret_cast<const uint32_t *>(src + 4));
+              st_shared16(sA + sw128_off(r0 + 32 * i, ch), pixels8_to_bf16(w0, w1));
+            }
+            fence_proxy_async();
+            mbar_arrive(full_bar(s));
+            ++g;
+            continue;
+          }
+          // A tile: im2col rows of the NHWC activation map
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint32_t off = sw128_off(r0 + 32 * i, ch);
             long long e;
             if (LAYER == 2) {
               const int pos = 2 * kb + (ch >> 2), ky = pos >> 2, kx = pos & 3;
@@ -344,65 +481,79 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
             cp_async16(sA + off, static_cast<const __nv_bfloat16 *>(p.a_hi) + e);
             if (C::A_LO) cp_async16(sAlo + off, static_cast<const __nv_bfloat16 *>(p.a_lo) + e);
           }
-        }
-        // B tile (weights, [NTOT][K] K-major)
+          // B tile (weights, [NTOT][K] K-major): hi rows, then lo rows
 #pragma unroll
-        for (int i = 0; i < BN / 16; ++i) {
-          const int r = r0 + 16 * i;
-          const uint32_t off = sw128_off(r, ch);
-          const long long e = (long long)(n0 + r) * G::K + kb * 64 + ch * 8;
-          cp_async16(sB + off, p.b_hi + e);
-          if (SPLIT) cp_async16(sBlo + off, p.b_lo + e);
+          for (int i = 0; i < BN / 32; ++i) {
+            const int r = r0 + 32 * i;
+            const uint32_t off = sw128_off(r, ch);
+            const long long e = (long long)(n0 + r) * G::K + kb * 64 + ch * 8;
+            cp_async16(sB + off, p.b_hi + e);
+            if (SPLIT) cp_async16(sBlo + off, p.b_lo + e);
+          }
+          cp_async_arrive(full_bar(s));
+          ++g;
         }
-        cp_commit();
-        if (pending >= 0) {
-          cp_wait<1>();
-          fence_proxy_async();
-          mbar_arrive(full_bar(pending));
-        }
-        pending = s;
-        ++g;
       }
+      asm volatile("cp.async.wait_all;" ::: "memory");  // nothing may still be landing at teardown
     }
-    cp_wait<0>();
-    fence_proxy_async();
-    if (pending >= 0) mbar_arrive(full_bar(pending));
-  } else if (warp == 8) {
+  } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(BN);
+      constexpr uint32_t idesc_wide = idesc_bf16(C::B_CAT ? 2 * BN : BN);  // [hi; lo] weight rows
+      constexpr uint32_t idesc_n = idesc_bf16(BN);
       int g = 0, it = 0;
       bool ok = true;
+      if (C::B_RES) ok = wait_bar(wready_bar, 0, abort_flag, p.d_err, 6);
       for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x, ++it) {
-        const int acc = it & 1;
-        if (!wait_bar(tempty_bar(acc), (uint32_t((it >> 1) & 1)) ^ 1u, abort_flag, p.d_err, 2)) break;
+        const int acc = it % NA;
+        if (!wait_bar(tempty_bar(acc), (uint32_t((it / NA) & 1)) ^ 1u, abort_flag, p.d_err, 2)) break;
         tc_fence_after();
-        const uint32_t d = tmem + uint32_t(acc * BN);
-        for (int kb = 0; kb < KB; ++kb) {
-          const int s = g % S;
-          const uint32_t round = uint32_t(g / S);
-          if (!wait_bar(full_bar(s), round & 1u, abort_flag, p.d_err, 3)) {
-            ok = false;
-            break;
+        const uint32_t d = tmem + uint32_t(acc * C::ACC_N);
+        // cp.async-fed stages were written through the generic proxy and the
+        // hardware arrival carries no proxy fence: one fence per F stages orders
+        // them before the tensor core's async-proxy reads.  conv1's producers
+        // write with st.shared and fence themselves.
+        constexpr bool kFence = !C::B_RES;
+        constexpr int F = (kFence && S >= 4) ? 2 : 1;
+        constexpr bool kTileCommit = LAYER == 1 && FUSED;  // one commit frees the tile's stages
+        for (int kb0 = 0; kb0 < KB && ok; kb0 += F) {
+          const int nf = (KB - kb0) < F ? (KB - kb0) : F;
+          for (int f = 0; f < nf; ++f) {
+            const int sf = (g + f) % S;
+            if (!wait_bar(full_bar(sf), uint32_t((g + f) / S) & 1u, abort_flag, p.d_err, 3)) {
+              ok = false;
+              break;
+            }
           }
+          if (!ok) break;
+          if (kFence) fence_proxy_async();
           tc_fence_after();
-          const uint32_t sA = base + s * C::STAGE_BYTES;
+          for (int f = 0; f < nf; ++f) {
+          const int kb = kb0 + f;
+          const int s = g % S;
+          const uint32_t sA = sA_of(s);
           const uint32_t sAlo = sA + C::A_BYTES;
-          const uint32_t sB = sA + C::A_BYTES * (C::A_LO ? 2 : 1);
+          const uint32_t sB = C::B_RES ? res + uint32_t(kb) * (C::B_ROWS * 128) : sB_of(s);
           const uint32_t sBlo = sB + C::B_BYTES;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {  // K = 16 bf16 = 32 bytes per instruction
             const uint32_t first = (kb | j) != 0;
             const uint64_t a = sw128_desc(sA) + uint64_t(2 * j);
             const uint64_t b = sw128_desc(sB) + uint64_t(2 * j);
-            mma_bf16(d, a, b, idesc, first);
-            if (SPLIT) {
-              mma_bf16(d, a, sw128_desc(sBlo) + uint64_t(2 * j), idesc, 1u);
-              if (C::A_LO) mma_bf16(d, sw128_desc(sAlo) + uint64_t(2 * j), b, idesc, 1u);
+            if (C::B_CAT) {
+              mma_bf16(d, a, b, idesc_wide, first);  // [A_hi B_hi | A_hi B_lo]
+              if (C::A_LO) mma_bf16(d, sw128_desc(sAlo) + uint64_t(2 * j), b, idesc_n, 1u);  // + A_lo B_hi
+            } else {
+              mma_bf16(d, a, b, idesc_n, first);
+              if (SPLIT) {
+                mma_bf16(d, a, sw128_desc(sBlo) + uint64_t(2 * j), idesc_n, 1u);
+                if (C::A_LO) mma_bf16(d, sw128_desc(sAlo) + uint64_t(2 * j), b, idesc_n, 1u);
+              }
             }
           }
-          mma_commit(empty_bar(s));  // stage free once these MMAs have read it
+          if (!kTileCommit || kb == KB - 1) mma_commit(empty_bar(s));  // stage(s) free once read
           ++g;
+          }
         }
         if (!ok) break;
         mma_commit(tfull_bar(acc));
@@ -422,45 +573,55 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
-    const int q = warp & 3;
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int row = q * 32 + lane;
+    for (int i = threadIdx.x - 32 * kEpiWarp0; i < G::NTOT; i += 128) bias_s[i] = p.bias[i];
+    named_bar_sync(2, 128);
     int it = 0;
     for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++it) {
-      const int acc = it & 1;
-      if (!wait_bar(tfull_bar(acc), uint32_t((it >> 1) & 1), abort_flag, p.d_err, 4)) break;
+      const int acc = it % NA;
+      if (!wait_bar(tfull_bar(acc), uint32_t((it / NA) & 1), abort_flag, p.d_err, 4)) break;
       tc_fence_after();
-      const long long m = (long long)(t / NT) * 128 + row;
+      const uint32_t m = uint32_t(t / NT) * 128u + uint32_t(row);
       const int n0 = (t % NT) * BN;
-      const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * BN);
+      const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * C::ACC_N);
 #pragma unroll 1
       for (int j = 0; j < BN / 16; ++j) {
         uint32_t r[16];
         tmem_ld16(tbase + uint32_t(j * 16), r);
-        tmem_wait_ld();
         float v[16];
+        if (C::B_CAT) {
+          uint32_t r2[16];  // the A_hi * B_lo half
+          tmem_ld16(tbase + uint32_t(BN + j * 16), r2);
+          tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const float x = __uint_as_float(r[e]) + __ldg(p.bias + n0 + j * 16 + e);
-          v[e] = x > 0.f ? x : 0.f;
+          for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]) + __uint_as_float(r2[e]);
+        } else {
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
         }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + bias_s[n0 + j * 16 + e], 0.f);
         if (m < p.M) {
           if (LAYER == 4) {
-            float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(p.out_hi) + m * G::NTOT + n0 + j * 16);
+            float4 *dst =
+                reinterpret_cast<float4 *>(static_cast<float *>(p.out_hi) + size_t(m) * G::NTOT + n0 + j * 16);
 #pragma unroll
             for (int e = 0; e < 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
           } else {
             uint32_t hi[8], lo[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-              const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]), h1 = __float2bfloat16_rn(v[2 * e + 1]);
-              hi[e] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
+              const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+              hi[e] = *reinterpret_cast<const uint32_t *>(&h);
               if (SPLIT) {
-                const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
-                const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
-                lo[e] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+                const float2 hf = __bfloat1622float2(h);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+                lo[e] = *reinterpret_cast<const uint32_t *>(&l);
               }
             }
-            const long long o = m * G::NTOT + n0 + j * 16;
+            const size_t o = size_t(m) * G::NTOT + n0 + j * 16;
             uint4 *dh = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(p.out_hi) + o);
             dh[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             dh[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
@@ -480,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
   // teardown: every role has left its loop (all waits are bounded)
   tc_fence_before();
   __syncthreads();
-  if (warp == 8) {
+  if (warp == kMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, C::TMEM_COLS);
   }
@@ -511,8 +672,9 @@ int launch(const GemmParams &p0, long long M, int kind, cudaStream_t st) {
                                     C::SMEM);
   });
   if (attr_err != cudaSuccess) return BCTS_ECUDA;
+  if (M > 0x7FFFFFFFLL) return BCTS_EINVAL;
   GemmParams p = p0;
-  p.M = M;
+  p.M = uint32_t(M);
   const long long mt = (M + 127) / 128;
   const long long tiles = mt * (Geo<LAYER>::NTOT / Geo<LAYER>::BN);
   if (tiles > 0x7FFFFFFFLL) return BCTS_EINVAL;

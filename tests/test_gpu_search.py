@@ -123,3 +123,25 @@ def test_atari_scale_sampled_roots(oracle_lib, dev, precision):
     # every root: actions are valid and values finite
     assert np.isfinite(val).all() and ((act >= 0) & (act < A)).all()
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [p for p in PRECISIONS if p in ("fp32", "bf16", "fp8")])
+def test_fused_render_equals_materialised_frames(oracle_lib, dev, precision):
+    """conv1 rendering its operand from node states must see exactly the pixels
+    the frame renderer writes: identical values with and without BCTS_FLAG_FRAMES."""
+    torch, bcts = dev
+    A, d = 9, 2
+    W = inputs.qnet_weights(A, seed=1234)
+    roots = inputs.root_states(range(70, 76))
+    out = []
+    for flags in (0, bcts.BCTS_FLAG_FRAMES):
+        try:
+            ctx = bcts.bcts_create(W, A, d, 0.99, 1.0, precision=precision, flags=flags)
+        except bcts.BctsError as e:
+            if e.code == bcts.BCTS_ENOKERNEL:
+                pytest.skip(str(e))
+            raise
+        out.append(bcts.bcts_search(ctx, roots))
+        ctx.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
