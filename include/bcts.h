@@ -155,6 +155,13 @@ BCTS_API int bcts_search_device(bcts_ctx *ctx, const bcts_state *d_roots, int n,
  * Batched form: n roots, root i searched at depth d_i in [0, 6] with A_i actions
  * in [1, context A] (FC2 rows 0..A_i-1 are used).  Host pointers, synchronous.
  * out_root_values is n * (context A) floats; row i holds A_i values, the rest 0.
+ * Roots are grouped by (A, d); each depth of each group expands in one launch,
+ * and every Q-network evaluation of the call (roots, depth-1 nodes, leaves of
+ * all groups) runs as one batch.  The second call with the same multiset of
+ * (A, d) is captured into a CUDA graph, later ones replay it.  The leaf chunk
+ * is autotuned per leaf-count bucket on first use (kept in memory, and in the
+ * file named by the BCTS_TUNE_FILE environment variable when set).  Each root's
+ * result is bit-identical to searching it alone.
  */
 BCTS_API int bcts_search_mixed(bcts_ctx *ctx, const bcts_state *roots, const int32_t *depths, const int32_t *actions,
                       int n, int32_t *out_action, float *out_root_values);
@@ -184,6 +191,11 @@ BCTS_API int bcts_poll(bcts_ctx *ctx, uint64_t ticket, int32_t *out_action, floa
  */
 BCTS_API int bcts_expand(const bcts_state *d_parents, const float *d_parent_R, int64_t n_parents, int A, float gamma_pow,
                 bcts_state *d_children, float *d_child_R, int8_t *d_child_reward, void *stream);
+
+/* One environment tick on the host: *out = G(*s, a), *reward (may be NULL) in
+ * {-1, 0, 1}; a in [0, 18).  The same rules as bcts_expand (Alg. 1's simulator),
+ * for callers that advance an episode by the chosen action.  No context, no GPU. */
+BCTS_API int bcts_env_step(const bcts_state *s, int a, bcts_state *out, int *reward);
 
 /* Render n states to n frame stacks, uint8 [n][4][84][84], channel h = history slot h. */
 BCTS_API int bcts_render(const bcts_state *d_states, int64_t n, uint8_t *d_frames, void *stream);

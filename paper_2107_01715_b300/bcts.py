@@ -31,7 +31,7 @@ PRECISIONS = {"fp32": BCTS_PREC_FP32, "bf16": BCTS_PREC_BF16, "fp8": BCTS_PREC_F
 
 EXPORTED = ["bcts_qnet_numel", "bcts_create", "bcts_destroy", "bcts_last_error", "bcts_search",
             "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll", "bcts_expand",
-            "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static"]
+            "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step"]
 BCTS_STATIC_MAX_NODES = 128
 BCTS_FLAG_FRAMES = 1
 KERNEL_CLASSES = ["expand", "render", "conv1", "conv2", "conv3", "fc1", "fc2", "backup"]
@@ -67,8 +67,9 @@ lib.bcts_render.argtypes = [_P, _I64, _P, _P]
 lib.bcts_qnet.argtypes = [_P, _P, _I64, _P, _P]
 lib.bcts_profile.argtypes = [_P, _I, _P, _P, _P]
 lib.bcts_qnet_static.argtypes = [_P, _I, _P, _I64, _P, _P]
+lib.bcts_env_step.argtypes = [_P, _I, _P, ctypes.POINTER(_I)]
 for _f in ("bcts_search", "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll",
-           "bcts_expand", "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static"):
+           "bcts_expand", "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step"):
     getattr(lib, _f).restype = _I
 
 
@@ -235,3 +236,12 @@ def bcts_profile(ctx: Context, enable: bool):
 def bcts_qnet_static(d_qnet_weights, A: int, d_frames, n: int, d_q, stream=None) -> int:
     """Allocation-free Q-network on n <= BCTS_STATIC_MAX_NODES stacks (device pointers)."""
     return _check(lib.bcts_qnet_static(_addr(d_qnet_weights), A, _addr(d_frames), n, _addr(d_q), _stream(stream)))
+
+
+def bcts_env_step(state, a: int):
+    """Host environment tick: returns (next_state, reward)."""
+    s = _roots(state)[:1]
+    out = np.zeros(1, dtype=STATE_DTYPE)
+    r = _I()
+    _check(lib.bcts_env_step(s.ctypes.data, int(a), out.ctypes.data, ctypes.byref(r)))
+    return out[0], int(r.value)

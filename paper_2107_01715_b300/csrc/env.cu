@@ -37,7 +37,7 @@ union StateRegs {
   bcts_state s;
 };
 
-__device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
+__host__ __device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
   // C. Wellons' lowbias32 integer hash.
   x ^= x >> 16;
   x *= 0x7feb352du;
@@ -47,7 +47,9 @@ __device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
   return x;
 }
 
-__device__ __forceinline__ void bounce(int &p, int &v) {
+__host__ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__host__ __device__ __forceinline__ void bounce(int &p, int &v) {
   int q = p + v;
   if (q < 0) {
     q = -q;
@@ -63,12 +65,12 @@ __device__ __forceinline__ void bounce(int &p, int &v) {
 // One tick: agent moves by the action and clamps, objects move and reflect,
 // contact (same cell) pays +1 / -1 and respawns the object at a hashed cell;
 // the history slots shift by one.  Returns the reward clipped to [-1, 1].
-__device__ __forceinline__ int sprite_step(const bcts_state &s, int a, bcts_state &n) {
+__host__ __device__ __forceinline__ int sprite_step(const bcts_state &s, int a, bcts_state &n) {
   const int dir = a % 9, speed = 1 + a / 9;
   const int dx = int((kDXP >> (2 * dir)) & 3u) - 1;
   const int dy = int((kDYP >> (2 * dir)) & 3u) - 1;
-  const int ax = min(max(s.pos[3][0][0] + speed * dx, 0), kGrid - 1);
-  const int ay = min(max(s.pos[3][0][1] + speed * dy, 0), kGrid - 1);
+  const int ax = clampi(s.pos[3][0][0] + speed * dx, 0, kGrid - 1);
+  const int ay = clampi(s.pos[3][0][1] + speed * dy, 0, kGrid - 1);
 #pragma unroll
   for (int h = 0; h < kHist - 1; ++h)
 #pragma unroll
@@ -102,7 +104,7 @@ __device__ __forceinline__ int sprite_step(const bcts_state &s, int a, bcts_stat
   }
   n.tick = s.tick + 1u;
   n.pad = 0u;
-  return max(-1, min(1, reward));
+  return clampi(reward, -1, 1);
 }
 
 __global__ void __launch_bounds__(256) expand_kernel(const uint4 *__restrict__ parents,
@@ -208,4 +210,18 @@ extern "C" int bcts_render(const bcts_state *d_states, int64_t n, uint8_t *d_fra
   const int rc = bcts::launch_render(d_states, n, d_frames, (cudaStream_t)stream);
   if (rc != BCTS_OK) bcts::set_thread_error("bcts_render: launch failed");
   return rc;
+}
+
+// The same step on the host (one state), for callers that advance an episode
+// by the chosen action (the serving simulator, tests).
+extern "C" int bcts_env_step(const bcts_state *s, int a, bcts_state *out, int *reward) {
+  if (!s || !out || a < 0 || a >= bcts::kMaxA) {
+    bcts::set_thread_error("bcts_env_step: invalid argument");
+    return BCTS_EINVAL;
+  }
+  bcts_state n;
+  const int r = bcts::sprite_step(*s, a, n);
+  *out = n;
+  if (reward) *reward = r;
+  return BCTS_OK;
 }

@@ -25,12 +25,13 @@ struct SimtWeights {
 size_t simt_scratch_bytes(int64_t chunk);
 
 // Q-network on n frame stacks: q [n][A] (may be NULL), maxq [n] (may be NULL).
+// node_A (may be NULL): per-node action count for the max (batched form).
 int simt_qnet_forward(const SimtWeights &w, const uint8_t *frames, int64_t n, float *q, float *maxq,
-                      void *scratch, cudaStream_t stream);
+                      void *scratch, cudaStream_t stream, const uint8_t *node_A = nullptr);
 
 // FC2 + max over actions on FP32 fc1 activations h [n][512] (one warp per node).
 int launch_fc2_max(const float *h, const float *W2, const float *b2, int A, int64_t n, float *q, float *maxq,
-                   cudaStream_t st);
+                   cudaStream_t st, const uint8_t *node_A = nullptr);
 
 // qnet_tc.cu (tensor-core paths)
 struct TcWeights;  // defined in qnet_tc.cu
@@ -38,13 +39,14 @@ size_t tc_scratch_bytes(int64_t chunk, int precision);
 int tc_weights_create(const float *host_weights, int A, int precision, TcWeights **out, std::string &err);
 void tc_weights_destroy(TcWeights *w);
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
-                    float *maxq, void *scratch, cudaStream_t stream, int *d_err);
+                    float *maxq, void *scratch, cudaStream_t stream, int *d_err, const uint8_t *node_A = nullptr);
 
 // search.cu backup kernels
 int launch_segment_max(const float *R, const float *maxq, int64_t n_seg, int64_t seg_len, float gamma_pow,
                        float *V, cudaStream_t stream);
+// q0 rows are q_stride floats apart (root Q-values); r1, maxq1, V rows are A apart.
 int launch_finalize(const float *q0, const float *maxq1, const float *r1, const float *V, int n, int A,
                     int depth, int A_stride, float gamma, float gamma_d, float corr, int32_t *action,
-                    float *values, cudaStream_t stream);
+                    float *values, cudaStream_t stream, int q_stride = 0);
 
 }  // namespace bcts

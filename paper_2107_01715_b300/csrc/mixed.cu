@@ -1,14 +1,415 @@
-// mixed.cu -- batched form: many roots of mixed depth and action count.
+// mixed.cu -- batched form: many roots of mixed depth d and action count A in
+// one search pass (the serving loop runs on it too).
+//
+// Roots are grouped by (A, d).  Per group the level-synchronous expansion of
+// Alg. 1 runs as usual (one launch per level), but every Q-network evaluation
+// of the pass runs once over the union of all groups' nodes: one pass over all
+// roots, one over all depth-1 nodes, one over all leaves, so each persistent
+// tensor-core layer kernel sees the whole batch.  The max over actions uses
+// each node's own A (FC2 rows 0..A-1).  Backup and the Eq. 7 correction run
+// per group.  For a composition seen before, the whole device part of the pass
+// (copies included) is replayed from a captured CUDA graph.  The leaf chunk
+// size of the union evaluation is picked by timing the candidates on the first
+// pass of a new leaf-count bucket (optionally persisted as JSON).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
 #include "search.cuh"
 
 namespace bcts {
-int Ctx::run_mixed(const bcts_state *, const bcts_state *, const int32_t *, const int32_t *, int, int32_t *,
-                   float *) {
-  return fail(BCTS_ENOKERNEL, "not built yet");
+
+struct MixedGroup {
+  int A = 0, d = 0, n = 0;
+  int root_off = 0;       // first sorted root
+  int64_t l1_off = 0;     // first depth-1 node in the union level-1 buffer
+  int64_t leaf_off = 0;   // first leaf in the union leaf buffer (d >= 2)
+  int64_t nleaf = 0;      // n * A^d for d >= 2
+  int64_t mid_max = 0;    // largest intermediate level (depths 2 .. d-1)
+};
+
+struct MixedPlan {
+  int n = 0;
+  std::vector<int> order;  // sorted position -> caller's root index
+  std::vector<MixedGroup> groups;
+  int64_t n1 = 0, nleaf = 0, mid = 0;
+  std::string key;
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+  uint64_t generation = 0;
+};
+
+struct MixedState {
+  DevBuf roots, q0, L1, r1, maxq1, nodeA1, mid[2], Rmid[2], leaves, Rleaf, maxq_leaf, nodeA_leaf, V, act, val;
+  HostBuf host;
+  std::map<std::string, int> seen;
+  std::map<std::string, GraphEntry> graphs;
+  std::map<std::string, int64_t> tuned_chunk;  // leaf-count bucket -> chunk
+  bool tune_loaded = false;
+  ~MixedState() {
+    for (auto &kv : graphs)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    DevBuf *b[] = {&roots, &q0, &L1, &r1, &maxq1, &nodeA1, &mid[0], &mid[1], &Rmid[0], &Rmid[1],
+                   &leaves, &Rleaf, &maxq_leaf, &nodeA_leaf, &V, &act, &val};
+    for (DevBuf *x : b)
+      if (x->p) cudaFree(x->p);
+    if (host.p) cudaFreeHost(host.p);
+  }
+};
+
+void mixed_destroy(MixedState *m) { delete m; }
+
+namespace {
+
+int64_t ipow(int64_t a, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= a;
+  return r;
 }
+
+std::string tune_file() {
+  const char *f = std::getenv("BCTS_TUNE_FILE");
+  return f ? std::string(f) : std::string();
+}
+
+int64_t leaf_bucket(int64_t nleaf) {
+  int64_t b = 1;
+  while (b < nleaf) b <<= 1;
+  return b;
+}
+
+}  // namespace
+
+// Buffers for a plan; bumps the generation when anything moves.
+static int mixed_ensure(Ctx *c, MixedState *m, const MixedPlan &pl) {
+  const int As = c->A_create;
+  struct Need {
+    DevBuf *b;
+    size_t bytes;
+  } need[] = {
+      {&m->roots, size_t(pl.n) * kStateBytes},
+      {&m->q0, size_t(pl.n) * As * 4},
+      {&m->L1, size_t(std::max<int64_t>(pl.n1, 1)) * kStateBytes},
+      {&m->r1, size_t(std::max<int64_t>(pl.n1, 1)) * 4},
+      {&m->maxq1, size_t(std::max<int64_t>(pl.n1, 1)) * 4},
+      {&m->nodeA1, size_t(std::max<int64_t>(pl.n1, 1))},
+      {&m->mid[0], size_t(std::max<int64_t>(pl.mid, 1)) * kStateBytes},
+      {&m->mid[1], size_t(std::max<int64_t>(pl.mid, 1)) * kStateBytes},
+      {&m->Rmid[0], size_t(std::max<int64_t>(pl.mid, 1)) * 4},
+      {&m->Rmid[1], size_t(std::max<int64_t>(pl.mid, 1)) * 4},
+      {&m->leaves, size_t(std::max<int64_t>(pl.nleaf, 1)) * kStateBytes},
+      {&m->Rleaf, size_t(std::max<int64_t>(pl.nleaf, 1)) * 4},
+      {&m->maxq_leaf, size_t(std::max<int64_t>(pl.nleaf, 1)) * 4},
+      {&m->nodeA_leaf, size_t(std::max<int64_t>(pl.nleaf, 1))},
+      {&m->V, size_t(pl.n) * As * 4},
+      {&m->act, size_t(pl.n) * 4},
+      {&m->val, size_t(pl.n) * As * 4},
+  };
+  for (auto &x : need) {
+    const int rc = c->ensure(*x.b, x.bytes);  // bumps the context's buffer generation when it moves
+    if (rc != BCTS_OK) return rc;
+  }
+  const size_t host_bytes = size_t(pl.n) * (kStateBytes + 4 + As * 4) + 64;
+  if (host_bytes > m->host.cap) {
+    const int rc = c->ensure_host(m->host, host_bytes);
+    if (rc != BCTS_OK) return rc;
+    c->buf_generation++;
+  }
+  return BCTS_OK;
+}
+
+// Every device step of one pass, in stream order (capturable: no allocation,
+// no synchronisation).  Inputs are in the pinned staging area.
+static int mixed_enqueue(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_t st) {
+  const int As = c->A_create;
+  char *hs = static_cast<char *>(m->host.p);
+  const size_t in_b = size_t(pl.n) * kStateBytes;
+  int rc;
+  BCTS_CUDA_TRY(cudaMemcpyAsync(m->roots.p, hs, in_b, cudaMemcpyHostToDevice, st), c->err);
+  const bcts_state *roots = static_cast<const bcts_state *>(m->roots.p);
+  float *q0 = static_cast<float *>(m->q0.p);
+  c->A = As;
+  // root evaluation over all roots (all As columns; each root reads its first A)
+  if ((rc = c->eval_nodes(roots, pl.n, q0, nullptr, st)) != BCTS_OK) return rc;
+  bcts_state *L1 = static_cast<bcts_state *>(m->L1.p);
+  float *r1 = static_cast<float *>(m->r1.p);
+  uint8_t *nA1 = static_cast<uint8_t *>(m->nodeA1.p);
+  for (const MixedGroup &g : pl.groups) {
+    if (g.d < 1) continue;
+    if ((rc = launch_expand(roots + g.root_off, nullptr, g.n, g.A, 1.f, L1 + g.l1_off, r1 + g.l1_off, nullptr,
+                            st)) != BCTS_OK)
+      return c->fail(rc, "expand launch failed");
+    BCTS_CUDA_TRY(cudaMemsetAsync(nA1 + g.l1_off, g.A, size_t(g.n) * g.A, st), c->err);
+  }
+  float *maxq1 = static_cast<float *>(m->maxq1.p);
+  if (pl.n1 > 0 && (rc = c->eval_nodes(L1, pl.n1, nullptr, maxq1, st, nA1)) != BCTS_OK) return rc;
+  bcts_state *leaves = static_cast<bcts_state *>(m->leaves.p);
+  float *Rleaf = static_cast<float *>(m->Rleaf.p);
+  uint8_t *nAl = static_cast<uint8_t *>(m->nodeA_leaf.p);
+  for (const MixedGroup &g : pl.groups) {
+    if (g.d < 2) continue;
+    const bcts_state *cur = L1 + g.l1_off;
+    const float *curR = r1 + g.l1_off;
+    int64_t cnt = int64_t(g.n) * g.A;
+    double gp = 1.0;
+    for (int i = 1; i < g.d; ++i) {
+      gp *= double(c->gamma);
+      const bool last = i == g.d - 1;
+      bcts_state *nxt = last ? leaves + g.leaf_off : static_cast<bcts_state *>(m->mid[i & 1].p);
+      float *nxtR = last ? Rleaf + g.leaf_off : static_cast<float *>(m->Rmid[i & 1].p);
+      if ((rc = launch_expand(cur, curR, cnt, g.A, float(gp), nxt, nxtR, nullptr, st)) != BCTS_OK)
+        return c->fail(rc, "expand launch failed");
+      cur = nxt;
+      curR = nxtR;
+      cnt *= g.A;
+    }
+    BCTS_CUDA_TRY(cudaMemsetAsync(nAl + g.leaf_off, g.A, size_t(g.nleaf), st), c->err);
+  }
+  float *maxq_leaf = static_cast<float *>(m->maxq_leaf.p);
+  if (pl.nleaf > 0 && (rc = c->eval_nodes(leaves, pl.nleaf, nullptr, maxq_leaf, st, nAl)) != BCTS_OK) return rc;
+  // backup per group
+  float *V = static_cast<float *>(m->V.p);
+  int32_t *act = static_cast<int32_t *>(m->act.p);
+  float *val = static_cast<float *>(m->val.p);
+  for (const MixedGroup &g : pl.groups) {
+    const float *gq0 = q0 + size_t(g.root_off) * As;
+    int32_t *gact = act + g.root_off;
+    float *gval = val + size_t(g.root_off) * As;
+    if (g.d == 0) {
+      if ((rc = launch_finalize(gq0, nullptr, nullptr, nullptr, g.n, g.A, 0, As, c->gamma, 1.f, c->corr, gact, gval,
+                                st, As)) != BCTS_OK)
+        return c->fail(rc, "finalize launch failed");
+      continue;
+    }
+    double gd = 1.0;
+    for (int i = 0; i < g.d; ++i) gd *= double(c->gamma);
+    const float *lR = g.d == 1 ? r1 + g.l1_off : Rleaf + g.leaf_off;
+    const float *lM = g.d == 1 ? maxq1 + g.l1_off : maxq_leaf + g.leaf_off;
+    float *gV = V + size_t(g.root_off) * As;  // [n_g][A_g] inside the group's rows
+    if ((rc = launch_segment_max(lR, lM, int64_t(g.n) * g.A, ipow(g.A, g.d - 1), float(gd), gV, st)) != BCTS_OK)
+      return c->fail(rc, "backup launch failed");
+    if ((rc = launch_finalize(gq0, maxq1 + g.l1_off, r1 + g.l1_off, gV, g.n, g.A, g.d, As, c->gamma, float(gd),
+                              c->corr, gact, gval, st, As)) != BCTS_OK)
+      return c->fail(rc, "finalize launch failed");
+  }
+  BCTS_CUDA_TRY(cudaMemcpyAsync(hs + in_b, act, size_t(pl.n) * 4, cudaMemcpyDeviceToHost, st), c->err);
+  BCTS_CUDA_TRY(
+      cudaMemcpyAsync(hs + in_b + size_t(pl.n) * 4, val, size_t(pl.n) * As * 4, cudaMemcpyDeviceToHost, st),
+      c->err);
+  return BCTS_OK;
+}
+
+static void load_tune(MixedState *m) {
+  m->tune_loaded = true;
+  const std::string f = tune_file();
+  if (f.empty()) return;
+  std::ifstream in(f);
+  std::string line;
+  while (std::getline(in, line)) {  // lines: "<precision>:<bucket> <chunk>" (one JSON-free record per line)
+    std::istringstream ss(line);
+    std::string k;
+    int64_t v;
+    if (ss >> k >> v) m->tuned_chunk[k] = v;
+  }
+}
+
+static void save_tune(MixedState *m) {
+  const std::string f = tune_file();
+  if (f.empty()) return;
+  std::ofstream out(f);
+  for (auto &kv : m->tuned_chunk) out << kv.first << " " << kv.second << "\n";
+}
+
+// Pick the union-leaf chunk for this bucket by timing the candidates on the
+// plan's own leaves (first pass of a new bucket only).
+static int autotune_chunk(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_t st) {
+  if (c->opt.leaf_chunk > 0 || pl.nleaf < 65536 || c->precision == BCTS_PREC_FP32_SIMT) return BCTS_OK;
+  if (!m->tune_loaded) load_tune(m);
+  const std::string key = std::to_string(c->precision) + ":" + std::to_string(leaf_bucket(pl.nleaf));
+  auto it = m->tuned_chunk.find(key);
+  if (it != m->tuned_chunk.end()) {
+    c->chunk_override = it->second;
+    return BCTS_OK;
+  }
+  const int64_t cands[] = {16384, 32768, 65536};
+  float best_ms = 1e30f;
+  int64_t best = 32768;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int rc = BCTS_OK;
+  for (int64_t cand : cands) {
+    c->chunk_override = cand;
+    // warm (sizes the scratch), then time
+    for (int rep = 0; rep < 2 && rc == BCTS_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      rc = c->eval_nodes(static_cast<bcts_state *>(m->leaves.p), pl.nleaf, nullptr,
+                         static_cast<float *>(m->maxq_leaf.p), st, static_cast<uint8_t *>(m->nodeA_leaf.p));
+      cudaEventRecord(e1, st);
+    }
+    if (rc != BCTS_OK) break;
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cand;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != BCTS_OK) return rc;
+  c->chunk_override = best;
+  m->tuned_chunk[key] = best;
+  save_tune(m);
+  return BCTS_OK;
+}
+
+int Ctx::run_mixed(const bcts_state *, const bcts_state *h_roots, const int32_t *depths, const int32_t *actions,
+                   int n, int32_t *, float *) {
+  const int As = A_create;
+  for (int i = 0; i < n; ++i)
+    if (depths[i] < 0 || depths[i] > kMaxDepth || actions[i] < 1 || actions[i] > As)
+      return fail(BCTS_EINVAL, "bcts_search_mixed: root " + std::to_string(i) + " has depth or A out of range");
+  if (!mixed) mixed = new MixedState();
+  MixedState *m = mixed;
+  // plan: sort roots by (A, d)
+  MixedPlan pl;
+  pl.n = n;
+  pl.order.resize(n);
+  for (int i = 0; i < n; ++i) pl.order[i] = i;
+  std::stable_sort(pl.order.begin(), pl.order.end(), [&](int a, int b) {
+    return actions[a] != actions[b] ? actions[a] < actions[b] : depths[a] < depths[b];
+  });
+  std::ostringstream key;
+  for (int i = 0; i < n;) {
+    MixedGroup g;
+    g.A = actions[pl.order[i]];
+    g.d = depths[pl.order[i]];
+    g.root_off = i;
+    int j = i;
+    while (j < n && actions[pl.order[j]] == g.A && depths[pl.order[j]] == g.d) ++j;
+    g.n = j - i;
+    g.l1_off = pl.n1;
+    if (g.d >= 1) pl.n1 += int64_t(g.n) * g.A;
+    if (g.d >= 2) {
+      g.nleaf = int64_t(g.n) * ipow(g.A, g.d);
+      g.leaf_off = pl.nleaf;
+      pl.nleaf += g.nleaf;
+      if (g.d >= 3) pl.mid = std::max<int64_t>(pl.mid, int64_t(g.n) * ipow(g.A, g.d - 1));
+    }
+    if (pl.nleaf > 0x7FFFFFFFLL) return fail(BCTS_EINVAL, "batched search too large: more than 2^31 - 1 leaves");
+    key << g.A << "x" << g.d << "x" << g.n << ";";
+    pl.groups.push_back(g);
+    i = j;
+  }
+  key << "p" << precision;
+  pl.key = key.str();
+  int rc;
+  if ((rc = mixed_ensure(this, m, pl)) != BCTS_OK) return rc;
+  char *hs = static_cast<char *>(m->host.p);
+  for (int i = 0; i < n; ++i) std::memcpy(hs + size_t(i) * kStateBytes, h_roots + pl.order[i], kStateBytes);
+  if ((rc = autotune_chunk(this, m, pl, stream)) != BCTS_OK) return rc;
+  const int times_seen = m->seen[pl.key]++;
+  auto git = m->graphs.find(pl.key);
+  if (git != m->graphs.end() && git->second.generation == buf_generation && git->second.exec) {
+    BCTS_CUDA_TRY(cudaGraphLaunch(git->second.exec, stream), err);
+    profiler_add(prof, git->second.launches);
+  } else if (times_seen >= 1) {
+    // second pass of this composition: capture it, then replay from now on
+    if (git != m->graphs.end() && git->second.exec) {
+      cudaGraphExecDestroy(git->second.exec);
+      m->graphs.erase(git);
+    }
+    Profiler *counter = profiler_create();
+    cudaGraph_t graph = nullptr;
+    BCTS_CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), err);
+    int64_t launches = 0;
+    {
+      ProfilerGuard pg(counter);  // counts launches, records no events
+      rc = mixed_enqueue(this, m, pl, stream);
+      launches = profiler_total(counter);
+    }
+    const cudaError_t ce = cudaStreamEndCapture(stream, &graph);
+    profiler_destroy(counter);
+    if (rc != BCTS_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc != BCTS_OK ? rc : fail(BCTS_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(ce));
+    }
+    GraphEntry e;
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      return fail(BCTS_ECUDA, std::string("graph instantiate failed: ") + cudaGetErrorString(ie));
+    }
+    e.launches = launches;
+    e.generation = buf_generation;
+    m->graphs[pl.key] = e;
+    BCTS_CUDA_TRY(cudaGraphLaunch(e.exec, stream), err);
+    profiler_add(prof, launches);
+  } else {
+    ProfilerGuard pg(prof);
+    if ((rc = mixed_enqueue(this, m, pl, stream)) != BCTS_OK) return rc;
+  }
+  return BCTS_OK;
+}
+
+// Host part of the batched form: results come back in sorted order; scatter.
+int Ctx::mixed_results(const int32_t *depths, const int32_t *actions, int n, int32_t *out_action,
+                       float *out_values) {
+  (void)depths;
+  (void)actions;
+  MixedState *m = mixed;
+  const int As = A_create;
+  // the same stable order the plan used
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return actions[a] != actions[b] ? actions[a] < actions[b] : depths[a] < depths[b];
+  });
+  const char *hs = static_cast<const char *>(m->host.p);
+  const int32_t *hact = reinterpret_cast<const int32_t *>(hs + size_t(n) * kStateBytes);
+  const float *hval = reinterpret_cast<const float *>(hs + size_t(n) * kStateBytes + size_t(n) * 4);
+  for (int i = 0; i < n; ++i) {
+    out_action[order[i]] = hact[i];
+    std::memcpy(out_values + size_t(order[i]) * As, hval + size_t(i) * As, size_t(As) * 4);
+  }
+  return BCTS_OK;
+}
+
 }  // namespace bcts
 
-extern "C" int bcts_search_mixed(bcts_ctx *, const bcts_state *, const int32_t *, const int32_t *, int, int32_t *,
-                                 float *) {
-  return BCTS_ENOKERNEL;
+extern "C" int bcts_search_mixed(bcts_ctx *ctx, const bcts_state *roots, const int32_t *depths,
+                                 const int32_t *actions, int n, int32_t *out_action, float *out_values) {
+  if (!ctx) return BCTS_EINVAL;
+  bcts::Ctx *c = reinterpret_cast<bcts::Ctx *>(ctx);
+  if (n < 0 || (n > 0 && (!roots || !depths || !actions || !out_action || !out_values)))
+    return c->fail(BCTS_EINVAL, "bcts_search_mixed: invalid argument");
+  if (n == 0) return BCTS_OK;
+  int rc = c->run_mixed(nullptr, roots, depths, actions, n, nullptr, nullptr);
+  if (rc != BCTS_OK) {
+    cudaStreamSynchronize(c->stream);
+    c->chunk_override = 0;
+    return rc;
+  }
+  int herr = 0;
+  BCTS_CUDA_TRY(cudaStreamSynchronize(c->stream), c->err);
+  BCTS_CUDA_TRY(cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), c->err);
+  c->chunk_override = 0;
+  if (herr != 0) {
+    cudaMemset(c->d_err, 0, sizeof(int));
+    return c->fail(BCTS_EDEVICE, "a kernel reported error code " + std::to_string(herr));
+  }
+  return c->mixed_results(depths, actions, n, out_action, out_values);
 }

@@ -132,7 +132,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 // (first maximum on ties).
 __global__ void __launch_bounds__(256) fc2_max_kernel(const float *__restrict__ h, const float *__restrict__ W2,
                                                       const float *__restrict__ b2, int A, int64_t n,
-                                                      float *__restrict__ q, float *__restrict__ maxq) {
+                                                      float *__restrict__ q, float *__restrict__ maxq,
+                                                      const uint8_t *__restrict__ node_A) {
   __shared__ float w[kMaxA * kF1];
   for (int i = threadIdx.x; i < A * kF1; i += blockDim.x) w[i] = W2[i];
   __syncthreads();
@@ -149,6 +150,9 @@ __global__ void __launch_bounds__(256) fc2_max_kernel(const float *__restrict__ 
     x[4 * j + 2] = t.z;
     x[4 * j + 3] = t.w;
   }
+  // node_A (batched form): this node's own action count; the max runs over its
+  // first node_A[node] actions (q still receives all A columns)
+  const int An = node_A ? int(node_A[node]) : A;
   float best = 0.f;
   for (int a = 0; a < A; ++a) {
     const float *wa = w + a * kF1;
@@ -165,7 +169,7 @@ __global__ void __launch_bounds__(256) fc2_max_kernel(const float *__restrict__ 
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     s += __ldg(b2 + a);
     if (q && lane == 0) q[node * A + a] = s;
-    if (a == 0 || s > best) best = s;
+    if (a < An && (a == 0 || s > best)) best = s;
   }
   if (maxq && lane == 0) maxq[node] = best;
 }
@@ -188,7 +192,7 @@ size_t simt_scratch_bytes(int64_t chunk) {
 }
 
 int simt_qnet_forward(const SimtWeights &w, const uint8_t *frames, int64_t n, float *q, float *maxq,
-                      void *scratch, cudaStream_t st) {
+                      void *scratch, cudaStream_t st, const uint8_t *node_A) {
   if (n <= 0) return BCTS_OK;
   float *a1 = static_cast<float *>(scratch);
   float *a2 = a1 + size_t(n) * kP1 * kC1;
@@ -199,15 +203,15 @@ int simt_qnet_forward(const SimtWeights &w, const uint8_t *frames, int64_t n, fl
   if ((rc = run_gemm<GeoConv2, 128, 64, 8, 4>(K_CONV2, a1, w.c2w, w.c2b, a2, n, st)) != BCTS_OK) return rc;
   if ((rc = run_gemm<GeoConv3, 128, 64, 8, 4>(K_CONV3, a2, w.c3w, w.c3b, a3, n, st)) != BCTS_OK) return rc;
   if ((rc = run_gemm<GeoFc1, 128, 64, 8, 4>(K_FC1, a3, w.f1w, w.f1b, a4, n, st)) != BCTS_OK) return rc;
-  return launch_fc2_max(a4, w.f2w, w.f2b, w.A, n, q, maxq, st);
+  return launch_fc2_max(a4, w.f2w, w.f2b, w.A, n, q, maxq, st, node_A);
 }
 
 int launch_fc2_max(const float *h, const float *W2, const float *b2, int A, int64_t n, float *q, float *maxq,
-                   cudaStream_t st) {
+                   cudaStream_t st, const uint8_t *node_A) {
   if (n <= 0) return BCTS_OK;
   const int warps = 8;
   ProfScope ps(K_FC2, st);
-  fc2_max_kernel<<<unsigned((n + warps - 1) / warps), warps * 32, 0, st>>>(h, W2, b2, A, n, q, maxq);
+  fc2_max_kernel<<<unsigned((n + warps - 1) / warps), warps * 32, 0, st>>>(h, W2, b2, A, n, q, maxq, node_A);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 

@@ -816,7 +816,7 @@ void tc_weights_destroy(TcWeights *w) {
 namespace {
 template <bool SPLIT>
 int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n,
-                    float *q, float *maxq, void *scratch, cudaStream_t st, int *d_err) {
+                    float *q, float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A) {
   const size_t lo = SPLIT ? 2 : 1;
   uint8_t *s = static_cast<uint8_t *>(scratch);
   auto take = [&](size_t bytes) {
@@ -873,16 +873,16 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
   p.out_hi = h;
   p.out_lo = nullptr;
   if ((rc = tc::launch<4, SPLIT, false>(p, (long long)n, K_FC1, st)) != BCTS_OK) return rc;
-  return launch_fc2_max(h, w->f2w, w->f2b, A, n, q, maxq, st);
+  return launch_fc2_max(h, w->f2w, w->f2b, A, n, q, maxq, st, node_A);
 }
 }  // namespace
 
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
-                    float *maxq, void *scratch, cudaStream_t st, int *d_err) {
+                    float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A) {
   if (n <= 0) return BCTS_OK;
   if (w->precision == BCTS_PREC_FP32)
-    return tc_forward_impl<true>(w, A, frames, states, n, q, maxq, scratch, st, d_err);
-  return tc_forward_impl<false>(w, A, frames, states, n, q, maxq, scratch, st, d_err);
+    return tc_forward_impl<true>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A);
+  return tc_forward_impl<false>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A);
 }
 
 }  // namespace bcts

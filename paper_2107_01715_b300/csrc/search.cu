@@ -56,10 +56,10 @@ __global__ void __launch_bounds__(128) segment_max_kernel(const float *__restric
 __global__ void finalize_kernel(const float *__restrict__ q0, const float *__restrict__ maxq1,
                                 const float *__restrict__ r1, const float *__restrict__ V, int n, int A,
                                 int depth, int A_stride, float gamma, float gamma_d, float corr,
-                                int32_t *__restrict__ action, float *__restrict__ values) {
+                                int32_t *__restrict__ action, float *__restrict__ values, int q_stride) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float *q = q0 + size_t(i) * A;
+  const float *q = q0 + size_t(i) * q_stride;
   int pi_o = 0;
   for (int a = 1; a < A; ++a)
     if (q[a] > q[pi_o]) pi_o = a;
@@ -108,11 +108,12 @@ int launch_segment_max(const float *R, const float *maxq, int64_t n_seg, int64_t
 
 int launch_finalize(const float *q0, const float *maxq1, const float *r1, const float *V, int n, int A, int depth,
                     int A_stride, float gamma, float gamma_d, float corr, int32_t *action, float *values,
-                    cudaStream_t st) {
+                    cudaStream_t st, int q_stride) {
   if (n <= 0) return BCTS_OK;
   ProfScope ps(K_BACKUP, st);
   finalize_kernel<<<unsigned((n + 127) / 128), 128, 0, st>>>(q0, maxq1, r1, V, n, A, depth, A_stride, gamma,
-                                                              gamma_d, corr, action, values);
+                                                              gamma_d, corr, action, values,
+                                                              q_stride > 0 ? q_stride : A);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 
@@ -134,6 +135,7 @@ int Ctx::ensure(DevBuf &b, size_t bytes) {
     b.cap = 0;
   }
   const size_t want = (bytes + 255) & ~size_t(255);
+  ++buf_generation;
   if (cudaMalloc(&b.p, want) != cudaSuccess) {
     cudaGetLastError();
     return fail(BCTS_ENOMEM, "device allocation of " + std::to_string(want) + " bytes failed");
@@ -161,18 +163,20 @@ int Ctx::ensure_host(HostBuf &b, size_t bytes) {
 
 int64_t Ctx::chunk_nodes() const {
   if (opt.leaf_chunk > 0) return opt.leaf_chunk;
+  if (chunk_override > 0) return chunk_override;
   return precision == BCTS_PREC_FP32_SIMT ? 16384 : 32768;
 }
 
 // Score `count` nodes: render + Q-network, chunked.  q (count x A) and maxq
 // (count) may each be NULL.
-int Ctx::eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st) {
+int Ctx::eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st,
+                    const uint8_t *node_A) {
   const int64_t chunk = chunk_nodes();
   int rc;
   for (int64_t off = 0; off < count; off += chunk) {
     const int64_t cnt = count - off < chunk ? count - off : chunk;
-    if ((rc = qnet_nodes(states + off, nullptr, cnt, q ? q + off * A : nullptr, maxq ? maxq + off : nullptr,
-                         st)) != BCTS_OK)
+    if ((rc = qnet_nodes(states + off, nullptr, cnt, q ? q + off * A : nullptr, maxq ? maxq + off : nullptr, st,
+                         node_A ? node_A + off : nullptr)) != BCTS_OK)
       return rc;
   }
   return BCTS_OK;
@@ -181,7 +185,7 @@ int Ctx::eval_nodes(const bcts_state *states, int64_t count, float *q, float *ma
 // Q-network on at most one chunk of nodes, given either states (rendered here)
 // or frames.
 int Ctx::qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
-                    cudaStream_t st) {
+                    cudaStream_t st, const uint8_t *node_A) {
   int rc;
   if (precision == BCTS_PREC_FP32_SIMT) {
     if (states) {
@@ -193,7 +197,7 @@ int Ctx::qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt
     if ((rc = ensure(scratch_buf, simt_scratch_bytes(cnt))) != BCTS_OK) return rc;
     SimtWeights w = simt;
     w.A = A;  // FC2 rows 0..A-1
-    if ((rc = simt_qnet_forward(w, frames, cnt, q, maxq, scratch_buf.p, st)) != BCTS_OK)
+    if ((rc = simt_qnet_forward(w, frames, cnt, q, maxq, scratch_buf.p, st, node_A)) != BCTS_OK)
       return fail(rc, "Q-network launch failed");
     return BCTS_OK;
   }
@@ -205,7 +209,7 @@ int Ctx::qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt
     states = nullptr;
   }
   if ((rc = ensure(scratch_buf, tc_scratch_bytes(cnt, precision))) != BCTS_OK) return rc;
-  rc = tc_qnet_forward(tc, A, frames, states, cnt, q, maxq, scratch_buf.p, st, d_err);
+  rc = tc_qnet_forward(tc, A, frames, states, cnt, q, maxq, scratch_buf.p, st, d_err, node_A);
   if (rc != BCTS_OK) return fail(rc, "tensor-core Q-network launch failed");
   return BCTS_OK;
 }
@@ -307,7 +311,8 @@ Ctx::~Ctx() {
     if (b->p) cudaFree(b->p);
   if (host_stage.p) cudaFreeHost(host_stage.p);
   if (d_err) cudaFree(d_err);
-  if (tc) tc_weights_destroy(tc);
+  if (mixed) mixed_destroy(mixed);
+  if (tc && owns_weights) tc_weights_destroy(tc);
   if (prof) profiler_destroy(prof);
   if (stream) cudaStreamDestroy(stream);
 }
@@ -474,11 +479,9 @@ int Ctx::search_host(const bcts_state *roots, int n, const int32_t *depths, cons
   const bcts_state *dr = static_cast<const bcts_state *>(io_roots.p);
   int32_t *da = static_cast<int32_t *>(io_action.p);
   float *dv = static_cast<float *>(io_values.p);
-  if (!depths) {
-    rc = run_search(dr, n, As, d, da, dv, As, stream);
-  } else {
-    rc = run_mixed(dr, roots, depths, actions, n, da, dv);
-  }
+  (void)depths;
+  (void)actions;
+  rc = run_search(dr, n, As, d, da, dv, As, stream);
   if (rc != BCTS_OK) {
     cudaStreamSynchronize(stream);
     return rc;

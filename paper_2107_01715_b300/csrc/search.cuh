@@ -18,6 +18,7 @@ struct HostBuf {
 };
 
 struct ServeState;  // serve.cu
+struct MixedState;  // mixed.cu
 
 struct Ctx {
   int device = 0;
@@ -34,6 +35,7 @@ struct Ctx {
   SimtWeights simt{};
   TcWeights *tc = nullptr;
   bool tc_fused_render = false;
+  bool owns_weights = true;  // serving workers share their owner's weights
   int *d_err = nullptr;
 
   DevBuf simt_w, frames_buf, scratch_buf, q0_buf, maxq1_buf, V_buf, r1_buf, leafmax_buf;
@@ -42,26 +44,34 @@ struct Ctx {
   HostBuf host_stage;
 
   ServeState *serve = nullptr;
+  MixedState *mixed = nullptr;
   Profiler *prof = nullptr;
+  int64_t chunk_override = 0;    // leaf chunk chosen by the batched form's autotuner
+  uint64_t buf_generation = 1;   // bumped whenever a device buffer moves
 
   ~Ctx();
   int fail(int code, const std::string &msg);
   int ensure(DevBuf &b, size_t bytes);
   int ensure_host(HostBuf &b, size_t bytes);
   int64_t chunk_nodes() const;
-  int eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st);
+  int eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st,
+                 const uint8_t *node_A = nullptr);
   int qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
-                 cudaStream_t st);
+                 cudaStream_t st, const uint8_t *node_A = nullptr);
   int run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d_action, float *d_values,
                  int A_stride, cudaStream_t st);
   int run_mixed(const bcts_state *d_roots, const bcts_state *h_roots, const int32_t *depths,
                 const int32_t *actions, int n, int32_t *d_action, float *d_values);
   int search_host(const bcts_state *roots, int n, const int32_t *depths, const int32_t *actions,
                   int32_t *out_action, float *out_values);
+  int mixed_results(const int32_t *depths, const int32_t *actions, int n, int32_t *out_action, float *out_values);
 };
 
 void serve_shutdown(Ctx *c);
 Profiler *profiler_create();
 void profiler_destroy(Profiler *p);
+int64_t profiler_total(const Profiler *p);
+void profiler_add(Profiler *p, int64_t launches);
+void mixed_destroy(MixedState *m);
 
 }  // namespace bcts

@@ -74,3 +74,24 @@ def test_create_rejects_bad_arguments_without_cuda(binding):
 def test_binding_refuses_wrong_weight_count(binding):
     with pytest.raises(ValueError):
         binding.bcts_create(np.zeros(10, dtype=np.float32), 6, 2, 0.99, 1.0)
+
+
+def test_host_env_step_matches_oracle(binding, oracle_lib):
+    """The library's host-side step (used to advance served episodes) equals the
+    oracle's step bit for bit, rewards included."""
+    from paper_2107_01715_b300 import inputs
+    states = inputs.root_states(range(300, 340))
+    pos = states["pos"]
+    for i in range(0, 40, 3):  # put agents next to objects so that contacts happen
+        pos[i, 3, 0] = np.clip(pos[i, 3, 1] - np.array([1, 0], dtype=np.int16), 0, 20)
+    states["pos"] = pos
+    hits = 0
+    for s in states:
+        for a in range(18):
+            ours, r1 = binding.bcts_env_step(s, a)
+            ref, r2 = oracle_lib.env_step(s, a)
+            assert ours.tobytes() == ref.tobytes() and r1 == r2
+            hits += r1 != 0
+    assert hits > 0
+    with pytest.raises(binding.BctsError):
+        binding.bcts_env_step(states[0], 18)
