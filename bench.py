@@ -44,6 +44,12 @@ WORKLOADS = {
                   name="plain Batch-BFS at Atari scale: 32 roots, |A|=18, d=3, FP32, correction on"),
     "precision": dict(n=8, A=18, d=4, gamma=0.99, c=1.0, precision="bf16",
                       name="precision form: 8 roots, |A|=18, d=4, leaf Q-net in reduced precision"),
+    "batched": dict(n=256, A=18, d=4, gamma=0.99, c=1.0, precision="bf16",
+                    name="batched form: 256 roots, d uniform in {1,2,3,4}, |A| in {4,9,18}, BF16, graph-replayed"),
+    "serving": dict(n=1024, A=18, d=4, gamma=0.99, c=1.0, precision="bf16", rate=2000.0, seconds=3.0,
+                    budget=120 << 30,
+                    name="serving form: Poisson requests from 1024 episodes, d in {2,3,4}, |A|=18, BF16, "
+                         "120 GB frame budget"),
 }
 # Per-leaf Nature-DQN multiply-accumulates (conv1, conv2, conv3, fc1, fc2 at A=18).
 MACS = {"conv1": 400 * 32 * 256, "conv2": 81 * 64 * 512, "conv3": 49 * 64 * 576, "fc1": 512 * 3136,
@@ -62,6 +68,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--roots", type=int, default=None, help="override the root count (smaller profiling cases)")
+    ap.add_argument("--rate", type=float, default=None, help="serving: mean request rate (req/s)")
+    ap.add_argument("--seconds", type=float, default=None, help="serving: length of the arrival stream (s)")
     return ap.parse_args()
 
 
@@ -318,6 +326,26 @@ def run_ours(args, wl):
     if not args.no_cpu_baseline:
         cb = cpu_baseline(W, wl)
 
+    precision_report = None
+    if args.workload == "precision" and precision != "fp32":
+        # reduced-precision leaf Q-network against the FP32-class run of the same roots
+        # (the FP32-class path is held to 1e-4 of the FP64 oracle by the tests)
+        fctx = bcts.bcts_create(W, A, d, wl["gamma"], wl["c"], precision="fp32")
+        a32, v32 = bcts.bcts_search(fctx, roots)
+        fctx.close()
+        a_lo, v_lo = bcts.bcts_search(ctx, roots)
+        err = np.abs(v_lo.astype(np.float64) - v32)
+        srt = np.sort(v32, axis=1)
+        margin = srt[:, -1] - srt[:, -2]
+        tol = float(err.max())
+        sure = margin > 2 * tol
+        precision_report = {"vs": "fp32-class run of the same roots",
+                            "max_abs_err": float(err.max()), "mean_abs_err": float(err.mean()),
+                            "action_agreement_all": float((a_lo == a32).mean()),
+                            "roots_with_margin_above_2x_err": int(sure.sum()),
+                            "action_agreement_where_margin_exceeds": (float((a_lo[sure] == a32[sure]).mean())
+                                                                      if sure.any() else None)}
+
     lat = sorted(step_ms)
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
@@ -344,10 +372,155 @@ def run_ours(args, wl):
         "plain_fp32": plain,
         "speedup_vs_plain_fp32": (value / plain["value"]) if plain else None,
         "cpu_baseline": cb,
+        "precision_report": precision_report,
         "clocks": clocks,
         "wall_s_timed": t_wall,
     }
     print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def _clock_line(clk, pk):
+    return clk.summary(pk.get("sm_max_mhz"))
+
+
+def run_batched(args, wl):
+    """Batched form: one bcts_search_mixed call per step over 256 mixed roots."""
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_2107_01715_b300 import bcts
+    precision = args.precision or wl["precision"]
+    W = inputs.qnet_weights(18, seed=1234)
+    ctx = bcts.bcts_create(W, 18, 4, wl["gamma"], wl["c"], precision=precision)
+    roots, ds, As = inputs.mixed_roots(wl["n"], seed=7 + rank)
+    leaves = int(sum(int(a) ** int(d) for a, d in zip(As, ds)))
+    for _ in range(args.warmup):
+        bcts.bcts_search_mixed(ctx, roots, ds, As)  # eager, captured, then replayed
+    bcts.bcts_profile(ctx, False)
+    pk, _ = peaks()
+    barrier(world)
+    with ClockSampler(local) as clk:
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            bcts.bcts_search_mixed(ctx, roots, ds, As)
+            times.append(time.perf_counter() - t0)
+    _, _, launches = bcts.bcts_profile(ctx, False)
+    total = max_over_ranks(world, sum(times), torch.device("cuda", local))
+    if rank == 0:
+        lat = sorted(times)
+        line = {"metric": METRIC, "value": world * leaves * args.steps / total, "unit": "leaf nodes/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": precision, "data": "synthetic",
+                "config": {"workload": wl["name"], "roots_per_step": wl["n"], "leaves_per_step": leaves,
+                           "depth_hist": {str(k): int((ds == k).sum()) for k in (1, 2, 3, 4)},
+                           "A_hist": {str(k): int((As == k).sum()) for k in (4, 9, 18)},
+                           "l2": f"{leaves} leaves per step, working set far above the 126 MB L2"},
+                "decisions_per_s": world * wl["n"] * args.steps / total,
+                "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[-1],
+                               "what": "one bcts_search_mixed call of the 256-root batch, host wall clock"},
+                "e2e": {"value": world * leaves * args.steps / total, "unit": "leaf nodes/s",
+                        "h2d_bytes_per_step": wl["n"] * 80, "d2h_bytes_per_step": wl["n"] * (4 + 18 * 4)},
+                "gpu_launches": launches, "clocks": _clock_line(clk, pk)}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_serving(args, wl):
+    """Serving form: Poisson arrivals from simulated episodes through bcts_submit /
+    bcts_poll; episodes advance by the returned action (bcts_env_step)."""
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_2107_01715_b300 import bcts
+    precision = args.precision or wl["precision"]
+    rate = args.rate or wl["rate"]
+    seconds = args.seconds or wl["seconds"]
+    A = 18
+    W = inputs.qnet_weights(A, seed=1234)
+    ctx = bcts.bcts_create(W, A, 4, wl["gamma"], wl["c"], precision=precision,
+                           frame_budget_bytes=wl["budget"], max_roots=64)
+    episodes = inputs.root_states(range(10000 + rank * wl["n"], 10000 + rank * wl["n"] + wl["n"]))
+    g = inputs.splitmix64(4242 + rank)
+
+    def uniform():
+        return (next(g) >> 11) / float(1 << 53)
+
+    # warm-up: every depth once (graphs, autotuner, lazy buffers)
+    for d in (2, 3, 4):
+        t = bcts.bcts_submit(ctx, episodes[:1], d, A)
+        bcts.bcts_poll(ctx, t, A, timeout_us=-1)
+    busy = set()
+    pending = {}  # ticket -> (episode, submit time)
+    lat, done_leaves, completed = [], 0, 0
+    t0 = time.perf_counter()
+    next_arrival = t0
+    pk, _ = peaks()
+    barrier(world)
+    with ClockSampler(local) as clk:
+        while True:
+            now = time.perf_counter()
+            while next_arrival <= now and next_arrival - t0 < seconds:
+                e = int(next(g) % wl["n"])
+                while e in busy:
+                    e = (e + 1) % wl["n"]
+                d = (2, 3, 4)[next(g) % 3]
+                tk = bcts.bcts_submit(ctx, episodes[e:e + 1], d, A)
+                pending[tk] = (e, next_arrival, d)
+                busy.add(e)
+                next_arrival += -np.log(1.0 - uniform()) / rate
+            # passes complete roughly in arrival order: poll the oldest tickets and
+            # stop after a run of still-pending ones
+            misses = 0
+            for tk in list(pending):
+                rc, a, _ = bcts.bcts_poll(ctx, tk, A, timeout_us=0)
+                if rc == bcts.BCTS_OK:
+                    e, ts, d = pending.pop(tk)
+                    lat.append(time.perf_counter() - ts)
+                    done_leaves += A ** d
+                    completed += 1
+                    episodes[e], _ = bcts.bcts_env_step(episodes[e], a)
+                    busy.discard(e)
+                else:
+                    misses += 1
+                    if misses >= 192:
+                        break
+            if next_arrival - t0 >= seconds and not pending:
+                break
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+    # plain FP32 sequential baseline on a bounded sample of the same kind of requests
+    pctx = bcts.bcts_create(W, A, 4, wl["gamma"], wl["c"], precision="fp32_simt")
+    seq_roots = inputs.root_states(range(20000, 20012))
+    tseq0 = time.perf_counter()
+    seq_leaves = 0
+    for i in range(len(seq_roots)):
+        d = (2, 3, 4)[i % 3]
+        bcts.bcts_search_mixed(pctx, seq_roots[i:i + 1], np.array([d], np.int32), np.array([A], np.int32))
+        seq_leaves += A ** d
+    tseq = time.perf_counter() - tseq0
+    pctx.close()
+    lat.sort()
+    if rank == 0:
+        line = {"metric": METRIC, "value": completed / wall, "unit": "decisions/s", "n_gpus": world,
+                "steps": completed, "warmup": 3, "ms_per_step": 1e3 * wall / max(completed, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": precision,
+                "data": "synthetic",
+                "config": {"workload": wl["name"], "offered_rate_req_s": rate, "arrival_seconds": seconds,
+                           "episodes": wl["n"]},
+                "leaf_nodes_per_s": done_leaves / wall,
+                "latency_ms": {"p50": 1e3 * lat[len(lat) // 2] if lat else None,
+                               "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
+                               "what": "submit to completion seen by the poller, host wall clock"},
+                "plain_fp32_sequential": {"decisions_per_s": len(seq_roots) / tseq,
+                                          "leaf_nodes_per_s": seq_leaves / tseq,
+                                          "how": "one request at a time, FP32 CUDA-core Q-network, d cycling 2,3,4"},
+                "e2e": {"value": completed / wall, "unit": "decisions/s", "h2d_bytes_per_step": 80,
+                        "d2h_bytes_per_step": 4 + A * 4},
+                "gpu_launches": None, "clocks": _clock_line(clk, pk)}
+        print(json.dumps(line), flush=True)
     ctx.close()
 
 
@@ -359,6 +532,10 @@ def main():
         wl["name"] += f" [reduced to {args.roots} roots]"
     if args.impl == "reference":
         run_reference(args, wl)
+    elif args.workload == "batched":
+        run_batched(args, wl)
+    elif args.workload == "serving":
+        run_serving(args, wl)
     else:
         run_ours(args, wl)
 
