@@ -55,6 +55,15 @@ WORKLOADS = {
 MACS = {"conv1": 400 * 32 * 256, "conv2": 81 * 64 * 512, "conv3": 49 * 64 * 576, "fc1": 512 * 3136,
         "fc2": 18 * 512}
 L2_BYTES = 126 * 2 ** 20
+# DRAM bytes (read + write) per node of each tensor-core layer kernel, from the ncu
+# captures summarised in profiles/tc_gemm_layers_4roots_a18_d3.md (launches over
+# 23,328 leaves; traffic grows in proportion to the nodes a launch processes).
+# Algorithmic DRAM bytes per node of each layer (bf16 maps; x2 for the hi + lo maps of the
+# FP32-class mode): conv1 reads the 80-byte node state (frames are rendered on chip) and
+# writes its 400x32 map; later layers read the previous map once and write their own.
+ALG_BYTES_PER_NODE = {"conv1": (80, 400 * 32 * 2), "conv2": (400 * 32 * 2, 81 * 64 * 2),
+                      "conv3": (81 * 64 * 2, 49 * 64 * 2), "fc1": (49 * 64 * 2, 512 * 4)}
+TRAFFIC_PER_NODE = {'fp32/conv1': 48969.9, 'fp32/conv2': 70781.6, 'fp32/conv3': 31745.8, 'fp32/fc1': 14435.4, 'bf16/conv1': 23345.5, 'bf16/conv2': 34822.7, 'bf16/conv3': 15084.4, 'bf16/fc1': 7341.1}
 
 
 def parse():
@@ -293,8 +302,17 @@ def run_ours(args, wl):
             bound, unit = "tensor", "TFLOP/s"
             pnote = (f"bf16 dense sustained ({pk_kind}) / {mma_per_mac} bf16 MMAs per algorithmic MAC"
                      if mma_per_mac > 1 else f"bf16 dense sustained ({pk_kind})")
+        tpn = TRAFFIC_PER_NODE.get(f"{precision}/{dom}")
+        traffic = tpn * nodes / prof_cnt[dom] if tpn and prof_cnt[dom] else None
         roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                    "frac": achieved / peak, "traffic": None, "peak_note": pnote + " (of measured)",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "traffic_note": ("DRAM bytes per launch: per-node bytes from the ncu capture of "
+                                     "profiles/tc_gemm_layers_4roots_a18_d3.md x nodes per launch") if traffic else None,
+                    "algorithmic_bytes_per_launch": (
+                        (lambda rb, wb: ((rb if dom == "conv1" else rb * (2 if precision == "fp32" else 1)) +
+                                         (wb if dom == "fc1" else wb * (2 if precision == "fp32" else 1))))(
+                            *ALG_BYTES_PER_NODE[dom]) * nodes / prof_cnt[dom] if prof_cnt[dom] else None),
+                    "peak_note": pnote + " (of measured)",
                     "mma_per_mac": mma_per_mac,
                     "executed_frac_of_bf16_peak": (achieved * mma_per_mac / pk["bf16_tflops_sustained"]
                                                    if bound == "tensor" else None),
