@@ -36,7 +36,9 @@ int launch_fc2_max(const float *h, const float *W2, const float *b2, int A, int6
 // qnet_tc.cu (tensor-core paths)
 struct TcWeights;  // defined in qnet_tc.cu
 size_t tc_scratch_bytes(int64_t chunk, int precision);
-int tc_weights_create(const float *host_weights, int A, int precision, TcWeights **out, std::string &err);
+// act_scale: FP8 activation scales of the conv1/conv2/conv3 output maps (NULL otherwise).
+int tc_weights_create(const float *host_weights, int A, int precision, const float *act_scale, TcWeights **out,
+                      std::string &err);
 void tc_weights_destroy(TcWeights *w);
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
                     float *maxq, void *scratch, cudaStream_t stream, int *d_err, const uint8_t *node_A = nullptr);

@@ -27,7 +27,10 @@
 // word and an abort flag, every role leaves its loop, in-flight copies and MMAs
 // are drained and TMEM is freed before the kernel returns.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -85,6 +88,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -158,6 +170,28 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f8f6f4: E4M3 A and B, FP32 accumulator, K-major,
+// M = 128, N = n (K = 32 elements = 32 bytes per instruction).
+__host__ __device__ constexpr uint32_t idesc_e4m3(int n) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+}
+
+// 16 uint8 pixels (four little-endian words) -> 16 E4M3 codes (saturating,
+// round to nearest; the renderer's palette values are exact).
+__device__ __forceinline__ uint4 pixels16_to_e4m3(const uint32_t (&w)[4]) {
+  uint32_t o[4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    float f[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) f[b] = __uint_as_float(__byte_perm(w[h], 0x4B000000u, 0x7440u + b)) - 8388608.0f;
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(f[0], f[1]), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(f[2], f[3]), __NV_SATFINITE, __NV_E4M3);
+    o[h] = lo | (hi << 16);
+  }
+  return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
 // Byte offset of 16-byte chunk `ch` of row `r` in a 128-byte-swizzled tile.
 __device__ __forceinline__ uint32_t sw128_off(int r, int ch) {
   return uint32_t(r) * 128u + (uint32_t(ch ^ (r & 7)) << 4);
@@ -211,9 +245,17 @@ struct Geo<4> {
   static constexpr int BN = 256, KB = 49, P = 1, NTOT = 512, K = 3136;
 };
 
-template <int LAYER, bool SPLIT>
+// MODE 0: BF16 operands; 1: FP32-class split (bf16 hi + lo); 2: FP8 E4M3 operands
+// with per-output-channel weight scales and per-layer activation scales.
+// A K block is always 128 bytes: 64 bf16 or 128 E4M3 elements (FP8 pads K to a
+// whole block with zero weights).
+template <int LAYER, int MODE>
 struct Cfg {
   using G = Geo<LAYER>;
+  static constexpr bool SPLIT = MODE == 1, FP8 = MODE == 2;
+  static constexpr int EB = FP8 ? 1 : 2;              // bytes per element
+  static constexpr int KB = FP8 ? (G::K + 127) / 128 : G::K / 64;
+  static constexpr int KPAD = KB * (128 / EB);        // weight row length in elements
   static constexpr bool A_LO = SPLIT && LAYER != 1;  // conv1's integer pixels are exact in bf16
   static constexpr bool B_RES = LAYER == 1;          // conv1's weights (16 / 32 KB) stay in shared memory
   // Split mode stores the weight tile as [hi rows; lo rows] so that one MMA of
@@ -224,13 +266,13 @@ struct Cfg {
   static constexpr int B_ROWS = G::BN * (SPLIT ? 2 : 1);
   static constexpr int B_BYTES = G::BN * 128;            // one of hi / lo
   static constexpr int ACC_N = B_CAT ? 2 * G::BN : G::BN;  // accumulator columns per tile
-  static constexpr int RES_BYTES = B_RES ? G::KB * B_ROWS * 128 : 0;
+  static constexpr int RES_BYTES = B_RES ? KB * B_ROWS * 128 : 0;
   static constexpr int STAGE_BYTES = A_BYTES * (A_LO ? 2 : 1) + (B_RES ? 0 : B_ROWS * 128);
   static constexpr int STAGES_RAW = (192 * 1024 - RES_BYTES) / STAGE_BYTES;
-  static constexpr int STAGES = B_RES ? 2 * G::KB : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
+  static constexpr int STAGES = B_RES ? 2 * KB : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
   // fused conv1: re-zero lists (2 tiles x 4 slots x 256 threads) + node-state ring (2 tiles x 2 nodes)
   static constexpr int DIRTY_BYTES = B_RES ? 2 * 4 * 256 * 4 + 2 * 2 * 80 : 0;
-  static constexpr int SMEM = RES_BYTES + STAGES * STAGE_BYTES + 1024 + 256 + DIRTY_BYTES + G::NTOT * 4;
+  static constexpr int SMEM = RES_BYTES + STAGES * STAGE_BYTES + 1024 + 256 + DIRTY_BYTES + 2 * G::NTOT * 4;
   // as many accumulators (up to 4) as TMEM's 512 columns hold, so the MMAs run
   // ahead of the two epilogue warpgroups
   static constexpr int NUM_ACC = (4 * ACC_N <= 512) ? 4 : 2;
@@ -244,9 +286,11 @@ struct Cfg {
 struct GemmParams {
   const void *a_hi;  // bf16 activations, uint8 frames or node states
   const void *a_lo;  // bf16 activation remainders (split mode, layers 2-4)
-  const __nv_bfloat16 *b_hi;
-  const __nv_bfloat16 *b_lo;
+  const void *b_hi;  // weights [NTOT][KPAD], bf16 or E4M3
+  const void *b_lo;
   const float *bias;
+  const float *colscale;  // FP8: per-output-channel weight scale x input activation scale
+  float out_inv_scale;    // FP8: 1 / activation scale of this layer's output map
   void *out_hi;  // bf16 NHWC (layers 1-3) or FP32 [M][512] (layer 4)
   void *out_lo;  // bf16 remainders (split mode, layers 1-3)
   uint32_t M;  // rows, < 2^31 (checked by the launcher)
@@ -261,11 +305,13 @@ constexpr int kEpiWarp0 = 8;
 constexpr int kMmaWarp = 12;
 constexpr int kThreads = 32 * (kMmaWarp + 1);
 
-template <int LAYER, bool SPLIT, bool FUSED>
+template <int LAYER, int MODE, bool FUSED>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
-  using C = Cfg<LAYER, SPLIT>;
+  using C = Cfg<LAYER, MODE>;
   using G = Geo<LAYER>;
-  constexpr int BN = G::BN, KB = G::KB, S = C::STAGES;
+  constexpr bool SPLIT = C::SPLIT, FP8 = C::FP8;
+  constexpr int EB = C::EB;
+  constexpr int BN = G::BN, KB = C::KB, S = C::STAGES;
   constexpr int NT = G::NTOT / BN;  // N tiles per M tile
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -320,8 +366,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
       for (int idx = pt; idx < KB * C::B_ROWS * 8; idx += kProd) {
         const int kb = idx / (C::B_ROWS * 8), rem = idx - kb * (C::B_ROWS * 8), r = rem >> 3, c = rem & 7;
         const uint32_t off = uint32_t(kb) * (C::B_ROWS * 128) + sw128_off(r, c);
-        const __nv_bfloat16 *src = r < BN ? p.b_hi : p.b_lo;
-        cp_async16(res + off, src + (long long)(r % BN) * G::K + kb * 64 + c * 8);
+        const uint8_t *src = static_cast<const uint8_t *>(r < BN ? p.b_hi : p.b_lo);
+        cp_async16(res + off, src + ((long long)(r % BN) * C::KPAD) * EB + kb * 128 + c * 16);
       }
       cp_commit();
       cp_wait<0>();
@@ -372,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
         cp_wait<0>();  // this tile's node states (fetched during the previous tile)
         uint32_t *dj = dirty + (c & 1) * (4 * kProd);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < KB; ++j) {
           const uint32_t a = dj[j * kProd + pt];
           if (a) st_shared16(a, make_uint4(0u, 0u, 0u, 0u));
         }
@@ -387,21 +433,32 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
         const uint32_t m0 = uint32_t(t) * 128u;
         const uint32_t mlast = (m0 + 127u < p.M - 1u) ? m0 + 127u : p.M - 1u;
         const uint32_t leaf0 = m0 / uint32_t(kP1), leaf_last = mlast / uint32_t(kP1);
+        // bf16: K block j = history slot j, chunk cc = kernel row cc (8 pixels);
+        // E4M3: K block j = slots 2j, 2j+1, chunk cc = slot 2j + cc/4, kernel rows
+        // 2(cc%4) and 2(cc%4)+1 (16 pixels)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {  // slot (= K block) j
+        for (int j = 0; j < KB; ++j) {
           uint32_t wrote = 0u;
           const uint32_t leaf = leaf0 + uint32_t(li);
-          const uint32_t wk = (k & 2) ? ((k & 1) ? P[j].w : P[j].z) : ((k & 1) ? P[j].y : P[j].x);
+          const uint4 Pv = FP8 ? ((cc >> 2) ? P[(2 * j + 1) & 3] : P[(2 * j) & 3]) : P[j & 3];
+          const uint32_t wk = (k & 2) ? ((k & 1) ? Pv.w : Pv.z) : ((k & 1) ? Pv.y : Pv.x);
           const int ox = int(int16_t(wk & 0xFFFFu)) - dx, oy = int(int16_t(wk >> 16)) - dy;
           const uint32_t m = leaf * uint32_t(kP1) + uint32_t(oy * 20 + ox);
           if (leaf <= leaf_last && ox >= 0 && ox <= 19 && oy >= 0 && oy <= 19 && m >= m0 && m <= mlast) {
             int oxs[4], oys[4];
-            unpack_slot(P[j], oxs, oys);
-            const int y = 4 * oy + cc;
-            const uint32_t w0 = render_word(oxs, oys, ox, y);
-            const uint32_t w1 = render_word(oxs, oys, ox + 1, y);
+            unpack_slot(Pv, oxs, oys);
+            uint4 v;
+            if (FP8) {
+              const int y = 4 * oy + 2 * (cc & 3);
+              const uint32_t w[4] = {render_word(oxs, oys, ox, y), render_word(oxs, oys, ox + 1, y),
+                                     render_word(oxs, oys, ox, y + 1), render_word(oxs, oys, ox + 1, y + 1)};
+              v = pixels16_to_e4m3(w);
+            } else {
+              const int y = 4 * oy + cc;
+              v = pixels8_to_bf16(render_word(oxs, oys, ox, y), render_word(oxs, oys, ox + 1, y));
+            }
             wrote = sA_of((g + j) % S) + sw128_off(int(m - m0), cc);
-            st_shared16(wrote, pixels8_to_bf16(w0, w1));
+            st_shared16(wrote, v);
           }
           dj[j * kProd + pt] = wrote;
         }
@@ -451,13 +508,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
           const uint32_t sB = sB_of(s);
           const uint32_t sBlo = sB + C::B_BYTES;
           if (LAYER == 1) {
-            // conv1 from uint8 frame stacks: 8 pixels of kernel row ch, converted
+            // conv1 from uint8 frame stacks: 8 pixels of kernel row ch (bf16), or
+            // 16 pixels of kernel rows 2(ch%4), 2(ch%4)+1 of slot 2 kb + ch/4 (E4M3)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-              const uint8_t *src = static_cast<const uint8_t *>(p.a_hi) + rowoff[i] + kb * 7056 + ch * 84;
-              const uint32_t w0 = __ldg(reinterpret_cast<const uint32_t *>(src));
-              const uint32_t w1 = __ldg(reinterpret_cast<const uint32_t *>(src + 4));
-              st_shared16(sA + sw128_off(r0 + 32 * i, ch), pixels8_to_bf16(w0, w1));
+              uint4 v;
+              if (FP8) {
+                const uint8_t *src = static_cast<const uint8_t *>(p.a_hi) + rowoff[i] +
+                                     (2 * kb + (ch >> 2)) * 7056 + 2 * (ch & 3) * 84;
+                const uint32_t w[4] = {__ldg(reinterpret_cast<const uint32_t *>(src)),
+                                       __ldg(reinterpret_cast<const uint32_t *>(src + 4)),
+                                       __ldg(reinterpret_cast<const uint32_t *>(src + 84)),
+                                       __ldg(reinterpret_cast<const uint32_t *>(src + 88))};
+                v = pixels16_to_e4m3(w);
+              } else {
+                const uint8_t *src = static_cast<const uint8_t *>(p.a_hi) + rowoff[i] + kb * 7056 + ch * 84;
+                v = pixels8_to_bf16(__ldg(reinterpret_cast<const uint32_t *>(src)),
+                                    __ldg(reinterpret_cast<const uint32_t *>(src + 4)));
+              }
+              st_shared16(sA + sw128_off(r0 + 32 * i, ch), v);
             }
             fence_proxy_async();
             mbar_arrive(full_bar(s));
@@ -468,8 +537,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const uint32_t off = sw128_off(r0 + 32 * i, ch);
-            long long e;
-            if (LAYER == 2) {
+            long long e;  // element offset; a 16-byte chunk is 8 bf16 or 16 E4M3 elements
+            if (FP8) {
+              if (LAYER == 2) {  // K block = 4 kernel positions x 32 channels
+                const int pos = 4 * kb + (ch >> 1), ky = pos >> 2, kx = pos & 3;
+                e = rowoff[i] + (ky * 20 + kx) * kC1 + (ch & 1) * 16;
+              } else if (LAYER == 3) {  // 2 positions x 64 channels; position 9 is padding
+                int pos = 2 * kb + (ch >> 2);
+                pos = pos > 8 ? 8 : pos;  // any finite data: the padded weights are zero
+                const int ky = pos / 3, kx = pos - 3 * (pos / 3);
+                e = rowoff[i] + (ky * 9 + kx) * kC2 + (ch & 3) * 16;
+              } else {  // fc1: K padded from 3136 to 3200
+                int off = kb * 128 + ch * 16;
+                off = off >= kKF ? off - 64 : off;
+                e = rowoff[i] + off;
+              }
+            } else if (LAYER == 2) {
               const int pos = 2 * kb + (ch >> 2), ky = pos >> 2, kx = pos & 3;
               e = rowoff[i] + (ky * 20 + kx) * kC1 + (ch & 3) * 8;
             } else if (LAYER == 3) {
@@ -478,17 +561,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
             } else {
               e = rowoff[i] + kb * 64 + ch * 8;
             }
-            cp_async16(sA + off, static_cast<const __nv_bfloat16 *>(p.a_hi) + e);
-            if (C::A_LO) cp_async16(sAlo + off, static_cast<const __nv_bfloat16 *>(p.a_lo) + e);
+            cp_async16(sA + off, static_cast<const uint8_t *>(p.a_hi) + e * EB);
+            if (C::A_LO) cp_async16(sAlo + off, static_cast<const uint8_t *>(p.a_lo) + e * EB);
           }
           // B tile (weights, [NTOT][K] K-major): hi rows, then lo rows
 #pragma unroll
           for (int i = 0; i < BN / 32; ++i) {
             const int r = r0 + 32 * i;
             const uint32_t off = sw128_off(r, ch);
-            const long long e = (long long)(n0 + r) * G::K + kb * 64 + ch * 8;
-            cp_async16(sB + off, p.b_hi + e);
-            if (SPLIT) cp_async16(sBlo + off, p.b_lo + e);
+            const long long eb = ((long long)(n0 + r) * C::KPAD) * EB + kb * 128 + ch * 16;  // bytes
+            cp_async16(sB + off, static_cast<const uint8_t *>(p.b_hi) + eb);
+            if (SPLIT) cp_async16(sBlo + off, static_cast<const uint8_t *>(p.b_lo) + eb);
           }
           cp_async_arrive(full_bar(s));
           ++g;
@@ -500,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc_wide = idesc_bf16(C::B_CAT ? 2 * BN : BN);  // [hi; lo] weight rows
-      constexpr uint32_t idesc_n = idesc_bf16(BN);
+      constexpr uint32_t idesc_n = FP8 ? idesc_e4m3(BN) : idesc_bf16(BN);
       int g = 0, it = 0;
       bool ok = true;
       if (C::B_RES) ok = wait_bar(wready_bar, 0, abort_flag, p.d_err, 6);
@@ -540,7 +623,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
             const uint32_t first = (kb | j) != 0;
             const uint64_t a = sw128_desc(sA) + uint64_t(2 * j);
             const uint64_t b = sw128_desc(sB) + uint64_t(2 * j);
-            if (C::B_CAT) {
+            if (FP8) {
+              mma_f8(d, a, b, idesc_n, first);
+            } else if (C::B_CAT) {
               mma_bf16(d, a, b, idesc_wide, first);  // [A_hi B_hi | A_hi B_lo]
               if (C::A_LO) mma_bf16(d, sw128_desc(sAlo) + uint64_t(2 * j), b, idesc_n, 1u);  // + A_lo B_hi
             } else {
@@ -575,7 +660,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int row = q * 32 + lane;
-    for (int i = threadIdx.x - 32 * kEpiWarp0; i < G::NTOT; i += 128) bias_s[i] = p.bias[i];
+    float *scale_s = bias_s + G::NTOT;
+    for (int i = threadIdx.x - 32 * kEpiWarp0; i < G::NTOT; i += 128) {
+      bias_s[i] = p.bias[i];
+      scale_s[i] = FP8 ? p.colscale[i] : 1.f;
+    }
     named_bar_sync(2, 128);
     int it = 0;
     for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++it) {
@@ -602,9 +691,26 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
           for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
         }
 #pragma unroll
-        for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + bias_s[n0 + j * 16 + e], 0.f);
+        for (int e = 0; e < 16; ++e) {
+          const int n = n0 + j * 16 + e;
+          v[e] = fmaxf(FP8 ? fmaf(v[e], scale_s[n], bias_s[n]) : v[e] + bias_s[n], 0.f);
+        }
         if (m < p.M) {
-          if (LAYER == 4) {
+          if (FP8 && LAYER != 4) {
+            // next layer's operand: E4M3 of value / activation scale, 16 bytes per chunk
+            uint32_t o[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const uint32_t lo = __nv_cvt_float2_to_fp8x2(
+                  make_float2(v[4 * h] * p.out_inv_scale, v[4 * h + 1] * p.out_inv_scale), __NV_SATFINITE, __NV_E4M3);
+              const uint32_t hi = __nv_cvt_float2_to_fp8x2(
+                  make_float2(v[4 * h + 2] * p.out_inv_scale, v[4 * h + 3] * p.out_inv_scale), __NV_SATFINITE,
+                  __NV_E4M3);
+              o[h] = lo | (hi << 16);
+            }
+            *reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.out_hi) + size_t(m) * G::NTOT + n0 + j * 16) =
+                make_uint4(o[0], o[1], o[2], o[3]);
+          } else if (LAYER == 4) {
             float4 *dst =
                 reinterpret_cast<float4 *>(static_cast<float *>(p.out_hi) + size_t(m) * G::NTOT + n0 + j * 16);
 #pragma unroll
@@ -661,14 +767,14 @@ int num_sms() {
   return sms;
 }
 
-template <int LAYER, bool SPLIT, bool FUSED>
+template <int LAYER, int MODE, bool FUSED>
 int launch(const GemmParams &p0, long long M, int kind, cudaStream_t st) {
-  using C = Cfg<LAYER, SPLIT>;
+  using C = Cfg<LAYER, MODE>;
   if (M <= 0) return BCTS_OK;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm<LAYER, SPLIT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(tc_gemm<LAYER, MODE, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     C::SMEM);
   });
   if (attr_err != cudaSuccess) return BCTS_ECUDA;
@@ -681,7 +787,7 @@ int launch(const GemmParams &p0, long long M, int kind, cudaStream_t st) {
   p.num_tiles = int(tiles);
   const int grid = int(tiles < num_sms() ? tiles : num_sms());
   ProfScope ps(kind, st);
-  tc_gemm<LAYER, SPLIT, FUSED><<<grid, kThreads, C::SMEM, st>>>(p);
+  tc_gemm<LAYER, MODE, FUSED><<<grid, kThreads, C::SMEM, st>>>(p);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 
@@ -705,9 +811,11 @@ struct TcWeights {
   int A = 0;
   int precision = 0;
   void *blob = nullptr;
-  const __nv_bfloat16 *w_hi[4] = {};  // conv1, conv2, conv3, fc1
-  const __nv_bfloat16 *w_lo[4] = {};
+  const void *w_hi[4] = {};  // conv1, conv2, conv3, fc1: bf16 hi (BF16 / split) or E4M3 (FP8), [rows][KPAD]
+  const void *w_lo[4] = {};  // bf16 lo (split)
   const float *bias[4] = {};
+  const float *colscale[4] = {};  // FP8: weight scale of each output channel x input activation scale
+  float out_inv_scale[4] = {};    // FP8: 1 / activation scale of each layer's output map
   const float *f2w = nullptr, *f2b = nullptr;
 };
 
@@ -719,19 +827,25 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 
 size_t tc_scratch_bytes(int64_t chunk, int precision) {
-  const size_t lo = precision == BCTS_PREC_FP32 ? 2 : 1;
-  return lo * (align256(size_t(chunk) * kP1 * kC1 * 2) + align256(size_t(chunk) * kP2 * kC2 * 2) +
-               align256(size_t(chunk) * kP3 * kC3 * 2)) +
-         align256(size_t(chunk) * kF1 * 4) + 4096;
+  const size_t maps = size_t(kP1) * kC1 + size_t(kP2) * kC2 + size_t(kP3) * kC3;  // elements per node
+  const size_t bytes = precision == BCTS_PREC_FP32 ? 4 : (precision == BCTS_PREC_FP8 ? 1 : 2);
+  return align256(size_t(chunk) * maps * bytes) + 3 * 256 + align256(size_t(chunk) * kF1 * 4) + 4096;
 }
 
 // `w` holds the weights in the CUDA-core layouts (conv1 pre-scaled by 1/255,
 // conv2/conv3 K = (ky, kx, c), fc1 columns NHWC); the same orders serve here.
-int tc_weights_create(const float *w, int A, int precision, TcWeights **out, std::string &err) {
+// act_scale (FP8 only): activation scales of the conv1, conv2, conv3 output maps.
+int tc_weights_create(const float *w, int A, int precision, const float *act_scale, TcWeights **out,
+                      std::string &err) {
   *out = nullptr;
-  if (precision != BCTS_PREC_FP32 && precision != BCTS_PREC_BF16) {
+  if (precision != BCTS_PREC_FP32 && precision != BCTS_PREC_BF16 && precision != BCTS_PREC_FP8) {
     err = "precision not available on the tensor-core path";
     return BCTS_ENOKERNEL;
+  }
+  const bool fp8 = precision == BCTS_PREC_FP8;
+  if (fp8 && !act_scale) {
+    err = "FP8 weights need activation scales";
+    return BCTS_EINVAL;
   }
   int dev = 0, major = 0, minor = 0;
   cudaGetDevice(&dev);
@@ -754,37 +868,58 @@ int tc_weights_create(const float *w, int A, int precision, TcWeights **out, std
   bsrc[3] = src[3] + size_t(512) * 3136;
   const float *f2w = bsrc[3] + 512;
   const float *f2b = f2w + size_t(A) * 512;
-  // blob: [hi, lo] bf16 per layer, then FP32 biases, fc2 weights and biases
+  int kpad[4];
+  for (int l = 0; l < 4; ++l) kpad[l] = fp8 ? (kWK[l] + 127) / 128 * 128 : kWK[l];
+  const size_t eb = fp8 ? 1 : 2;
+  // blob: per layer [hi, lo] weights, then FP32 biases, column scales, fc2 weights and biases
   std::vector<size_t> off;
   size_t total = 0;
   for (int l = 0; l < 4; ++l) {
     off.push_back(total);
-    total += align256(size_t(kWRows[l]) * kWK[l] * 2);
+    total += align256(size_t(kWRows[l]) * kpad[l] * eb);
     off.push_back(total);
-    total += align256(size_t(kWRows[l]) * kWK[l] * 2);
+    total += align256(size_t(kWRows[l]) * kpad[l] * eb);
   }
-  for (int l = 0; l < 4; ++l) {
+  for (int l = 0; l < 8; ++l) {  // biases (0..3), column scales (4..7)
     off.push_back(total);
-    total += align256(size_t(kWRows[l]) * 4);
+    total += align256(size_t(kWRows[l % 4]) * 4);
   }
   const size_t off_f2w = total;
   total += align256(size_t(A) * 512 * 4);
   const size_t off_f2b = total;
   total += align256(size_t(A) * 4);
   std::vector<uint8_t> h(total, 0);
+  TcWeights *t = new TcWeights();
   for (int l = 0; l < 4; ++l) {
-    uint16_t *hi = reinterpret_cast<uint16_t *>(h.data() + off[2 * l]);
-    uint16_t *lo = reinterpret_cast<uint16_t *>(h.data() + off[2 * l + 1]);
-    const size_t n = size_t(kWRows[l]) * kWK[l];
-    for (size_t i = 0; i < n; ++i) {
-      hi[i] = tc::f2bf(src[l][i]);
-      lo[i] = tc::f2bf(src[l][i] - tc::bf2f(hi[i]));
+    const size_t R = kWRows[l], K = kWK[l], KP = kpad[l];
+    if (fp8) {
+      // per-output-channel scale: the row's max |w| maps to 448, E4M3's largest normal
+      uint8_t *q = h.data() + off[2 * l];
+      float *cs = reinterpret_cast<float *>(h.data() + off[12 + l]);
+      const float s_in = l == 0 ? 1.f : act_scale[l - 1];  // conv1 reads raw pixel values
+      for (size_t r = 0; r < R; ++r) {
+        float mx = 0.f;
+        for (size_t k = 0; k < K; ++k) mx = std::max(mx, std::fabs(src[l][r * K + k]));
+        const float sw = mx > 0.f ? mx / 448.f : 1.f;
+        for (size_t k = 0; k < K; ++k)
+          q[r * KP + k] = uint8_t(__nv_cvt_float_to_fp8(src[l][r * K + k] / sw, __NV_SATFINITE, __NV_E4M3));
+        cs[r] = sw * s_in;  // padded columns K..KP stay zero
+      }
+      t->out_inv_scale[l] = l < 3 ? 1.f / act_scale[l] : 1.f;
+    } else {
+      uint16_t *hi = reinterpret_cast<uint16_t *>(h.data() + off[2 * l]);
+      uint16_t *lo = reinterpret_cast<uint16_t *>(h.data() + off[2 * l + 1]);
+      for (size_t i = 0; i < R * K; ++i) {
+        hi[i] = tc::f2bf(src[l][i]);
+        lo[i] = tc::f2bf(src[l][i] - tc::bf2f(hi[i]));
+      }
+      float *cs = reinterpret_cast<float *>(h.data() + off[12 + l]);
+      for (size_t r = 0; r < R; ++r) cs[r] = 1.f;
     }
-    std::memcpy(h.data() + off[8 + l], bsrc[l], size_t(kWRows[l]) * 4);
+    std::memcpy(h.data() + off[8 + l], bsrc[l], R * 4);
   }
   std::memcpy(h.data() + off_f2w, f2w, size_t(A) * 512 * 4);
   std::memcpy(h.data() + off_f2b, f2b, size_t(A) * 4);
-  TcWeights *t = new TcWeights();
   t->A = A;
   t->precision = precision;
   if (cudaMalloc(&t->blob, total) != cudaSuccess ||
@@ -797,9 +932,10 @@ int tc_weights_create(const float *w, int A, int precision, TcWeights **out, std
   }
   uint8_t *b = static_cast<uint8_t *>(t->blob);
   for (int l = 0; l < 4; ++l) {
-    t->w_hi[l] = reinterpret_cast<const __nv_bfloat16 *>(b + off[2 * l]);
-    t->w_lo[l] = reinterpret_cast<const __nv_bfloat16 *>(b + off[2 * l + 1]);
+    t->w_hi[l] = b + off[2 * l];
+    t->w_lo[l] = b + off[2 * l + 1];
     t->bias[l] = reinterpret_cast<const float *>(b + off[8 + l]);
+    t->colscale[l] = reinterpret_cast<const float *>(b + off[12 + l]);
   }
   t->f2w = reinterpret_cast<const float *>(b + off_f2w);
   t->f2b = reinterpret_cast<const float *>(b + off_f2b);
@@ -814,65 +950,46 @@ void tc_weights_destroy(TcWeights *w) {
 }
 
 namespace {
-template <bool SPLIT>
+template <int MODE>
 int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n,
                     float *q, float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A) {
-  const size_t lo = SPLIT ? 2 : 1;
+  constexpr bool SPLIT = MODE == 1;
+  const size_t eb = MODE == 2 ? 1 : 2;
   uint8_t *s = static_cast<uint8_t *>(scratch);
   auto take = [&](size_t bytes) {
     uint8_t *r = s;
     s += align256(bytes);
     return r;
   };
-  __nv_bfloat16 *a1 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP1 * kC1 * 2));
-  __nv_bfloat16 *a1l = SPLIT ? reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP1 * kC1 * 2)) : nullptr;
-  __nv_bfloat16 *a2 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP2 * kC2 * 2));
-  __nv_bfloat16 *a2l = SPLIT ? reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP2 * kC2 * 2)) : nullptr;
-  __nv_bfloat16 *a3 = reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP3 * kC3 * 2));
-  __nv_bfloat16 *a3l = SPLIT ? reinterpret_cast<__nv_bfloat16 *>(take(size_t(n) * kP3 * kC3 * 2)) : nullptr;
+  const size_t m1 = size_t(n) * kP1 * kC1, m2 = size_t(n) * kP2 * kC2, m3 = size_t(n) * kP3 * kC3;
+  void *a1 = take(m1 * eb), *a1l = SPLIT ? take(m1 * eb) : nullptr;
+  void *a2 = take(m2 * eb), *a2l = SPLIT ? take(m2 * eb) : nullptr;
+  void *a3 = take(m3 * eb), *a3l = SPLIT ? take(m3 * eb) : nullptr;
   float *h = reinterpret_cast<float *>(take(size_t(n) * kF1 * 4));
-  (void)lo;
   int rc;
   tc::GemmParams p{};
   p.d_err = d_err;
-  // conv1
-  p.a_hi = states ? static_cast<const void *>(states) : static_cast<const void *>(frames);
-  p.a_lo = nullptr;
-  p.b_hi = w->w_hi[0];
-  p.b_lo = w->w_lo[0];
-  p.bias = w->bias[0];
-  p.out_hi = a1;
-  p.out_lo = a1l;
-  rc = states ? tc::launch<1, SPLIT, true>(p, (long long)n * kP1, K_CONV1, st)
-              : tc::launch<1, SPLIT, false>(p, (long long)n * kP1, K_CONV1, st);
+  auto layer = [&](int l, const void *in, const void *in_lo, void *o, void *o_lo) {
+    p.a_hi = in;
+    p.a_lo = in_lo;
+    p.b_hi = w->w_hi[l];
+    p.b_lo = w->w_lo[l];
+    p.bias = w->bias[l];
+    p.colscale = w->colscale[l];
+    p.out_inv_scale = w->out_inv_scale[l];
+    p.out_hi = o;
+    p.out_lo = o_lo;
+  };
+  layer(0, states ? static_cast<const void *>(states) : static_cast<const void *>(frames), nullptr, a1, a1l);
+  rc = states ? tc::launch<1, MODE, true>(p, (long long)n * kP1, K_CONV1, st)
+              : tc::launch<1, MODE, false>(p, (long long)n * kP1, K_CONV1, st);
   if (rc != BCTS_OK) return rc;
-  // conv2
-  p.a_hi = a1;
-  p.a_lo = a1l;
-  p.b_hi = w->w_hi[1];
-  p.b_lo = w->w_lo[1];
-  p.bias = w->bias[1];
-  p.out_hi = a2;
-  p.out_lo = a2l;
-  if ((rc = tc::launch<2, SPLIT, false>(p, (long long)n * kP2, K_CONV2, st)) != BCTS_OK) return rc;
-  // conv3
-  p.a_hi = a2;
-  p.a_lo = a2l;
-  p.b_hi = w->w_hi[2];
-  p.b_lo = w->w_lo[2];
-  p.bias = w->bias[2];
-  p.out_hi = a3;
-  p.out_lo = a3l;
-  if ((rc = tc::launch<3, SPLIT, false>(p, (long long)n * kP3, K_CONV3, st)) != BCTS_OK) return rc;
-  // fc1 (FP32 output for FC2)
-  p.a_hi = a3;
-  p.a_lo = a3l;
-  p.b_hi = w->w_hi[3];
-  p.b_lo = w->w_lo[3];
-  p.bias = w->bias[3];
-  p.out_hi = h;
-  p.out_lo = nullptr;
-  if ((rc = tc::launch<4, SPLIT, false>(p, (long long)n, K_FC1, st)) != BCTS_OK) return rc;
+  layer(1, a1, a1l, a2, a2l);
+  if ((rc = tc::launch<2, MODE, false>(p, (long long)n * kP2, K_CONV2, st)) != BCTS_OK) return rc;
+  layer(2, a2, a2l, a3, a3l);
+  if ((rc = tc::launch<3, MODE, false>(p, (long long)n * kP3, K_CONV3, st)) != BCTS_OK) return rc;
+  layer(3, a3, a3l, h, nullptr);  // FP32 output for FC2
+  if ((rc = tc::launch<4, MODE, false>(p, (long long)n, K_FC1, st)) != BCTS_OK) return rc;
   return launch_fc2_max(h, w->f2w, w->f2b, A, n, q, maxq, st, node_A);
 }
 }  // namespace
@@ -881,8 +998,10 @@ int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts
                     float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A) {
   if (n <= 0) return BCTS_OK;
   if (w->precision == BCTS_PREC_FP32)
-    return tc_forward_impl<true>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A);
-  return tc_forward_impl<false>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A);
+    return tc_forward_impl<1>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A);
+  if (w->precision == BCTS_PREC_FP8)
+    return tc_forward_impl<2>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A);
+  return tc_forward_impl<0>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A);
 }
 
 }  // namespace bcts

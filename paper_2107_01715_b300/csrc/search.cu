@@ -2,6 +2,7 @@
 // (Alg. 1), the backup kernels (Eq. 1 max over each root action's sub-tree,
 // Prop. 1 Bellman errors, Eq. 7 penalty, Eq. 3 correction, Eq. 4 argmax) and the
 // C-ABI entry points that run them.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -321,6 +322,80 @@ Ctx::~Ctx() {
 
 using bcts::Ctx;
 
+namespace bcts {
+// FP8 activation scales: run the plain FP32 network on a fixed calibration set
+// (512 states from an internal Knuth MMIX LCG, each advanced three ticks so the
+// history slots differ) and map each output map's largest value to 448, the
+// largest normal E4M3 number.
+static int calibrate_fp8(Ctx *c, float act_scale[3], std::string &err) {
+  const int n = 512;
+  std::vector<bcts_state> hs(n);
+  uint64_t x = 0x2545F4914F6CDD1Dull;
+  auto next = [&]() {
+    x = x * 6364136223846793005ull + 1442695040888963407ull;
+    return uint32_t(x >> 33);
+  };
+  for (int i = 0; i < n; ++i) {
+    bcts_state s{};
+    for (int k = 0; k < kObj; ++k)
+      for (int hh = 0; hh < kHist; ++hh) {
+        if (hh == 0) {
+          s.pos[0][k][0] = int16_t(next() % kGrid);
+          s.pos[0][k][1] = int16_t(next() % kGrid);
+        } else {
+          s.pos[hh][k][0] = s.pos[0][k][0];
+          s.pos[hh][k][1] = s.pos[0][k][1];
+        }
+      }
+    for (int k = 1; k < kObj; ++k) {
+      s.vel[k][0] = int8_t(int(next() % 3) - 1);
+      s.vel[k][1] = int8_t(int(next() % 3) - 1);
+    }
+    s.tick = next() & 0xFFFF;
+    for (int t = 0; t < 3; ++t) {
+      bcts_state nx;
+      bcts_env_step(&s, int(next() % kMaxA), &nx, nullptr);
+      s = nx;
+    }
+    hs[i] = s;
+  }
+  void *d_states = nullptr, *d_frames = nullptr, *d_scratch = nullptr, *d_q = nullptr;
+  const size_t scratch_b = simt_scratch_bytes(n);
+  int rc = BCTS_OK;
+  std::vector<float> maps(size_t(n) * (kP1 * kC1 + kP2 * kC2 + kP3 * kC3));
+  if (cudaMalloc(&d_states, size_t(n) * kStateBytes) != cudaSuccess ||
+      cudaMalloc(&d_frames, size_t(n) * kFrameBytes) != cudaSuccess || cudaMalloc(&d_scratch, scratch_b) != cudaSuccess ||
+      cudaMalloc(&d_q, size_t(n) * c->A_create * 4) != cudaSuccess) {
+    rc = BCTS_ENOMEM;
+    err = "calibration allocation failed";
+  }
+  if (rc == BCTS_OK && (cudaMemcpy(d_states, hs.data(), size_t(n) * kStateBytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+                        launch_render(static_cast<bcts_state *>(d_states), n, static_cast<uint8_t *>(d_frames), 0) !=
+                            BCTS_OK ||
+                        simt_qnet_forward(c->simt, static_cast<uint8_t *>(d_frames), n, static_cast<float *>(d_q),
+                                          nullptr, d_scratch, 0) != BCTS_OK ||
+                        cudaMemcpy(maps.data(), d_scratch, maps.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+    rc = BCTS_ECUDA;
+    err = "calibration run failed";
+  }
+  cudaGetLastError();
+  if (d_states) cudaFree(d_states);
+  if (d_frames) cudaFree(d_frames);
+  if (d_scratch) cudaFree(d_scratch);
+  if (d_q) cudaFree(d_q);
+  if (rc != BCTS_OK) return rc;
+  const size_t len[3] = {size_t(n) * kP1 * kC1, size_t(n) * kP2 * kC2, size_t(n) * kP3 * kC3};
+  size_t o = 0;
+  for (int l = 0; l < 3; ++l) {
+    float mx = 0.f;
+    for (size_t i = 0; i < len[l]; ++i) mx = std::max(mx, maps[o + i]);
+    o += len[l];
+    act_scale[l] = mx > 0.f ? mx / 448.f : 1.f;
+  }
+  return BCTS_OK;
+}
+}  // namespace bcts
+
 extern "C" size_t bcts_qnet_numel(int A) {
   if (A < 1) return 0;
   return size_t(32) * 256 + 32 + size_t(64) * 512 + 64 + size_t(64) * 576 + 64 + size_t(512) * 3136 + 512 +
@@ -418,7 +493,12 @@ extern "C" int bcts_create(const bcts_env_desc *env, const float *w, int A, int 
   c->simt.A = A;
   if (c->precision != BCTS_PREC_FP32_SIMT) {
     std::string e;
-    const int rc = tc_weights_create(hw.data(), A, c->precision, &c->tc, e);
+    float act_scale[3] = {1.f, 1.f, 1.f};
+    int rc = BCTS_OK;
+    if (c->precision == BCTS_PREC_FP8) rc = calibrate_fp8(c, act_scale, e);
+    if (rc == BCTS_OK)
+      rc = tc_weights_create(hw.data(), A, c->precision, c->precision == BCTS_PREC_FP8 ? act_scale : nullptr,
+                             &c->tc, e);
     if (rc != BCTS_OK) {
       delete c;
       set_thread_error("bcts_create: " + e);

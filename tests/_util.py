@@ -36,3 +36,14 @@ def check_actions(gpu_actions, ref_values, tol):
 def as_state_bytes(tensor_u8, n):
     from paper_2107_01715_b300.inputs import STATE_DTYPE
     return tensor_u8.cpu().numpy().view(STATE_DTYPE).reshape(n)
+
+
+def pi_o_decided(q0_row, tol):
+    """pi_o (argmax of the root Q-values, Sec. 3.3) is a discrete decision: where the
+    oracle's top-2 root Q margin is within the precision's tolerance, a reduced-
+    precision run may pick the other action and the Eq. 7 penalty then lands on
+    different actions.  Values are compared only where pi_o is decided."""
+    q = np.sort(np.asarray(q0_row, dtype=np.float64))
+    if q.size < 2:
+        return True
+    return q[-1] - q[-2] > 2 * tol * max(abs(q[-1]), 1.0)
