@@ -40,8 +40,16 @@ size_t tc_scratch_bytes(int64_t chunk, int precision);
 int tc_weights_create(const float *host_weights, int A, int precision, const float *act_scale, TcWeights **out,
                       std::string &err);
 void tc_weights_destroy(TcWeights *w);
+// Leaf conv1 from the parent partial maps: parent of leaf i = (leaf0 + i) / branch.
+struct ZLeaf {
+  const float *zmap;
+  uint32_t leaf0, branch;
+};
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
-                    float *maxq, void *scratch, cudaStream_t stream, int *d_err, const uint8_t *node_A = nullptr);
+                    float *maxq, void *scratch, cudaStream_t stream, int *d_err, const uint8_t *node_A = nullptr,
+                    const ZLeaf *zl = nullptr);
+bool tc_has_partial(const TcWeights *w);
+int tc_conv1_partial(const TcWeights *w, const bcts_state *states, int64_t n, float *z, cudaStream_t st, int *d_err);
 
 // search.cu backup kernels
 int launch_segment_max(const float *R, const float *maxq, int64_t n_seg, int64_t seg_len, float gamma_pow,

@@ -9,11 +9,11 @@
 //              or rendered on the fly from the node states) and the weight tile
 //              into 128-byte-swizzled shared memory (cp.async, or st.shared
 //              after the uint8 -> bf16 conversion), then signal a full barrier;
-//   warp 12    allocates TMEM and, from one lane, issues tcgen05.mma (M = 128,
+//   last warp  allocates TMEM and, from one lane, issues tcgen05.mma (M = 128,
 //              K = 16 per instruction) over the K blocks, committing each stage
 //              back to its producer barrier and each finished tile to the
 //              epilogue;
-//   warps 8-11 epilogue: tcgen05.ld the accumulator (one TMEM lane per thread),
+//   warps 8-11 (conv1: 8-15) epilogue: tcgen05.ld the accumulator (one TMEM lane per thread),
 //              add bias, ReLU, round to bf16 (and, in the FP32-class mode, the
 //              bf16 remainder) and store NHWC; up to four accumulators rotate so
 //              the next tiles' MMAs overlap this tile's epilogue.
@@ -245,17 +245,30 @@ struct Geo<4> {
   static constexpr int BN = 256, KB = 49, P = 1, NTOT = 512, K = 3136;
 };
 
+// Epilogue staging: 32 rows of up to 128 bytes (+16 to spread the banks) per warp.
+constexpr int kStgRow = 144;
+constexpr int kBarBytes = 512;  // mbarriers, TMEM address, abort flag
+
 // MODE 0: BF16 operands; 1: FP32-class split (bf16 hi + lo); 2: FP8 E4M3 operands
 // with per-output-channel weight scales and per-layer activation scales.
 // A K block is always 128 bytes: 64 bf16 or 128 E4M3 elements (FP8 pads K to a
 // whole block with zero weights).
-template <int LAYER, int MODE>
+// conv1 variants (bf16 and split modes): V = 0 the full 4-channel convolution;
+// V = 1 the parent partial Z = W_0 * slot1 + W_1 * slot2 + W_2 * slot3 + b (FP32
+// out, no ReLU); V = 2 a leaf: W_3 * slot3 + Z(parent), then ReLU.  A child's
+// slots 0..2 are its parent's slots 1..3 (frame stacking), and the convolution is
+// linear, so the leaf level needs one channel instead of four.
+template <int LAYER, int MODE, int V = 0>
 struct Cfg {
   using G = Geo<LAYER>;
   static constexpr bool SPLIT = MODE == 1, FP8 = MODE == 2;
   static constexpr int EB = FP8 ? 1 : 2;              // bytes per element
-  static constexpr int KB = FP8 ? (G::K + 127) / 128 : G::K / 64;
-  static constexpr int KPAD = KB * (128 / EB);        // weight row length in elements
+  static_assert(V == 0 || (LAYER == 1 && !FP8), "conv1 variants are bf16 / split only");
+  static constexpr int SLOT0 = V == 1 ? 1 : (V == 2 ? 3 : 0);  // first history slot read (K block 0)
+  static constexpr int WC0 = V == 2 ? 3 : 0;                     // first weight channel used
+  static constexpr int KB_FULL = FP8 ? (G::K + 127) / 128 : G::K / 64;
+  static constexpr int KB = V == 1 ? 3 : (V == 2 ? 1 : KB_FULL);  // K blocks this kernel multiplies
+  static constexpr int KPAD = KB_FULL * (128 / EB);  // stored weight row length in elements
   static constexpr bool A_LO = SPLIT && LAYER != 1;  // conv1's integer pixels are exact in bf16
   static constexpr bool B_RES = LAYER == 1;          // conv1's weights (16 / 32 KB) stay in shared memory
   // Split mode stores the weight tile as [hi rows; lo rows] so that one MMA of
@@ -269,13 +282,21 @@ struct Cfg {
   static constexpr int RES_BYTES = B_RES ? KB * B_ROWS * 128 : 0;
   static constexpr int STAGE_BYTES = A_BYTES * (A_LO ? 2 : 1) + (B_RES ? 0 : B_ROWS * 128);
   static constexpr int STAGES_RAW = (192 * 1024 - RES_BYTES) / STAGE_BYTES;
-  static constexpr int STAGES = B_RES ? 2 * KB : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
-  // fused conv1: re-zero lists (2 tiles x 4 slots x 256 threads) + node-state ring (2 tiles x 2 nodes)
-  static constexpr int DIRTY_BYTES = B_RES ? 2 * 4 * 256 * 4 + 2 * 2 * 80 : 0;
-  static constexpr int SMEM = RES_BYTES + STAGES * STAGE_BYTES + 1024 + 256 + DIRTY_BYTES + 2 * G::NTOT * 4;
+  // fused conv1 fills all KB stages of a tile together: a ring of RING tiles
+  static constexpr int RING = B_RES ? (8 / KB >= 2 ? 8 / KB : 2) : 1;
+  static constexpr int STAGES = B_RES ? RING * KB : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
+  // fused conv1: re-zero lists (8 x 256 entries) + node-state ring (3 tiles x 2 nodes)
+  static constexpr int DIRTY_BYTES = B_RES ? 2 * 4 * 256 * 4 + 3 * 2 * 80 : 0;
+  // conv1 (32-column tiles, the lightest epilogue) runs two epilogue warpgroups
+  // on alternating tiles so each has two tiles' time to hide its load latency
+  static constexpr int EPI_WG = LAYER == 1 ? 2 : 1;
+  static constexpr int MMA_WARP = 8 + 4 * EPI_WG;
+  static constexpr int THREADS = 32 * (MMA_WARP + 1);
+  static constexpr int SMEM = RES_BYTES + STAGES * STAGE_BYTES + 1024 + kBarBytes + DIRTY_BYTES + 2 * G::NTOT * 4 +
+                              4 * EPI_WG * 32 * kStgRow;
   // as many accumulators (up to 4) as TMEM's 512 columns hold, so the MMAs run
   // ahead of the two epilogue warpgroups
-  static constexpr int NUM_ACC = (4 * ACC_N <= 512) ? 4 : 2;
+  static constexpr int NUM_ACC = (8 * ACC_N <= 512) ? 8 : ((4 * ACC_N <= 512) ? 4 : 2);
   static constexpr uint32_t TMEM_COLS = NUM_ACC * ACC_N < 32 ? 32 : NUM_ACC * ACC_N;
   static_assert(STAGES >= 2, "pipeline depth");
   static_assert(RES_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0, "1024-byte aligned tiles");
@@ -291,6 +312,9 @@ struct GemmParams {
   const float *bias;
   const float *colscale;  // FP8: per-output-channel weight scale x input activation scale
   float out_inv_scale;    // FP8: 1 / activation scale of this layer's output map
+  const float *zmap;      // conv1 leaf variant: parent partial maps [parent][400][32] FP32
+  uint32_t z_leaf0;       // global index (within the level) of this launch's first leaf
+  uint32_t z_branch;      // A: parent of leaf i = (z_leaf0 + i) / A
   void *out_hi;  // bf16 NHWC (layers 1-3) or FP32 [M][512] (layer 4)
   void *out_lo;  // bf16 remainders (split mode, layers 1-3)
   uint32_t M;  // rows, < 2^31 (checked by the launcher)
@@ -298,16 +322,15 @@ struct GemmParams {
   int *d_err;
 };
 
-// warps 0-7 producers, 8-11 epilogue, 12 MMA
+// warps 0-7 producers, 8 .. 8 + 4 EPI_WG - 1 epilogue, then the MMA warp
 constexpr int kProdWarps = 8;
 constexpr int kProd = 32 * kProdWarps;  // producer threads
 constexpr int kEpiWarp0 = 8;
-constexpr int kMmaWarp = 12;
-constexpr int kThreads = 32 * (kMmaWarp + 1);
 
-template <int LAYER, int MODE, bool FUSED>
-__global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
-  using C = Cfg<LAYER, MODE>;
+template <int LAYER, int MODE, bool FUSED, int V = 0>
+__global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const GemmParams p) {
+  using C = Cfg<LAYER, MODE, V>;
+  constexpr int kMmaWarp = C::MMA_WARP;
   using G = Geo<LAYER>;
   constexpr bool SPLIT = C::SPLIT, FP8 = C::FP8;
   constexpr int EB = C::EB;
@@ -331,8 +354,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
   uint8_t *meta = gbase + C::RES_BYTES + S * C::STAGE_BYTES + 8 * (2 * S + 2 * NA + 2);
   volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(meta);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(meta + 4);
-  uint32_t *dirty = reinterpret_cast<uint32_t *>(gbase + C::RES_BYTES + S * C::STAGE_BYTES + 256);
-  float *bias_s = reinterpret_cast<float *>(gbase + C::RES_BYTES + S * C::STAGE_BYTES + 256 + C::DIRTY_BYTES);
+  uint32_t *dirty = reinterpret_cast<uint32_t *>(gbase + C::RES_BYTES + S * C::STAGE_BYTES + kBarBytes);
+  float *bias_s = reinterpret_cast<float *>(gbase + C::RES_BYTES + S * C::STAGE_BYTES + kBarBytes + C::DIRTY_BYTES);
+  static_assert(8 * (2 * S + 2 * C::NUM_ACC + 2) + 8 <= kBarBytes, "barrier area");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto sA_of = [&](int s) { return stage0 + uint32_t(s) * C::STAGE_BYTES; };
   auto sB_of = [&](int s) { return sA_of(s) + C::A_BYTES * (C::A_LO ? 2 : 1); };
@@ -367,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
         const int kb = idx / (C::B_ROWS * 8), rem = idx - kb * (C::B_ROWS * 8), r = rem >> 3, c = rem & 7;
         const uint32_t off = uint32_t(kb) * (C::B_ROWS * 128) + sw128_off(r, c);
         const uint8_t *src = static_cast<const uint8_t *>(r < BN ? p.b_hi : p.b_lo);
-        cp_async16(res + off, src + ((long long)(r % BN) * C::KPAD) * EB + kb * 128 + c * 16);
+        cp_async16(res + off, src + ((long long)(r % BN) * C::KPAD) * EB + (C::WC0 + kb) * 128 + c * 16);
       }
       cp_commit();
       cp_wait<0>();
@@ -383,13 +407,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
       // object k, patch offset dy dx, 16-byte chunk cc): this thread owns
       // (li, k, dy, dx, cc) = its index and the 4 slots; duplicates write
       // identical bytes.  What a thread wrote into a stage is re-zeroed when
-      // the stage next comes round (S = 2 KB: every other tile).
-      static_assert(!(LAYER == 1 && FUSED) || S == 2 * KB, "ring of two tiles");
+      // the stage next comes round (S = RING x KB: every RING-th tile).
+      static_assert(!(LAYER == 1 && FUSED) || (S == C::RING * KB && C::RING * KB * kProd <= 8 * 256),
+                    "ring of RING tiles");
       for (int idx = pt; idx < S * (C::STAGE_BYTES / 16); idx += kProd)
         st_shared16(stage0 + uint32_t(idx) * 16u, make_uint4(0u, 0u, 0u, 0u));
       for (int j = 0; j < 8; ++j) dirty[j * kProd + pt] = 0u;
       const int li = pt >> 7, k = (pt >> 5) & 3, dy = (pt >> 4) & 1, dx = (pt >> 3) & 1, cc = pt & 7;
-      // node states of a tile's <= 2 nodes, fetched one tile ahead into a ring
+      // node states of a tile's <= 2 nodes, fetched two tiles ahead into a ring of
+      // three; every tile commits one cp.async group (possibly empty), so at the
+      // start of a tile exactly its own group and the next one are outstanding.
+      // The fetch is issued after the tile's proxy fence so the fence never waits
+      // for it.
       const uint32_t ring = smem_u32(dirty + 8 * kProd);
       auto prefetch_states = [&](int t, int slot) {
         if (pt < 10) {
@@ -403,6 +432,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
         cp_commit();
       };
       if (int(blockIdx.x) < p.num_tiles) prefetch_states(blockIdx.x, 0);
+      else cp_commit();
+      if (int(blockIdx.x + gridDim.x) < p.num_tiles) prefetch_states(blockIdx.x + gridDim.x, 1);
+      else cp_commit();
       int c = 0;
       for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++c) {
         const int g = c * KB;
@@ -415,19 +447,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
         }
         named_bar_sync(1, kProd);  // every producer decides together
         if (*abort_flag) break;
-        cp_wait<0>();  // this tile's node states (fetched during the previous tile)
-        uint32_t *dj = dirty + (c & 1) * (4 * kProd);
+        cp_wait<1>();  // this tile's node states (the next tile's may still be in flight)
+        uint32_t *dj = dirty + (c % C::RING) * (KB * kProd);
 #pragma unroll
         for (int j = 0; j < KB; ++j) {
           const uint32_t a = dj[j * kProd + pt];
           if (a) st_shared16(a, make_uint4(0u, 0u, 0u, 0u));
         }
         named_bar_sync(1, kProd);  // states visible, re-zeroing done
-        const int tn = t + int(gridDim.x);
-        if (tn < p.num_tiles) prefetch_states(tn, (c + 1) & 1);
         uint4 P[4];
         const uint4 *Ps = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(dirty + 8 * kProd) +
-                                                          (c & 1) * 160 + li * 80);
+                                                          (c % 3) * 160 + li * 80);
 #pragma unroll
         for (int j = 0; j < 4; ++j) P[j] = Ps[j];
         const uint32_t m0 = uint32_t(t) * 128u;
@@ -440,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
         for (int j = 0; j < KB; ++j) {
           uint32_t wrote = 0u;
           const uint32_t leaf = leaf0 + uint32_t(li);
-          const uint4 Pv = FP8 ? ((cc >> 2) ? P[(2 * j + 1) & 3] : P[(2 * j) & 3]) : P[j & 3];
+          const uint4 Pv = FP8 ? ((cc >> 2) ? P[(2 * j + 1) & 3] : P[(2 * j) & 3]) : P[(C::SLOT0 + j) & 3];
           const uint32_t wk = (k & 2) ? ((k & 1) ? Pv.w : Pv.z) : ((k & 1) ? Pv.y : Pv.x);
           const int ox = int(int16_t(wk & 0xFFFFu)) - dx, oy = int(int16_t(wk >> 16)) - dy;
           const uint32_t m = leaf * uint32_t(kP1) + uint32_t(oy * 20 + ox);
@@ -465,6 +495,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
         fence_proxy_async();
 #pragma unroll
         for (int kb = 0; kb < KB; ++kb) mbar_arrive(full_bar((g + kb) % S));
+        const int t2 = t + 2 * int(gridDim.x);
+        if (t2 < p.num_tiles) prefetch_states(t2, (c + 2) % 3);
+        else cp_commit();
       }
       asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
@@ -658,23 +691,74 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
+    // Each warp owns 32 accumulator rows (its TMEM lane quarter).  Results are
+    // staged row by row in shared memory and written out as contiguous 16-byte
+    // segments, so every global store instruction covers whole lines; the
+    // parent partial rows of the conv1 leaf variant are read the same way.
     const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int row = q * 32 + lane;
     float *scale_s = bias_s + G::NTOT;
-    for (int i = threadIdx.x - 32 * kEpiWarp0; i < G::NTOT; i += 128) {
+    const int eg = (warp - kEpiWarp0) >> 2;  // warpgroup: tiles it with it % EPI_WG == eg
+    for (int i = threadIdx.x - 32 * kEpiWarp0; i < G::NTOT; i += 128 * C::EPI_WG) {
       bias_s[i] = p.bias[i];
       scale_s[i] = FP8 ? p.colscale[i] : 1.f;
     }
-    named_bar_sync(2, 128);
-    int it = 0;
-    for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++it) {
+    named_bar_sync(2, 128 * C::EPI_WG);
+    uint8_t *stg = reinterpret_cast<uint8_t *>(bias_s + 2 * G::NTOT) + (warp - kEpiWarp0) * (32 * kStgRow);
+    // output row bytes of one array (conv layers: whole rows; fc1: one 16-column chunk)
+    constexpr int ROWB = V == 1 ? kC1 * 4 : (LAYER == 4 ? 64 : (FP8 ? BN : BN * 2));
+    constexpr int SEGS = ROWB / 16;  // 16-byte segments per row
+    static_assert(ROWB + 16 <= kStgRow && kC1 * 4 + 16 <= kStgRow, "staging row");
+    // write the warp's 32 staged rows (ROWB bytes each) to dst rows of `stride` bytes
+    auto flush = [&](uint8_t *dst, size_t stride, uint32_t mw0) {
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < SEGS; ++i) {
+        const int k = lane + 32 * i, r = k / SEGS, sgm = k - r * SEGS;
+        if (mw0 + uint32_t(r) < p.M)
+          *reinterpret_cast<uint4 *>(dst + size_t(mw0 + r) * stride + sgm * 16) =
+              *reinterpret_cast<const uint4 *>(stg + r * kStgRow + sgm * 16);
+      }
+      __syncwarp();
+    };
+    float4 zc[V == 2 ? 8 : 1];  // conv1 leaf: partial rows, fetched cooperatively (row i*4 + lane/8)
+    auto zload = [&](int t) {
+      if constexpr (V == 2) {
+        const uint32_t mw0 = uint32_t(t / NT) * 128u + uint32_t(q * 32);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          uint32_t mm = mw0 + uint32_t(i * 4 + (lane >> 3));
+          mm = mm < p.M ? mm : p.M - 1u;
+          const uint32_t leaf = mm / uint32_t(kP1), px = mm - leaf * uint32_t(kP1);
+          zc[i] = __ldg(reinterpret_cast<const float4 *>(
+                            p.zmap + (size_t((p.z_leaf0 + leaf) / p.z_branch) * kP1 + px) * kC1) +
+                        (lane & 7));
+        }
+      }
+    };
+    constexpr int EW = C::EPI_WG;
+    if (V == 2 && int(blockIdx.x + eg * gridDim.x) < p.num_tiles) zload(blockIdx.x + eg * gridDim.x);
+    int it = eg;
+    for (int t = blockIdx.x + eg * int(gridDim.x); t < p.num_tiles; t += EW * int(gridDim.x), it += EW) {
       const int acc = it % NA;
       if (!wait_bar(tfull_bar(acc), uint32_t((it / NA) & 1), abort_flag, p.d_err, 4)) break;
       tc_fence_after();
-      const uint32_t m = uint32_t(t / NT) * 128u + uint32_t(row);
+      const uint32_t mw0 = uint32_t(t / NT) * 128u + uint32_t(q * 32);
       const int n0 = (t % NT) * BN;
       const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * C::ACC_N);
-#pragma unroll 1
+      if constexpr (V == 2) {
+        // partial rows into this warp's staging rows; chunk j reads bytes [64 j, 64 j + 64)
+        // of its row before it writes output bytes [32 j, 32 j + 32), so nothing is
+        // overwritten before it is read
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          *reinterpret_cast<float4 *>(stg + (i * 4 + (lane >> 3)) * kStgRow + (lane & 7) * 16) = zc[i];
+        __syncwarp();
+      }
+      // this thread's output row: hi part staged as it is produced, lo part kept
+      // in registers until the hi rows are written
+      constexpr int OW = LAYER == 4 ? 1 : (FP8 ? BN / 4 : BN / 2);
+      uint32_t olo[SPLIT && LAYER != 4 ? OW : 1];
+#pragma unroll
       for (int j = 0; j < BN / 16; ++j) {
         uint32_t r[16];
         tmem_ld16(tbase + uint32_t(j * 16), r);
@@ -690,58 +774,79 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm(const GemmParams p) {
 #pragma unroll
           for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
         }
+        if constexpr (V == 2) {
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int n = n0 + j * 16 + e;
-          v[e] = fmaxf(FP8 ? fmaf(v[e], scale_s[n], bias_s[n]) : v[e] + bias_s[n], 0.f);
+          for (int e = 0; e < 4; ++e) {  // the partial carries the bias
+            const float4 z4 = *reinterpret_cast<const float4 *>(stg + lane * kStgRow + j * 64 + e * 16);
+            v[4 * e] = fmaxf(v[4 * e] + z4.x, 0.f);
+            v[4 * e + 1] = fmaxf(v[4 * e + 1] + z4.y, 0.f);
+            v[4 * e + 2] = fmaxf(v[4 * e + 2] + z4.z, 0.f);
+            v[4 * e + 3] = fmaxf(v[4 * e + 3] + z4.w, 0.f);
+          }
+        } else if constexpr (V == 1) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] += bias_s[n0 + j * 16 + e];  // partial sum: no ReLU yet
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int n = n0 + j * 16 + e;
+            v[e] = fmaxf(FP8 ? fmaf(v[e], scale_s[n], bias_s[n]) : v[e] + bias_s[n], 0.f);
+          }
         }
-        if (m < p.M) {
-          if (FP8 && LAYER != 4) {
-            // next layer's operand: E4M3 of value / activation scale, 16 bytes per chunk
-            uint32_t o[4];
+        if constexpr (V == 1) {
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const uint32_t lo = __nv_cvt_float2_to_fp8x2(
-                  make_float2(v[4 * h] * p.out_inv_scale, v[4 * h + 1] * p.out_inv_scale), __NV_SATFINITE, __NV_E4M3);
-              const uint32_t hi = __nv_cvt_float2_to_fp8x2(
-                  make_float2(v[4 * h + 2] * p.out_inv_scale, v[4 * h + 3] * p.out_inv_scale), __NV_SATFINITE,
-                  __NV_E4M3);
-              o[h] = lo | (hi << 16);
-            }
-            *reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.out_hi) + size_t(m) * G::NTOT + n0 + j * 16) =
-                make_uint4(o[0], o[1], o[2], o[3]);
-          } else if (LAYER == 4) {
-            float4 *dst =
-                reinterpret_cast<float4 *>(static_cast<float *>(p.out_hi) + size_t(m) * G::NTOT + n0 + j * 16);
+          for (int e = 0; e < 4; ++e)
+            *reinterpret_cast<float4 *>(stg + lane * kStgRow + j * 64 + e * 16) =
+                make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        } else if constexpr (LAYER == 4) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-          } else {
-            uint32_t hi[8], lo[8];
+          for (int e = 0; e < 4; ++e)
+            *reinterpret_cast<float4 *>(stg + lane * kStgRow + e * 16) =
+                make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+          flush(static_cast<uint8_t *>(p.out_hi) + (size_t(n0) + j * 16) * 4, size_t(G::NTOT) * 4, mw0);
+        } else if constexpr (FP8) {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-              hi[e] = *reinterpret_cast<const uint32_t *>(&h);
-              if (SPLIT) {
-                const float2 hf = __bfloat1622float2(h);
-                const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
-                lo[e] = *reinterpret_cast<const uint32_t *>(&l);
-              }
-            }
-            const size_t o = size_t(m) * G::NTOT + n0 + j * 16;
-            uint4 *dh = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(p.out_hi) + o);
-            dh[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            dh[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-            if (SPLIT) {
-              uint4 *dl = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(p.out_lo) + o);
-              dl[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-              dl[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+          for (int h = 0; h < 4; ++h) {
+            const uint32_t lo = __nv_cvt_float2_to_fp8x2(
+                make_float2(v[4 * h] * p.out_inv_scale, v[4 * h + 1] * p.out_inv_scale), __NV_SATFINITE, __NV_E4M3);
+            const uint32_t hi = __nv_cvt_float2_to_fp8x2(
+                make_float2(v[4 * h + 2] * p.out_inv_scale, v[4 * h + 3] * p.out_inv_scale), __NV_SATFINITE,
+                __NV_E4M3);
+            olo[0] = lo | (hi << 16);  // reuse as a temporary
+            reinterpret_cast<uint32_t *>(stg + lane * kStgRow + j * 16)[h] = olo[0];
+          }
+        } else {
+          uint32_t hh[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+            hh[e] = *reinterpret_cast<const uint32_t *>(&h);
+            if constexpr (SPLIT) {
+              const float2 hf = __bfloat1622float2(h);
+              const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+              olo[j * 8 + e] = *reinterpret_cast<const uint32_t *>(&l);
             }
           }
+          *reinterpret_cast<uint4 *>(stg + lane * kStgRow + j * 32) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+          *reinterpret_cast<uint4 *>(stg + lane * kStgRow + j * 32 + 16) = make_uint4(hh[4], hh[5], hh[6], hh[7]);
+        }
+      }
+      if constexpr (V == 1) {
+        flush(static_cast<uint8_t *>(p.out_hi), size_t(kC1) * 4, mw0);
+      } else if constexpr (LAYER != 4) {
+        flush(static_cast<uint8_t *>(p.out_hi), size_t(ROWB), mw0);
+        if constexpr (SPLIT) {
+#pragma unroll
+          for (int i = 0; i < OW / 4; ++i)
+            *reinterpret_cast<uint4 *>(stg + lane * kStgRow + i * 16) =
+                make_uint4(olo[4 * i], olo[4 * i + 1], olo[4 * i + 2], olo[4 * i + 3]);
+          flush(static_cast<uint8_t *>(p.out_lo), size_t(ROWB), mw0);
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty_bar(acc));
+      if (V == 2 && t + EW * int(gridDim.x) < p.num_tiles) zload(t + EW * int(gridDim.x));
     }
   }
   // teardown: every role has left its loop (all waits are bounded)
@@ -767,14 +872,14 @@ int num_sms() {
   return sms;
 }
 
-template <int LAYER, int MODE, bool FUSED>
+template <int LAYER, int MODE, bool FUSED, int V = 0>
 int launch(const GemmParams &p0, long long M, int kind, cudaStream_t st) {
-  using C = Cfg<LAYER, MODE>;
+  using C = Cfg<LAYER, MODE, V>;
   if (M <= 0) return BCTS_OK;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm<LAYER, MODE, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(tc_gemm<LAYER, MODE, FUSED, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     C::SMEM);
   });
   if (attr_err != cudaSuccess) return BCTS_ECUDA;
@@ -787,7 +892,7 @@ int launch(const GemmParams &p0, long long M, int kind, cudaStream_t st) {
   p.num_tiles = int(tiles);
   const int grid = int(tiles < num_sms() ? tiles : num_sms());
   ProfScope ps(kind, st);
-  tc_gemm<LAYER, MODE, FUSED><<<grid, kThreads, C::SMEM, st>>>(p);
+  tc_gemm<LAYER, MODE, FUSED, V><<<grid, C::THREADS, C::SMEM, st>>>(p);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 
@@ -952,7 +1057,8 @@ void tc_weights_destroy(TcWeights *w) {
 namespace {
 template <int MODE>
 int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n,
-                    float *q, float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A) {
+                    float *q, float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A,
+                    const ZLeaf *zl) {
   constexpr bool SPLIT = MODE == 1;
   const size_t eb = MODE == 2 ? 1 : 2;
   uint8_t *s = static_cast<uint8_t *>(scratch);
@@ -981,8 +1087,20 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
     p.out_lo = o_lo;
   };
   layer(0, states ? static_cast<const void *>(states) : static_cast<const void *>(frames), nullptr, a1, a1l);
-  rc = states ? tc::launch<1, MODE, true>(p, (long long)n * kP1, K_CONV1, st)
-              : tc::launch<1, MODE, false>(p, (long long)n * kP1, K_CONV1, st);
+  if constexpr (MODE != 2) {
+    if (zl && states) {
+      p.zmap = zl->zmap;
+      p.z_leaf0 = zl->leaf0;
+      p.z_branch = zl->branch;
+      rc = tc::launch<1, MODE, true, 2>(p, (long long)n * kP1, K_CONV1, st);
+    } else {
+      rc = states ? tc::launch<1, MODE, true>(p, (long long)n * kP1, K_CONV1, st)
+                  : tc::launch<1, MODE, false>(p, (long long)n * kP1, K_CONV1, st);
+    }
+  } else {
+    rc = states ? tc::launch<1, MODE, true>(p, (long long)n * kP1, K_CONV1, st)
+                : tc::launch<1, MODE, false>(p, (long long)n * kP1, K_CONV1, st);
+  }
   if (rc != BCTS_OK) return rc;
   layer(1, a1, a1l, a2, a2l);
   if ((rc = tc::launch<2, MODE, false>(p, (long long)n * kP2, K_CONV2, st)) != BCTS_OK) return rc;
@@ -995,13 +1113,32 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
 }  // namespace
 
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
-                    float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A) {
+                    float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A,
+                    const ZLeaf *zl) {
   if (n <= 0) return BCTS_OK;
   if (w->precision == BCTS_PREC_FP32)
-    return tc_forward_impl<1>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A);
+    return tc_forward_impl<1>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl);
   if (w->precision == BCTS_PREC_FP8)
-    return tc_forward_impl<2>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A);
-  return tc_forward_impl<0>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A);
+    return tc_forward_impl<2>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, nullptr);
+  return tc_forward_impl<0>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl);
+}
+
+bool tc_has_partial(const TcWeights *w) { return w->precision == BCTS_PREC_FP32 || w->precision == BCTS_PREC_BF16; }
+
+// Parent partial maps Z = W_0 * slot1 + W_1 * slot2 + W_2 * slot3 + b, FP32 [n][400][32].
+int tc_conv1_partial(const TcWeights *w, const bcts_state *states, int64_t n, float *z, cudaStream_t st, int *d_err) {
+  if (n <= 0) return BCTS_OK;
+  tc::GemmParams p{};
+  p.d_err = d_err;
+  p.a_hi = states;
+  p.b_hi = w->w_hi[0];
+  p.b_lo = w->w_lo[0];
+  p.bias = w->bias[0];
+  p.colscale = w->colscale[0];
+  p.out_hi = z;
+  if (w->precision == BCTS_PREC_FP32) return tc::launch<1, 1, true, 1>(p, (long long)n * kP1, K_CONV1, st);
+  if (w->precision == BCTS_PREC_BF16) return tc::launch<1, 0, true, 1>(p, (long long)n * kP1, K_CONV1, st);
+  return BCTS_ENOKERNEL;
 }
 
 }  // namespace bcts

@@ -171,13 +171,14 @@ int64_t Ctx::chunk_nodes() const {
 // Score `count` nodes: render + Q-network, chunked.  q (count x A) and maxq
 // (count) may each be NULL.
 int Ctx::eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st,
-                    const uint8_t *node_A) {
+                    const uint8_t *node_A, const float *zmap, uint32_t zbranch) {
   const int64_t chunk = chunk_nodes();
   int rc;
   for (int64_t off = 0; off < count; off += chunk) {
     const int64_t cnt = count - off < chunk ? count - off : chunk;
+    const ZLeaf zl{zmap, uint32_t(off), zbranch};
     if ((rc = qnet_nodes(states + off, nullptr, cnt, q ? q + off * A : nullptr, maxq ? maxq + off : nullptr, st,
-                         node_A ? node_A + off : nullptr)) != BCTS_OK)
+                         node_A ? node_A + off : nullptr, zmap ? &zl : nullptr)) != BCTS_OK)
       return rc;
   }
   return BCTS_OK;
@@ -186,7 +187,7 @@ int Ctx::eval_nodes(const bcts_state *states, int64_t count, float *q, float *ma
 // Q-network on at most one chunk of nodes, given either states (rendered here)
 // or frames.
 int Ctx::qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
-                    cudaStream_t st, const uint8_t *node_A) {
+                    cudaStream_t st, const uint8_t *node_A, const ZLeaf *zl) {
   int rc;
   if (precision == BCTS_PREC_FP32_SIMT) {
     if (states) {
@@ -210,7 +211,8 @@ int Ctx::qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt
     states = nullptr;
   }
   if ((rc = ensure(scratch_buf, tc_scratch_bytes(cnt, precision))) != BCTS_OK) return rc;
-  rc = tc_qnet_forward(tc, A, frames, states, cnt, q, maxq, scratch_buf.p, st, d_err, node_A);
+  rc = tc_qnet_forward(tc, A, frames, states, cnt, q, maxq, scratch_buf.p, st, d_err, node_A,
+                       states ? zl : nullptr);
   if (rc != BCTS_OK) return fail(rc, "tensor-core Q-network launch failed");
   return BCTS_OK;
 }
@@ -278,9 +280,32 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
         curR = nxtR;
       }
       if (rc != BCTS_OK) break;
-      // a4 + a5: leaf render and Q-network, max over actions
+      // a4 + a5: leaf render and Q-network, max over actions.  With a tensor-core
+      // context the leaf conv1 needs only the newest frame: the parents' three
+      // newer slots (the leaves' older three) enter as partial maps computed
+      // once per parent (when they fit: 51.2 KB per parent).
       if ((rc = ensure(leafmax_buf, size_t(N[d_]) * sizeof(float))) != BCTS_OK) break;
-      if ((rc = eval_nodes(cur, N[d_], nullptr, static_cast<float *>(leafmax_buf.p), st)) != BCTS_OK) break;
+      const float *zmap = nullptr;
+      const size_t zbytes = size_t(N[d_ - 1]) * kP1 * kC1 * sizeof(float);
+      if (tc && tc_fused_render && tc_has_partial(tc) && zbytes <= (size_t(8) << 30)) {
+        if ((rc = ensure(z_buf, zbytes)) != BCTS_OK) break;
+        const bcts_state *par = static_cast<const bcts_state *>(lvl_buf[(d_ - 1) & 1].p);
+        if (d_ - 1 == 1) par = L1;
+        const int64_t chunk = chunk_nodes();
+        for (int64_t off = 0; off < N[d_ - 1] && rc == BCTS_OK; off += chunk) {
+          const int64_t cnt = N[d_ - 1] - off < chunk ? N[d_ - 1] - off : chunk;
+          rc = tc_conv1_partial(tc, par + off, cnt, static_cast<float *>(z_buf.p) + size_t(off) * kP1 * kC1, st,
+                                d_err);
+        }
+        if (rc != BCTS_OK) {
+          rc = fail(rc, "conv1 partial launch failed");
+          break;
+        }
+        zmap = static_cast<const float *>(z_buf.p);
+      }
+      if ((rc = eval_nodes(cur, N[d_], nullptr, static_cast<float *>(leafmax_buf.p), st, nullptr, zmap,
+                           uint32_t(A_))) != BCTS_OK)
+        break;
       leafR = curR;
       leafMax = static_cast<float *>(leafmax_buf.p);
     }
@@ -307,7 +332,7 @@ Ctx::~Ctx() {
   if (stream) cudaStreamSynchronize(stream);
   DevBuf *bufs[] = {&frames_buf, &scratch_buf, &q0_buf, &maxq1_buf, &V_buf, &r1_buf, &leafmax_buf,
                     &lvl_buf[0], &lvl_buf[1], &R_buf[0], &R_buf[1], &io_roots, &io_action, &io_values,
-                    &simt_w, &mixed_buf};
+                    &simt_w, &mixed_buf, &z_buf};
   for (DevBuf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (host_stage.p) cudaFreeHost(host_stage.p);

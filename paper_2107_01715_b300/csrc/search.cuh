@@ -40,7 +40,7 @@ struct Ctx {
 
   DevBuf simt_w, frames_buf, scratch_buf, q0_buf, maxq1_buf, V_buf, r1_buf, leafmax_buf;
   DevBuf lvl_buf[2], R_buf[2];
-  DevBuf io_roots, io_action, io_values, mixed_buf;
+  DevBuf io_roots, io_action, io_values, mixed_buf, z_buf;
   HostBuf host_stage;
 
   ServeState *serve = nullptr;
@@ -55,9 +55,9 @@ struct Ctx {
   int ensure_host(HostBuf &b, size_t bytes);
   int64_t chunk_nodes() const;
   int eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st,
-                 const uint8_t *node_A = nullptr);
+                 const uint8_t *node_A = nullptr, const float *zmap = nullptr, uint32_t zbranch = 0);
   int qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
-                 cudaStream_t st, const uint8_t *node_A = nullptr);
+                 cudaStream_t st, const uint8_t *node_A = nullptr, const ZLeaf *zl = nullptr);
   int run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d_action, float *d_values,
                  int A_stride, cudaStream_t st);
   int run_mixed(const bcts_state *d_roots, const bcts_state *h_roots, const int32_t *depths,

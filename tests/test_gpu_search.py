@@ -132,7 +132,10 @@ def test_atari_scale_sampled_roots(oracle_lib, dev, precision):
 @pytest.mark.parametrize("precision", [p for p in PRECISIONS if p in ("fp32", "bf16", "fp8")])
 def test_fused_render_equals_materialised_frames(oracle_lib, dev, precision):
     """conv1 rendering its operand from node states must see exactly the pixels
-    the frame renderer writes: identical values with and without BCTS_FLAG_FRAMES."""
+    the frame renderer writes.  Without BCTS_FLAG_FRAMES the BF16 and split
+    modes also take the leaves' older three slots from per-parent partial maps
+    (a different summation order), so those agree within the tolerance; FP8
+    renders all four slots either way and agrees exactly."""
     torch, bcts = dev
     A, d = 9, 2
     W = inputs.qnet_weights(A, seed=1234)
@@ -147,5 +150,9 @@ def test_fused_render_equals_materialised_frames(oracle_lib, dev, precision):
             raise
         out.append(bcts.bcts_search(ctx, roots))
         ctx.close()
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1], out[1][1])
+    if precision == "fp8":
+        assert np.array_equal(out[0][0], out[1][0])
+        assert np.array_equal(out[0][1], out[1][1])
+    else:
+        assert value_close(out[0][1], out[1][1], TOL[precision] / 10).all()
+        check_actions(out[0][0], out[1][1].astype(np.float64), TOL[precision] / 10)
