@@ -46,30 +46,101 @@ WORKLOADS = {
                       name="precision form: 8 roots, |A|=18, d=4, leaf Q-net in reduced precision"),
     "batched": dict(n=256, A=18, d=4, gamma=0.99, c=1.0, precision="bf16",
                     name="batched form: 256 roots, d uniform in {1,2,3,4}, |A| in {4,9,18}, BF16, graph-replayed"),
-    "serving": dict(n=1024, A=18, d=4, gamma=0.99, c=1.0, precision="bf16", rate=2000.0, seconds=3.0,
+    "serving": dict(n=1024, A=18, d=4, gamma=0.99, c=1.0, precision="bf16", rate=500.0, seconds=4.0,
                     budget=120 << 30,
                     name="serving form: Poisson requests from 1024 episodes, d in {2,3,4}, |A|=18, BF16, "
                          "120 GB frame budget"),
 }
-# Per-leaf Nature-DQN multiply-accumulates (conv1, conv2, conv3, fc1, fc2 at A=18).
-MACS = {"conv1": 400 * 32 * 256, "conv2": 81 * 64 * 512, "conv3": 49 * 64 * 576, "fc1": 512 * 3136,
-        "fc2": 18 * 512}
 L2_BYTES = 126 * 2 ** 20
-# DRAM bytes (read + write) per node of each tensor-core layer kernel, from the ncu
-# captures summarised in profiles/tc_gemm_layers_4roots_a18_d3.md (launches over
-# 23,328 leaves; traffic grows in proportion to the nodes a launch processes).
-# Algorithmic DRAM bytes per node of each layer (bf16 maps; x2 for the hi + lo maps of the
-# FP32-class mode): conv1 reads the 80-byte node state (frames are rendered on chip) and
-# writes its 400x32 map; later layers read the previous map once and write their own.
-ALG_BYTES_PER_NODE = {"conv1": (80, 400 * 32 * 2), "conv2": (400 * 32 * 2, 81 * 64 * 2),
-                      "conv3": (81 * 64 * 2, 49 * 64 * 2), "fc1": (49 * 64 * 2, 512 * 4)}
-TRAFFIC_PER_NODE = {'fp32/conv1': 48969.9, 'fp32/conv2': 70781.6, 'fp32/conv3': 31745.8, 'fp32/fc1': 14435.4, 'bf16/conv1': 23345.5, 'bf16/conv2': 34822.7, 'bf16/conv3': 15084.4, 'bf16/fc1': 7341.1}
+# Multiply-accumulates per node each kernel class executes (Nature-DQN layers; conv1 over a
+# whole 4-frame stack, over three stack slots for a parent's partial map, over the one new
+# slot for a leaf scored from its parent's partial map).
+EXEC_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 400 * 32 * 192, "conv1_leaf": 400 * 32 * 64,
+             "conv2": 81 * 64 * 512, "conv3": 49 * 64 * 576, "fc1": 512 * 3136}
+# DRAM bytes per node of each tensor-core kernel class, read + write, from the ncu captures
+# of the current kernels summarised in profiles/tc_gemm_layers_4roots_a18_d3.md (launches
+# over 23,328 leaves; traffic grows in proportion to the nodes a launch processes).
+TRAFFIC_PER_NODE = {"fp32/conv1_leaf": 51538.5, "fp32/conv2": 70863.0,
+                    "bf16/conv1_leaf": 25957.4, "bf16/conv2": 34907.3,
+                    "fp8/conv1": 10289.1, "fp8/conv2": 16963.0, "fp8/conv3": 7030.6, "fp8/fc1": 3549.4}
+
+
+def layer_model(cls, precision, A):
+    """Roofline terms of one node of a kernel class: (executed MACs, tensor MMAs per MAC,
+    algorithmic DRAM bytes read, written).  Activation maps are bf16 (2 bytes), bf16 hi + lo
+    in the FP32-class split mode (4 bytes), E4M3 in FP8 (1 byte); the partial conv1 map of a
+    parent is FP32 and each of its A children reads it, so a leaf's share is 1/A of it; the
+    fc1 output is FP32.  Weights stay resident in shared memory (read once per CTA)."""
+    e = {"fp32": 4, "bf16": 2, "fp8": 1}.get(precision, 4)
+    c1, c2, c3, f1 = 400 * 32, 81 * 64, 49 * 64, 512
+    rw = {"conv1": (80, c1 * e), "conv1_partial": (80, c1 * 4), "conv1_leaf": (80 + c1 * 4 / A, c1 * e),
+          "conv2": (c1 * e, c2 * e), "conv3": (c2 * e, c3 * e), "fc1": (c3 * e, f1 * 4),
+          "fc2": (f1 * 4, 4)}.get(cls, (0, 0))
+    macs = EXEC_MACS.get(cls, A * 512 if cls == "fc2" else 0)
+    mma = (2 if cls.startswith("conv1") else 3) if precision == "fp32" else 1
+    return macs, mma, rw[0], rw[1]
+
+
+def class_nodes(cls, n, A, d, prof_cnt):
+    """Nodes one search step sends through a kernel class: every root, depth-1 node and leaf
+    runs the Q-network once; with partial maps the leaves' conv1 is split into the parents'
+    partial maps (depth d-1) and the leaves' last slot."""
+    leaves = n * A ** d if d >= 2 else 0
+    total = n + n * A + leaves
+    partial = prof_cnt.get("conv1_leaf", 0) > 0
+    if cls == "conv1":
+        return total - leaves if partial else total
+    if cls == "conv1_partial":
+        return n * A ** (d - 1) if partial else 0
+    if cls == "conv1_leaf":
+        return leaves if partial else 0
+    return total
+
+
+def roofline_for(dom, precision, A, nodes, ms, launches, pk, pk_kind):
+    """Roofline of the dominant kernel class.  The binding resource is the one whose
+    minimum time (executed tensor FLOPs at the tensor peak for the operand type, or
+    algorithmic DRAM bytes at the measured copy bandwidth) is longer; achieved is that
+    quantity per second over the class's CUDA-event time."""
+    macs, mma, rd, wr = layer_model(dom, precision, A)
+    secs = ms / 1e3
+    bytes_ = (rd + wr) * nodes
+    hbm = pk["hbm_gbs"]
+    if precision == "fp32_simt":
+        peak_t = pk.get("sm_max_mhz", 2032.0) * 1e6 * 148 * 128 * 2 / 1e12
+        t_unit, t_note, t_bound = "TFLOP/s", "FP32 FMA: 148 SMs x 128 lanes x 2 FLOP x max SM clock", "alu"
+        flops = 2.0 * macs * nodes
+    else:
+        ratio = 2.0 if precision == "fp8" else 1.0  # nominal dense fp8 / bf16 = 4.5 / 2.25
+        peak_t = pk["bf16_tflops_sustained"] * ratio
+        flops = 2.0 * macs * nodes * mma  # executed tensor FLOPs (3 or 2 bf16 MMAs per MAC when split)
+        t_unit, t_bound = "TFLOP/s", "tensor"
+        t_note = "bf16 dense sustained" + (" x 2 (nominal fp8/bf16 ratio)" if ratio > 1 else "")
+    t_tensor = flops / (peak_t * 1e12)
+    t_hbm = bytes_ / (hbm * 1e9)
+    per_launch = nodes / max(launches, 1)
+    tpn = TRAFFIC_PER_NODE.get(f"{precision}/{dom}")
+    common = {"kernel": dom, "traffic": tpn * per_launch if tpn else None,
+              "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per node of the current "
+                               "kernel (profiles/tc_gemm_layers_4roots_a18_d3.md) x nodes per launch")
+              if tpn else "no ncu capture of this kernel class",
+              "algorithmic_bytes_per_launch": (rd + wr) * per_launch,
+              "executed_flops_per_launch": flops / max(launches, 1),
+              "avg_launch_ms": ms / max(launches, 1), "launches": launches,
+              "min_time_ms": {"tensor_or_alu": 1e3 * t_tensor, "hbm": 1e3 * t_hbm}}
+    if t_hbm >= t_tensor:
+        ach = bytes_ / secs / 1e9
+        return dict(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                    peak_note=f"STREAM-style copy bandwidth (of {pk_kind})", **common)
+    ach = flops / secs / 1e12
+    return dict(bound=t_bound, achieved=ach, peak=peak_t, unit=t_unit, frac=ach / peak_t,
+                peak_note=f"{t_note} (of {pk_kind})", **common)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="atari", choices=sorted(WORKLOADS))
@@ -283,44 +354,9 @@ def run_ours(args, wl):
     # dominant kernel class by device time inside the timed region
     dom = max(prof_ms, key=lambda k: prof_ms[k])
     roofline = None
-    if dom in MACS and prof_ms[dom] > 0:
-        # every leaf, root and depth-1 node runs the Q-network once per step
-        nodes = args.steps * (leaves + n + n * A) if d >= 2 else args.steps * (n + n * A)
-        macs = MACS[dom] if dom != "fc2" else A * 512
-        flops = 2.0 * macs * nodes
-        achieved = flops / (prof_ms[dom] / 1e3) / 1e12
-        mma_per_mac = 1
-        if precision == "fp32_simt":
-            peak = pk.get("sm_max_mhz", 2032.0) * 1e6 * 148 * 128 * 2 / 1e12
-            bound, unit, pnote = "alu", "TFLOP/s", "FP32 FMA: 148 SMs x 128 lanes x 2 FLOP x max SM clock"
-        else:
-            # FP32-class split mode runs hi*hi + hi*lo + lo*hi bf16 MMAs per MAC (2 for
-            # conv1, whose pixels are exact in bf16): its ceiling is the bf16 peak / that.
-            if precision == "fp32":
-                mma_per_mac = 2 if dom == "conv1" else 3
-            peak = pk["bf16_tflops_sustained"] / mma_per_mac
-            bound, unit = "tensor", "TFLOP/s"
-            pnote = (f"bf16 dense sustained ({pk_kind}) / {mma_per_mac} bf16 MMAs per algorithmic MAC"
-                     if mma_per_mac > 1 else f"bf16 dense sustained ({pk_kind})")
-        tpn = TRAFFIC_PER_NODE.get(f"{precision}/{dom}")
-        traffic = tpn * nodes / prof_cnt[dom] if tpn and prof_cnt[dom] else None
-        roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                    "frac": achieved / peak, "traffic": traffic,
-                    "traffic_note": ("DRAM bytes per launch: per-node bytes from the ncu capture of "
-                                     "profiles/tc_gemm_layers_4roots_a18_d3.md x nodes per launch") if traffic else None,
-                    "algorithmic_bytes_per_launch": (
-                        (lambda rb, wb: ((rb if dom == "conv1" else rb * (2 if precision == "fp32" else 1)) +
-                                         (wb if dom == "fc1" else wb * (2 if precision == "fp32" else 1))))(
-                            *ALG_BYTES_PER_NODE[dom]) * nodes / prof_cnt[dom] if prof_cnt[dom] else None),
-                    "peak_note": pnote + " (of measured)",
-                    "mma_per_mac": mma_per_mac,
-                    "executed_frac_of_bf16_peak": (achieved * mma_per_mac / pk["bf16_tflops_sustained"]
-                                                   if bound == "tensor" else None),
-                    "avg_launch_ms": prof_ms[dom] / max(prof_cnt[dom], 1)}
-    elif prof_ms[dom] > 0:
-        roofline = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": None, "traffic": None}
-
+    if prof_ms[dom] > 0:
+        nodes = args.steps * class_nodes(dom, n, A, d, prof_cnt)
+        roofline = roofline_for(dom, precision, A, nodes, prof_ms[dom], prof_cnt[dom], pk, pk_kind)
     plain = None
     if not args.no_plain and precision != "fp32_simt":
         # the plain FP32 method: CUDA-core Q-network, one root per launch
@@ -479,10 +515,15 @@ def run_serving(args, wl):
     def uniform():
         return (next(g) >> 11) / float(1 << 53)
 
-    # warm-up: every depth once (graphs, autotuner, lazy buffers)
+    # warm-up: every depth alone, then two full-size mixed bursts, so that both
+    # workers have sized their buffers and tuned their leaf chunks before the clock
     for d in (2, 3, 4):
         t = bcts.bcts_submit(ctx, episodes[:1], d, A)
         bcts.bcts_poll(ctx, t, A, timeout_us=-1)
+    for _ in range(2):
+        tks = [bcts.bcts_submit(ctx, episodes[i:i + 1], (2, 3, 4)[i % 3], A) for i in range(256)]
+        for t in tks:
+            bcts.bcts_poll(ctx, t, A, timeout_us=-1)
     busy = set()
     pending = {}  # ticket -> (episode, submit time)
     lat, done_leaves, completed = [], 0, 0
@@ -493,7 +534,10 @@ def run_serving(args, wl):
     with ClockSampler(local) as clk:
         while True:
             now = time.perf_counter()
-            while next_arrival <= now and next_arrival - t0 < seconds:
+            # an arrival needs an idle episode; while every episode waits for its
+            # decision, arrivals are deferred (their latency still counts from the
+            # scheduled arrival time)
+            while next_arrival <= now and next_arrival - t0 < seconds and len(busy) < wl["n"]:
                 e = int(next(g) % wl["n"])
                 while e in busy:
                     e = (e + 1) % wl["n"]

@@ -169,9 +169,13 @@ BCTS_API int bcts_search_mixed(bcts_ctx *ctx, const bcts_state *roots, const int
 /*
  * Serving form: continuous batching.  bcts_submit queues one decision request
  * (root, depth d in [0, 6], A in [1, context A]) and returns at once with a
- * ticket; a scheduler thread admits queued requests while their leaf work fits
- * the frame budget, runs the admitted requests' levels together on the device,
- * and completes them independently.  bcts_poll waits up to timeout_us
+ * ticket.  Two worker threads (each with its own stream and buffers, sharing
+ * the context's weights) take queued requests in arrival order while their
+ * leaf work fits the frame budget (A^d x 28,224 bytes per request, default
+ * 8 GiB, at most max_roots per pass, default 64) and run each admitted set as
+ * one batched pass (bcts_search_mixed); while one pass is on the device, a
+ * worker with fewer than about 1M queued leaves waits up to 2 ms for more.
+ * Requests complete independently.  bcts_poll waits up to timeout_us
  * microseconds (0 = do not wait, <0 = wait without limit) for a ticket:
  * BCTS_OK with out_action (1 int32) and out_root_values (A floats, host)
  * filled and the ticket released; BCTS_PENDING if not finished; BCTS_ENOTICKET
@@ -201,10 +205,15 @@ BCTS_API int bcts_env_step(const bcts_state *s, int a, bcts_state *out, int *rew
 BCTS_API int bcts_render(const bcts_state *d_states, int64_t n, uint8_t *d_frames, void *stream);
 
 /* ---- measurement ------------------------------------------------------------ */
-/* Kernel classes timed by bcts_profile. */
+/* Kernel classes timed by bcts_profile.  BCTS_KERN_CONV1 is conv1 over whole
+ * frame stacks; when a search scores its leaves from their parents' partial
+ * conv1 maps (frame-stacking linearity: the three older history slots of a
+ * leaf are its parent's three newest), the parents' maps are
+ * BCTS_KERN_CONV1_PARTIAL and the leaves' remaining slot BCTS_KERN_CONV1_LEAF. */
 enum {
     BCTS_KERN_EXPAND = 0, BCTS_KERN_RENDER, BCTS_KERN_CONV1, BCTS_KERN_CONV2, BCTS_KERN_CONV3,
-    BCTS_KERN_FC1, BCTS_KERN_FC2, BCTS_KERN_BACKUP, BCTS_KERN_COUNT
+    BCTS_KERN_FC1, BCTS_KERN_FC2, BCTS_KERN_BACKUP, BCTS_KERN_CONV1_PARTIAL, BCTS_KERN_CONV1_LEAF,
+    BCTS_KERN_COUNT
 };
 
 /*
@@ -221,6 +230,14 @@ BCTS_API int bcts_profile(bcts_ctx *ctx, int enable, double *out_ms, int64_t *ou
 
 /* Score n frame stacks with the context's Q-network in its precision: q [n][A] floats. */
 BCTS_API int bcts_qnet(bcts_ctx *ctx, const uint8_t *d_frames, int64_t n, float *d_q, void *stream);
+
+/* Failure-path self-test (no counterpart in the paper): runs one device wait on
+ * an mbarrier that nothing arrives on, with the same bounded-wait code the
+ * Q-network kernels use, limited to timeout_us microseconds (1 .. 2e6).  The
+ * wait must give up and report through the device error word: the call returns
+ * BCTS_ETIMEOUT when it did (the expected outcome) and BCTS_OK if no time-out
+ * was reported.  Nothing faults, traps or hangs; the device stays usable. */
+BCTS_API int bcts_selftest_wait(int timeout_us);
 
 /* ---- allocation-free Q-network evaluation ------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that

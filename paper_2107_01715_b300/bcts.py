@@ -31,10 +31,11 @@ PRECISIONS = {"fp32": BCTS_PREC_FP32, "bf16": BCTS_PREC_BF16, "fp8": BCTS_PREC_F
 
 EXPORTED = ["bcts_qnet_numel", "bcts_create", "bcts_destroy", "bcts_last_error", "bcts_search",
             "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll", "bcts_expand",
-            "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step"]
+            "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait"]
 BCTS_STATIC_MAX_NODES = 128
 BCTS_FLAG_FRAMES = 1
-KERNEL_CLASSES = ["expand", "render", "conv1", "conv2", "conv3", "fc1", "fc2", "backup"]
+KERNEL_CLASSES = ["expand", "render", "conv1", "conv2", "conv3", "fc1", "fc2", "backup", "conv1_partial",
+                  "conv1_leaf"]
 
 
 class bcts_options(ctypes.Structure):
@@ -68,8 +69,9 @@ lib.bcts_qnet.argtypes = [_P, _P, _I64, _P, _P]
 lib.bcts_profile.argtypes = [_P, _I, _P, _P, _P]
 lib.bcts_qnet_static.argtypes = [_P, _I, _P, _I64, _P, _P]
 lib.bcts_env_step.argtypes = [_P, _I, _P, ctypes.POINTER(_I)]
+lib.bcts_selftest_wait.argtypes = [_I]
 for _f in ("bcts_search", "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll",
-           "bcts_expand", "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step"):
+           "bcts_expand", "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait"):
     getattr(lib, _f).restype = _I
 
 
@@ -245,3 +247,8 @@ def bcts_env_step(state, a: int):
     r = _I()
     _check(lib.bcts_env_step(s.ctypes.data, int(a), out.ctypes.data, ctypes.byref(r)))
     return out[0], int(r.value)
+
+
+def bcts_selftest_wait(timeout_us: int) -> int:
+    """Run the bounded-wait self-test; returns the raw status (BCTS_ETIMEOUT expected)."""
+    return int(lib.bcts_selftest_wait(int(timeout_us)))

@@ -46,13 +46,20 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
   uint64_t generation = 0;
+  uint64_t last_use = 0;
 };
+
+// Bounds of the per-context caches: a serving stream produces a new batch
+// composition nearly every pass, so neither map may grow without limit.
+constexpr size_t kMaxGraphs = 64;
+constexpr size_t kMaxSeen = 4096;
 
 struct MixedState {
   DevBuf roots, q0, L1, r1, maxq1, nodeA1, mid[2], Rmid[2], leaves, Rleaf, maxq_leaf, nodeA_leaf, V, act, val;
   HostBuf host;
   std::map<std::string, int> seen;
   std::map<std::string, GraphEntry> graphs;
+  uint64_t use_clock = 0;
   std::map<std::string, int64_t> tuned_chunk;  // leaf-count bucket -> chunk
   bool tune_loaded = false;
   ~MixedState() {
@@ -319,16 +326,25 @@ int Ctx::run_mixed(const bcts_state *, const bcts_state *h_roots, const int32_t 
   char *hs = static_cast<char *>(m->host.p);
   for (int i = 0; i < n; ++i) std::memcpy(hs + size_t(i) * kStateBytes, h_roots + pl.order[i], kStateBytes);
   if ((rc = autotune_chunk(this, m, pl, stream)) != BCTS_OK) return rc;
+  if (m->seen.size() >= kMaxSeen) m->seen.clear();
   const int times_seen = m->seen[pl.key]++;
   auto git = m->graphs.find(pl.key);
   if (git != m->graphs.end() && git->second.generation == buf_generation && git->second.exec) {
+    git->second.last_use = ++m->use_clock;
     BCTS_CUDA_TRY(cudaGraphLaunch(git->second.exec, stream), err);
     profiler_add(prof, git->second.launches);
   } else if (times_seen >= 1) {
     // second pass of this composition: capture it, then replay from now on
-    if (git != m->graphs.end() && git->second.exec) {
-      cudaGraphExecDestroy(git->second.exec);
+    if (git != m->graphs.end()) {
+      if (git->second.exec) cudaGraphExecDestroy(git->second.exec);
       m->graphs.erase(git);
+    }
+    if (m->graphs.size() >= kMaxGraphs) {  // evict the least recently launched graph
+      auto lru = m->graphs.begin();
+      for (auto it = m->graphs.begin(); it != m->graphs.end(); ++it)
+        if (it->second.last_use < lru->second.last_use) lru = it;
+      if (lru->second.exec) cudaGraphExecDestroy(lru->second.exec);
+      m->graphs.erase(lru);
     }
     Profiler *counter = profiler_create();
     cudaGraph_t graph = nullptr;
@@ -355,6 +371,7 @@ int Ctx::run_mixed(const bcts_state *, const bcts_state *h_roots, const int32_t 
     }
     e.launches = launches;
     e.generation = buf_generation;
+    e.last_use = ++m->use_clock;
     m->graphs[pl.key] = e;
     BCTS_CUDA_TRY(cudaGraphLaunch(e.exec, stream), err);
     profiler_add(prof, launches);

@@ -6,6 +6,8 @@
 
 namespace bcts {
 
+static_assert(int(K_COUNT) == int(BCTS_KERN_COUNT), "kernel classes must match the public enum");
+
 struct Profiler {
   bool on = false;
   struct Pair {

@@ -202,14 +202,14 @@ constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at the maximum SM 
 // Bounded mbarrier wait.  On time-out: error code into the device error word,
 // abort flag for the whole CTA, returns false.
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *d_err,
-                                         int code) {
+                                         int code, long long limit = kWaitCycles) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   int spins = 0;
   while (!mbar_try(bar, parity)) {
     if (*abort_flag) return false;
     if (++spins > 4096) __nanosleep(32);
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       if (d_err) atomicCAS(d_err, 0, code);
       return false;
@@ -263,11 +263,18 @@ struct Cfg {
   using G = Geo<LAYER>;
   static constexpr bool SPLIT = MODE == 1, FP8 = MODE == 2;
   static constexpr int EB = FP8 ? 1 : 2;              // bytes per element
-  static_assert(V == 0 || (LAYER == 1 && !FP8), "conv1 variants are bf16 / split only");
-  static constexpr int SLOT0 = V == 1 ? 1 : (V == 2 ? 3 : 0);  // first history slot read (K block 0)
-  static constexpr int WC0 = V == 2 ? 3 : 0;                     // first weight channel used
+  static_assert(V == 0 || LAYER == 1, "partial-map variants are conv1 only");
+  // A 128-byte K block holds one history slot (bf16) or two (E4M3: slots 2j, 2j + 1).
+  // V1 (a parent's partial map) multiplies weight channels 0-2 with the parent's
+  // slots 1-3; V2 (a leaf) weight channel 3 with the leaf's slot 3.
+  static constexpr int SLOT0 = V == 1 ? 1 : (V == 2 ? (FP8 ? 2 : 3) : 0);  // slot of K block 0 (first half)
+  static constexpr int WC0 = V == 2 ? (FP8 ? 1 : 3) : 0;                   // first weight K block used
   static constexpr int KB_FULL = FP8 ? (G::K + 127) / 128 : G::K / 64;
-  static constexpr int KB = V == 1 ? 3 : (V == 2 ? 1 : KB_FULL);  // K blocks this kernel multiplies
+  static constexpr int KB = V == 1 ? (FP8 ? 2 : 3) : (V == 2 ? 1 : KB_FULL);  // K blocks this kernel multiplies
+  // K steps (32 bytes each, four per K block) that carry data: E4M3 V2 uses only
+  // the second half of its K block (slot 3), E4M3 V1 only the first half of its last
+  static constexpr int J0 = (FP8 && V == 2) ? 2 : 0;  // first K step of K block 0
+  static constexpr int JL = (FP8 && V == 1) ? 2 : 4;  // K steps of the last K block
   static constexpr int KPAD = KB_FULL * (128 / EB);  // stored weight row length in elements
   static constexpr bool A_LO = SPLIT && LAYER != 1;  // conv1's integer pixels are exact in bf16
   static constexpr bool B_RES = LAYER == 1;          // conv1's weights (16 / 32 KB) stay in shared memory
@@ -470,11 +477,16 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
         for (int j = 0; j < KB; ++j) {
           uint32_t wrote = 0u;
           const uint32_t leaf = leaf0 + uint32_t(li);
-          const uint4 Pv = FP8 ? ((cc >> 2) ? P[(2 * j + 1) & 3] : P[(2 * j) & 3]) : P[(C::SLOT0 + j) & 3];
+          const int slot = FP8 ? C::SLOT0 + 2 * j + (cc >> 2) : C::SLOT0 + j;
+          // E4M3 partial-map variants leave the halves their MMAs skip unrendered
+          const bool used = slot <= 3 && !(FP8 && V == 2 && cc < 4);
+          // the slot depends on the chunk (E4M3): read it from the state ring, not
+          // from a runtime-indexed register array (which would live in local memory)
+          const uint4 Pv = FP8 ? Ps[slot & 3] : P[slot & 3];
           const uint32_t wk = (k & 2) ? ((k & 1) ? Pv.w : Pv.z) : ((k & 1) ? Pv.y : Pv.x);
           const int ox = int(int16_t(wk & 0xFFFFu)) - dx, oy = int(int16_t(wk >> 16)) - dy;
           const uint32_t m = leaf * uint32_t(kP1) + uint32_t(oy * 20 + ox);
-          if (leaf <= leaf_last && ox >= 0 && ox <= 19 && oy >= 0 && oy <= 19 && m >= m0 && m <= mlast) {
+          if (used && leaf <= leaf_last && ox >= 0 && ox <= 19 && oy >= 0 && oy <= 19 && m >= m0 && m <= mlast) {
             int oxs[4], oys[4];
             unpack_slot(Pv, oxs, oys);
             uint4 v;
@@ -652,8 +664,9 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
           const uint32_t sB = C::B_RES ? res + uint32_t(kb) * (C::B_ROWS * 128) : sB_of(s);
           const uint32_t sBlo = sB + C::B_BYTES;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {  // K = 16 bf16 = 32 bytes per instruction
-            const uint32_t first = (kb | j) != 0;
+          for (int j = 0; j < 4; ++j) {  // K = 16 bf16 / 32 E4M3 = 32 bytes per instruction
+            if ((kb == 0 && j < C::J0) || (kb == KB - 1 && j >= C::JL)) continue;
+            const uint32_t first = (kb != 0 || j != C::J0) ? 1u : 0u;
             const uint64_t a = sw128_desc(sA) + uint64_t(2 * j);
             const uint64_t b = sw128_desc(sB) + uint64_t(2 * j);
             if (FP8) {
@@ -778,6 +791,13 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
 #pragma unroll
           for (int e = 0; e < 4; ++e) {  // the partial carries the bias
             const float4 z4 = *reinterpret_cast<const float4 *>(stg + lane * kStgRow + j * 64 + e * 16);
+            const int n = n0 + j * 16 + 4 * e;
+            if (FP8) {  // E4M3 accumulators carry the weight and input scales
+              v[4 * e] *= scale_s[n];
+              v[4 * e + 1] *= scale_s[n + 1];
+              v[4 * e + 2] *= scale_s[n + 2];
+              v[4 * e + 3] *= scale_s[n + 3];
+            }
             v[4 * e] = fmaxf(v[4 * e] + z4.x, 0.f);
             v[4 * e + 1] = fmaxf(v[4 * e + 1] + z4.y, 0.f);
             v[4 * e + 2] = fmaxf(v[4 * e + 2] + z4.z, 0.f);
@@ -785,7 +805,10 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
           }
         } else if constexpr (V == 1) {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] += bias_s[n0 + j * 16 + e];  // partial sum: no ReLU yet
+          for (int e = 0; e < 16; ++e) {  // partial sum: no ReLU yet
+            const int n = n0 + j * 16 + e;
+            v[e] = FP8 ? fmaf(v[e], scale_s[n], bias_s[n]) : v[e] + bias_s[n];
+          }
         } else {
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
@@ -1087,16 +1110,11 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
     p.out_lo = o_lo;
   };
   layer(0, states ? static_cast<const void *>(states) : static_cast<const void *>(frames), nullptr, a1, a1l);
-  if constexpr (MODE != 2) {
-    if (zl && states) {
-      p.zmap = zl->zmap;
-      p.z_leaf0 = zl->leaf0;
-      p.z_branch = zl->branch;
-      rc = tc::launch<1, MODE, true, 2>(p, (long long)n * kP1, K_CONV1, st);
-    } else {
-      rc = states ? tc::launch<1, MODE, true>(p, (long long)n * kP1, K_CONV1, st)
-                  : tc::launch<1, MODE, false>(p, (long long)n * kP1, K_CONV1, st);
-    }
+  if (zl && states) {
+    p.zmap = zl->zmap;
+    p.z_leaf0 = zl->leaf0;
+    p.z_branch = zl->branch;
+    rc = tc::launch<1, MODE, true, 2>(p, (long long)n * kP1, K_CONV1_LEAF, st);
   } else {
     rc = states ? tc::launch<1, MODE, true>(p, (long long)n * kP1, K_CONV1, st)
                 : tc::launch<1, MODE, false>(p, (long long)n * kP1, K_CONV1, st);
@@ -1119,11 +1137,13 @@ int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts
   if (w->precision == BCTS_PREC_FP32)
     return tc_forward_impl<1>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl);
   if (w->precision == BCTS_PREC_FP8)
-    return tc_forward_impl<2>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, nullptr);
+    return tc_forward_impl<2>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl);
   return tc_forward_impl<0>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl);
 }
 
-bool tc_has_partial(const TcWeights *w) { return w->precision == BCTS_PREC_FP32 || w->precision == BCTS_PREC_BF16; }
+bool tc_has_partial(const TcWeights *w) {
+  return w->precision == BCTS_PREC_FP32 || w->precision == BCTS_PREC_BF16 || w->precision == BCTS_PREC_FP8;
+}
 
 // Parent partial maps Z = W_0 * slot1 + W_1 * slot2 + W_2 * slot3 + b, FP32 [n][400][32].
 int tc_conv1_partial(const TcWeights *w, const bcts_state *states, int64_t n, float *z, cudaStream_t st, int *d_err) {
@@ -1136,9 +1156,67 @@ int tc_conv1_partial(const TcWeights *w, const bcts_state *states, int64_t n, fl
   p.bias = w->bias[0];
   p.colscale = w->colscale[0];
   p.out_hi = z;
-  if (w->precision == BCTS_PREC_FP32) return tc::launch<1, 1, true, 1>(p, (long long)n * kP1, K_CONV1, st);
-  if (w->precision == BCTS_PREC_BF16) return tc::launch<1, 0, true, 1>(p, (long long)n * kP1, K_CONV1, st);
+  if (w->precision == BCTS_PREC_FP32) return tc::launch<1, 1, true, 1>(p, (long long)n * kP1, K_CONV1_PARTIAL, st);
+  if (w->precision == BCTS_PREC_BF16) return tc::launch<1, 0, true, 1>(p, (long long)n * kP1, K_CONV1_PARTIAL, st);
+  if (w->precision == BCTS_PREC_FP8) return tc::launch<1, 2, true, 1>(p, (long long)n * kP1, K_CONV1_PARTIAL, st);
   return BCTS_ENOKERNEL;
 }
 
 }  // namespace bcts
+
+// ---------------------------------------------------------------------------
+// Failure-path self-test: one bounded wait on an mbarrier that nothing ever
+// arrives on.  It must give up after `limit` cycles and report through the
+// error word, leaving the context usable.
+// ---------------------------------------------------------------------------
+namespace bcts {
+namespace {
+__global__ void wait_probe_kernel(int *d_err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) tc::wait_bar(tc::smem_u32(&bar), 0, &abort_flag, d_err, 7, limit);
+}
+}  // namespace
+}  // namespace bcts
+
+extern "C" int bcts_selftest_wait(int timeout_us) {
+  if (timeout_us < 1 || timeout_us > 2000000) {
+    bcts::set_thread_error("bcts_selftest_wait: timeout_us must be in [1, 2e6]");
+    return BCTS_EINVAL;
+  }
+  int dev = 0, khz = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess) {
+    cudaGetLastError();
+    bcts::set_thread_error("bcts_selftest_wait: no CUDA device");
+    return BCTS_ECUDA;
+  }
+  int *d_err = nullptr;
+  if (cudaMalloc(&d_err, sizeof(int)) != cudaSuccess || cudaMemset(d_err, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    bcts::set_thread_error("bcts_selftest_wait: allocation failed");
+    return BCTS_ENOMEM;
+  }
+  const long long limit = (long long)timeout_us * (long long)(khz > 0 ? khz : 2000000) / 1000;
+  bcts::wait_probe_kernel<<<1, 32>>>(d_err, limit);
+  int herr = 0;
+  const cudaError_t e1 = cudaGetLastError();
+  const cudaError_t e2 = cudaDeviceSynchronize();
+  const cudaError_t e3 = cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d_err);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    bcts::set_thread_error("bcts_selftest_wait: CUDA error");
+    return BCTS_ECUDA;
+  }
+  if (herr == 7) {
+    bcts::set_thread_error("bcts_selftest_wait: the bounded wait ran out and reported it (expected)");
+    return BCTS_ETIMEOUT;
+  }
+  bcts::set_thread_error("bcts_selftest_wait: the wait did not report a time-out");
+  return BCTS_OK;
+}

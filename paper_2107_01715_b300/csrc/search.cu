@@ -129,17 +129,28 @@ int Ctx::fail(int code, const std::string &msg) {
 
 int Ctx::ensure(DevBuf &b, size_t bytes) {
   if (bytes <= b.cap) return BCTS_OK;
+  const size_t old_cap = b.cap;
   if (b.p) {
     cudaStreamSynchronize(stream);
     cudaFree(b.p);
     b.p = nullptr;
     b.cap = 0;
   }
-  const size_t want = (bytes + 255) & ~size_t(255);
+  // Grow by at least half of the old capacity, so that a slowly rising size
+  // (a serving load ramping up) reallocates only O(log) times: every
+  // reallocation synchronises the device and invalidates captured graphs.
+  const size_t exact = (bytes + 255) & ~size_t(255);
+  const size_t grown = (std::max(exact, old_cap + old_cap / 2) + 255) & ~size_t(255);
   ++buf_generation;
+  size_t want = grown;
   if (cudaMalloc(&b.p, want) != cudaSuccess) {
     cudaGetLastError();
-    return fail(BCTS_ENOMEM, "device allocation of " + std::to_string(want) + " bytes failed");
+    want = exact;
+    if (want == grown || cudaMalloc(&b.p, want) != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      return fail(BCTS_ENOMEM, "device allocation of " + std::to_string(want) + " bytes failed");
+    }
   }
   b.cap = want;
   return BCTS_OK;

@@ -42,12 +42,17 @@ struct ServeState {
   bool stop = false;
   size_t budget = 0, inflight = 0;
   int max_batch = 64;
+  int busy_workers = 0;
+  size_t queued_cost = 0;  // sum of the queued requests' costs
   static constexpr int kWorkers = 2;
   std::thread worker[kWorkers];
   Ctx *wctx[kWorkers] = {};
 };
 
 namespace {
+
+constexpr auto kWindow = std::chrono::microseconds(2000);
+constexpr size_t kFullPassLeaves = size_t(1) << 20;  // about 1M leaves keep all SMs busy
 
 size_t request_cost(int A, int d) {
   size_t leaves = 1;
@@ -65,6 +70,9 @@ Ctx *clone_ctx(const Ctx *o) {
   c->corr = o->corr;
   c->precision = o->precision;
   c->opt = o->opt;
+  // serving passes rarely repeat a composition: a fixed leaf chunk instead of
+  // timing candidates on the first pass of every new size
+  if (c->opt.leaf_chunk <= 0) c->opt.leaf_chunk = 32768;
   c->simt = o->simt;
   c->tc = o->tc;
   c->tc_fused_render = o->tc_fused_render;
@@ -92,6 +100,16 @@ void worker_loop(ServeState *s, int w) {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
       if (s->stop && s->queue.empty()) return;
+      // batching window: while another pass keeps the GPU busy, a small queue
+      // waits (up to kWindow) for more requests, so that passes stay large
+      // enough to fill the device instead of splitting the load into many
+      // small passes; an idle device starts at once
+      const auto until = std::chrono::steady_clock::now() + kWindow;
+      while (!s->stop && s->busy_workers > 0 && int(s->queue.size()) < s->max_batch &&
+             s->queued_cost < kFullPassLeaves * size_t(kFrameBytes)) {
+        if (s->cv_work.wait_until(lk, until) == std::cv_status::timeout) break;
+      }
+      if (s->queue.empty()) continue;
       batch.clear();
       // admission: FIFO while the pass limit and the budget allow (the first
       // request of a pass is always admitted once nothing else is in flight)
@@ -100,6 +118,7 @@ void worker_loop(ServeState *s, int w) {
         const bool fits = s->inflight + cost + r.cost <= s->budget;
         if (!fits && !(batch.empty() && s->inflight == 0)) break;
         cost += r.cost;
+        s->queued_cost -= r.cost;
         batch.push_back(s->queue.front());
         s->queue.pop_front();
       }
@@ -109,6 +128,7 @@ void worker_loop(ServeState *s, int w) {
         continue;
       }
       s->inflight += cost;
+      ++s->busy_workers;
       roots.resize(batch.size());
       depths.resize(batch.size());
       actions.resize(batch.size());
@@ -138,6 +158,7 @@ void worker_loop(ServeState *s, int w) {
         }
       }
       s->inflight -= cost;
+      --s->busy_workers;
     }
     s->cv_done.notify_all();
     s->cv_work.notify_all();
@@ -205,6 +226,7 @@ extern "C" int bcts_submit(bcts_ctx *ctx, const bcts_state *root, int d, int A, 
     r.d = d;
     r.A = A;
     r.cost = bcts::request_cost(A, d);
+    s->queued_cost += r.cost;
     s->queue.push_back(t);
     *out_ticket = t;
   }
