@@ -128,50 +128,70 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   }
 }
 
-// FC2 + max over actions: one warp per node.  q = W2 h + b2; maxq = max_a q[a]
-// (first maximum on ties).
+// FC2 + max over actions: q = W2 h + b2, maxq = max_a q[a].  A persistent grid:
+// each block stages W2 (A x 512, at most 36 KB) in shared memory once and its
+// warps then take nodes in turn.  Lane l holds h[4 l + 128 j .. + 3]; its 16
+// products per action are summed across the warp by a reduce-scatter butterfly
+// (31 shuffles for all actions at once), after which lane a holds q[a].
 __global__ void __launch_bounds__(256) fc2_max_kernel(const float *__restrict__ h, const float *__restrict__ W2,
                                                       const float *__restrict__ b2, int A, int64_t n,
                                                       float *__restrict__ q, float *__restrict__ maxq,
                                                       const uint8_t *__restrict__ node_A) {
-  __shared__ float w[kMaxA * kF1];
+  __shared__ __align__(16) float w[kMaxA * kF1];
   for (int i = threadIdx.x; i < A * kF1; i += blockDim.x) w[i] = W2[i];
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int64_t node = int64_t(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5);
-  if (node >= n) return;
-  float x[16];
-  const float4 *hv = reinterpret_cast<const float4 *>(h + node * kF1);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float4 t = __ldg(hv + lane + 32 * j);
-    x[4 * j] = t.x;
-    x[4 * j + 1] = t.y;
-    x[4 * j + 2] = t.z;
-    x[4 * j + 3] = t.w;
-  }
-  // node_A (batched form): this node's own action count; the max runs over its
-  // first node_A[node] actions (q still receives all A columns)
-  const int An = node_A ? int(node_A[node]) : A;
-  float best = 0.f;
-  for (int a = 0; a < A; ++a) {
-    const float *wa = w + a * kF1;
-    float s = 0.f;
+  const float bias = lane < A ? __ldg(b2 + lane) : 0.f;
+  const int64_t nwarps = int64_t(gridDim.x) * (blockDim.x / 32);
+  for (int64_t node = int64_t(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5); node < n; node += nwarps) {
+    float x[16];
+    const float4 *hv = reinterpret_cast<const float4 *>(h + node * kF1);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int base = 4 * (lane + 32 * j);
-      s = fmaf(x[4 * j], wa[base], s);
-      s = fmaf(x[4 * j + 1], wa[base + 1], s);
-      s = fmaf(x[4 * j + 2], wa[base + 2], s);
-      s = fmaf(x[4 * j + 3], wa[base + 3], s);
+      const float4 t = __ldg(hv + lane + 32 * j);
+      x[4 * j] = t.x;
+      x[4 * j + 1] = t.y;
+      x[4 * j + 2] = t.z;
+      x[4 * j + 3] = t.w;
     }
+    float v[32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    s += __ldg(b2 + a);
-    if (q && lane == 0) q[node * A + a] = s;
-    if (a < An && (a == 0 || s > best)) best = s;
+    for (int a = 0; a < 32; ++a) {
+      float s = 0.f;
+      if (a < kMaxA && a < A) {
+        const float4 *wa = reinterpret_cast<const float4 *>(w + a * kF1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 c = wa[lane + 32 * j];
+          s = fmaf(x[4 * j], c.x, s);
+          s = fmaf(x[4 * j + 1], c.y, s);
+          s = fmaf(x[4 * j + 2], c.z, s);
+          s = fmaf(x[4 * j + 3], c.w, s);
+        }
+      }
+      v[a] = s;
+    }
+    // reduce-scatter: at offset o a lane keeps the half of its remaining actions
+    // selected by its bit o and receives its partner's partial sums for them
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < o; ++i) {
+        const float send = up ? v[i] : v[i + o];
+        const float keep = up ? v[i + o] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    const float s = v[0] + bias;  // q[node][lane] for lane < A
+    if (q && lane < A) q[node * A + lane] = s;
+    // node_A (batched form): the max runs over this node's own first node_A actions
+    const int An = node_A ? int(node_A[node]) : A;
+    float best = lane < An ? s : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (maxq && lane == 0) maxq[node] = best;
   }
-  if (maxq && lane == 0) maxq[node] = best;
 }
 
 template <class Geo, int BM, int BN, int TM, int TN>
@@ -210,8 +230,17 @@ int launch_fc2_max(const float *h, const float *W2, const float *b2, int A, int6
                    cudaStream_t st, const uint8_t *node_A) {
   if (n <= 0) return BCTS_OK;
   const int warps = 8;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
+  }
+  // persistent: four blocks per SM (36 KB of W2 each), never more blocks than node groups
+  const int64_t groups = (n + warps - 1) / warps;
+  const unsigned grid = unsigned(groups < int64_t(4) * sms ? groups : int64_t(4) * sms);
   ProfScope ps(K_FC2, st);
-  fc2_max_kernel<<<unsigned((n + warps - 1) / warps), warps * 32, 0, st>>>(h, W2, b2, A, n, q, maxq, node_A);
+  fc2_max_kernel<<<grid, warps * 32, 0, st>>>(h, W2, b2, A, n, q, maxq, node_A);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 

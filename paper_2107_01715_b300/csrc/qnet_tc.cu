@@ -297,6 +297,10 @@ struct Cfg {
   // conv1 (32-column tiles, the lightest epilogue) runs two epilogue warpgroups
   // on alternating tiles so each has two tiles' time to hide its load latency
   static constexpr int EPI_WG = LAYER == 1 ? 2 : 1;
+  // contiguous tile range per CTA (see the tile schedule in the kernel): the
+  // conv1 leaf variant (siblings share a parent's partial map) and conv2/conv3
+  // (neighbouring output rows share input rows) gain from it; fc1 does not
+  static constexpr bool CONTIG = V == 2 || LAYER == 2 || LAYER == 3;
   static constexpr int MMA_WARP = 8 + 4 * EPI_WG;
   static constexpr int THREADS = 32 * (MMA_WARP + 1);
   static constexpr int SMEM = RES_BYTES + STAGES * STAGE_BYTES + 1024 + kBarBytes + DIRTY_BYTES + 2 * G::NTOT * 4 +
@@ -366,6 +370,19 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
   static_assert(8 * (2 * S + 2 * C::NUM_ACC + 2) + 8 <= kBarBytes, "barrier area");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto sA_of = [&](int s) { return stage0 + uint32_t(s) * C::STAGE_BYTES; };
+  // Tile schedule, the same for every role: CTA b takes tiles T0, T0 + TS, ...
+  // below TE.  Grid-stride, or one contiguous range per CTA (CONTIG): then the
+  // tiles of a parent's children (which all read that parent's partial map) run
+  // on one SM and the map is read from L1 rather than once per child from L2,
+  // and consecutive conv2/conv3 tiles re-read each other's input rows while they
+  // are still in L2.
+  int T0 = blockIdx.x, TS = gridDim.x, TE = p.num_tiles;
+  if (C::CONTIG) {
+    const int per = (p.num_tiles + int(gridDim.x) - 1) / int(gridDim.x);
+    T0 = int(blockIdx.x) * per;
+    TS = 1;
+    TE = T0 + per < p.num_tiles ? T0 + per : p.num_tiles;
+  }
   auto sB_of = [&](int s) { return sA_of(s) + C::A_BYTES * (C::A_LO ? 2 : 1); };
 
   if (threadIdx.x == 0) {
@@ -438,12 +455,12 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
         }
         cp_commit();
       };
-      if (int(blockIdx.x) < p.num_tiles) prefetch_states(blockIdx.x, 0);
+      if (T0 < TE) prefetch_states(T0, 0);
       else cp_commit();
-      if (int(blockIdx.x + gridDim.x) < p.num_tiles) prefetch_states(blockIdx.x + gridDim.x, 1);
+      if (T0 + TS < TE) prefetch_states(T0 + TS, 1);
       else cp_commit();
       int c = 0;
-      for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++c) {
+      for (int t = T0; t < TE; t += TS, ++c) {
         const int g = c * KB;
         {
           // the MMA thread commits once per tile, to the tile's last stage: its
@@ -507,8 +524,8 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
         fence_proxy_async();
 #pragma unroll
         for (int kb = 0; kb < KB; ++kb) mbar_arrive(full_bar((g + kb) % S));
-        const int t2 = t + 2 * int(gridDim.x);
-        if (t2 < p.num_tiles) prefetch_states(t2, (c + 2) % 3);
+        const int t2 = t + 2 * TS;
+        if (t2 < TE) prefetch_states(t2, (c + 2) % 3);
         else cp_commit();
       }
       asm volatile("cp.async.wait_all;" ::: "memory");
@@ -517,7 +534,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       // counts one hardware arrival per producer thread at that moment
       int g = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+      for (int t = T0; t < TE && ok; t += TS) {
         const uint32_t m0 = uint32_t(t / NT) * 128u;
         const int n0 = (t % NT) * BN;
         // per-row source offsets for this tile (rows r0 + 32 i)
@@ -632,7 +649,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       int g = 0, it = 0;
       bool ok = true;
       if (C::B_RES) ok = wait_bar(wready_bar, 0, abort_flag, p.d_err, 6);
-      for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x, ++it) {
+      for (int t = T0; t < TE && ok; t += TS, ++it) {
         const int acc = it % NA;
         if (!wait_bar(tempty_bar(acc), (uint32_t((it / NA) & 1)) ^ 1u, abort_flag, p.d_err, 2)) break;
         tc_fence_after();
@@ -736,22 +753,36 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
     float4 zc[V == 2 ? 8 : 1];  // conv1 leaf: partial rows, fetched cooperatively (row i*4 + lane/8)
     auto zload = [&](int t) {
       if constexpr (V == 2) {
+        // a warp's 32 rows span at most two leaves (400 rows each): one division
+        // by the branching factor per tile gives both parents
         const uint32_t mw0 = uint32_t(t / NT) * 128u + uint32_t(q * 32);
+        const uint32_t mwc = mw0 < p.M ? mw0 : p.M - 1u;  // a warp past the end reads row M - 1
+        const uint32_t leafA = mwc / uint32_t(kP1), pxA = mwc - leafA * uint32_t(kP1);
+        const uint32_t gA = p.z_leaf0 + leafA, parA = gA / p.z_branch;
+        const uint32_t parB = parA + ((gA - parA * p.z_branch + 1u == p.z_branch) ? 1u : 0u);
+        const float *zA = p.zmap + size_t(parA) * (kP1 * kC1);
+        const float *zB = p.zmap + size_t(parB) * (kP1 * kC1);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          uint32_t mm = mw0 + uint32_t(i * 4 + (lane >> 3));
-          mm = mm < p.M ? mm : p.M - 1u;
-          const uint32_t leaf = mm / uint32_t(kP1), px = mm - leaf * uint32_t(kP1);
-          zc[i] = __ldg(reinterpret_cast<const float4 *>(
-                            p.zmap + (size_t((p.z_leaf0 + leaf) / p.z_branch) * kP1 + px) * kC1) +
-                        (lane & 7));
+          const uint32_t r = uint32_t(i * 4 + (lane >> 3));
+          uint32_t px = pxA + r;
+          const float *zrow = zA;
+          if (px >= uint32_t(kP1)) {
+            px -= uint32_t(kP1);
+            zrow = zB;
+          }
+          if (mw0 + r >= p.M) {  // ragged last tile: a valid row (its output is not stored)
+            px = pxA;
+            zrow = zA;
+          }
+          zc[i] = __ldg(reinterpret_cast<const float4 *>(zrow + size_t(px) * kC1) + (lane & 7));
         }
       }
     };
     constexpr int EW = C::EPI_WG;
-    if (V == 2 && int(blockIdx.x + eg * gridDim.x) < p.num_tiles) zload(blockIdx.x + eg * gridDim.x);
+    if (V == 2 && T0 + eg * TS < TE) zload(T0 + eg * TS);
     int it = eg;
-    for (int t = blockIdx.x + eg * int(gridDim.x); t < p.num_tiles; t += EW * int(gridDim.x), it += EW) {
+    for (int t = T0 + eg * TS; t < TE; t += EW * TS, it += EW) {
       const int acc = it % NA;
       if (!wait_bar(tfull_bar(acc), uint32_t((it / NA) & 1), abort_flag, p.d_err, 4)) break;
       tc_fence_after();
@@ -766,6 +797,9 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
         for (int i = 0; i < 8; ++i)
           *reinterpret_cast<float4 *>(stg + (i * 4 + (lane >> 3)) * kStgRow + (lane & 7) * 16) = zc[i];
         __syncwarp();
+        // the registers are free again: fetch the next tile's rows now, so their
+        // latency overlaps this whole tile
+        if (t + EW * TS < TE) zload(t + EW * TS);
       }
       // this thread's output row: hi part staged as it is produced, lo part kept
       // in registers until the hi rows are written
@@ -869,7 +903,6 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty_bar(acc));
-      if (V == 2 && t + EW * int(gridDim.x) < p.num_tiles) zload(t + EW * int(gridDim.x));
     }
   }
   // teardown: every role has left its loop (all waits are bounded)
