@@ -277,7 +277,10 @@ struct Cfg {
   static constexpr int JL = (FP8 && V == 1) ? 2 : 4;  // K steps of the last K block
   static constexpr int KPAD = KB_FULL * (128 / EB);  // stored weight row length in elements
   static constexpr bool A_LO = SPLIT && LAYER != 1;  // conv1's integer pixels are exact in bf16
-  static constexpr bool B_RES = LAYER == 1;          // conv1's weights (16 / 32 KB) stay in shared memory
+  // Weights resident in shared memory for the whole kernel: conv1 (8-32 KB) and,
+  // outside split mode, conv2/conv3 (32-72 KB), instead of one weight tile per
+  // K block of every output tile fetched again from L2.
+  static constexpr bool B_RES = LAYER == 1 || (!SPLIT && (LAYER == 2 || LAYER == 3));
   // Split mode stores the weight tile as [hi rows; lo rows] so that one MMA of
   // twice the width gives A_hi*B_hi and A_hi*B_lo side by side in TMEM (the
   // epilogue adds the halves); fc1's 256-wide tiles keep separate MMAs.
@@ -290,10 +293,10 @@ struct Cfg {
   static constexpr int STAGE_BYTES = A_BYTES * (A_LO ? 2 : 1) + (B_RES ? 0 : B_ROWS * 128);
   static constexpr int STAGES_RAW = (192 * 1024 - RES_BYTES) / STAGE_BYTES;
   // fused conv1 fills all KB stages of a tile together: a ring of RING tiles
-  static constexpr int RING = B_RES ? (8 / KB >= 2 ? 8 / KB : 2) : 1;
-  static constexpr int STAGES = B_RES ? RING * KB : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
+  static constexpr int RING = LAYER == 1 ? (8 / KB >= 2 ? 8 / KB : 2) : 1;
+  static constexpr int STAGES = LAYER == 1 ? RING * KB : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
   // fused conv1: re-zero lists (8 x 256 entries) + node-state ring (3 tiles x 2 nodes)
-  static constexpr int DIRTY_BYTES = B_RES ? 2 * 4 * 256 * 4 + 3 * 2 * 80 : 0;
+  static constexpr int DIRTY_BYTES = LAYER == 1 ? 2 * 4 * 256 * 4 + 3 * 2 * 80 : 0;
   // conv1 (32-column tiles, the lightest epilogue) runs two epilogue warpgroups
   // on alternating tiles so each has two tiles' time to hide its load latency
   static constexpr int EPI_WG = LAYER == 1 ? 2 : 1;
@@ -628,7 +631,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
           }
           // B tile (weights, [NTOT][K] K-major): hi rows, then lo rows
 #pragma unroll
-          for (int i = 0; i < BN / 32; ++i) {
+          for (int i = 0; i < (C::B_RES ? 0 : BN / 32); ++i) {
             const int r = r0 + 32 * i;
             const uint32_t off = sw128_off(r, ch);
             const long long eb = ((long long)(n0 + r) * C::KPAD) * EB + kb * 128 + ch * 16;  // bytes
@@ -658,7 +661,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
         // hardware arrival carries no proxy fence: one fence per F stages orders
         // them before the tensor core's async-proxy reads.  conv1's producers
         // write with st.shared and fence themselves.
-        constexpr bool kFence = !C::B_RES;
+        constexpr bool kFence = LAYER != 1;
         constexpr int F = (kFence && S >= 4) ? 2 : 1;
         constexpr bool kTileCommit = LAYER == 1 && FUSED;  // one commit frees the tile's stages
         for (int kb0 = 0; kb0 < KB && ok; kb0 += F) {
