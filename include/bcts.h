@@ -96,6 +96,12 @@ typedef struct bcts_options {
  * renders its operand tiles from the node states on the fly and the frames of
  * the searched nodes never reach device memory). */
 #define BCTS_FLAG_FRAMES 1
+/* BCTS_FLAG_EXACT_GEV: the penalty of Eq. 3 is the exact bias gap
+ * B_e(sigma_e, A, d) - B_o(sigma_o, A, d) of Lemma 2 (normal quantiles of
+ * 1 - 1/(A^d - A^(d-1)) and 1 - 1/A^(d-1) plus the Euler-Mascheroni GEV term,
+ * sigma = delta / sqrt(2) by Prop. 1) instead of its closed-form approximation
+ * Eq. 7.  Both are scaled by gamma^d and the correction multiplier c. */
+#define BCTS_FLAG_EXACT_GEV 2
 
 typedef struct bcts_ctx bcts_ctx;
 

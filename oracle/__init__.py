@@ -52,6 +52,13 @@ def _load():
         lib.or_search.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                   ctypes.c_double, P, P, P]
         lib.or_search.restype = ctypes.c_int
+        lib.or_search_ex.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, P, P, P]
+        lib.or_search_ex.restype = ctypes.c_int
+        lib.or_bellman_penalty_exact.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+        lib.or_bellman_penalty_exact.restype = ctypes.c_double
+        lib.or_normal_upper_quantile.argtypes = [ctypes.c_double]
+        lib.or_normal_upper_quantile.restype = ctypes.c_double
         lib.or_replay.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_double, P, P]
         lib.or_level.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                  ctypes.c_double, P, P]
@@ -104,8 +111,19 @@ def bellman_penalty(delta_e: float, delta_o: float, A: int, d: int) -> float:
     return float(_load().or_bellman_penalty(delta_e, delta_o, A, d))
 
 
-def search(roots, weights: np.ndarray, A: int, d: int, gamma: float, correction: float):
-    """Full BCTS search.  Returns dict(action [n], values [n][A], q0, v_uncorrected,
+def bellman_penalty_exact(delta_e: float, delta_o: float, A: int, d: int) -> float:
+    """Lemma 2's exact bias gap B_e - B_o at sigma = delta / sqrt(2)."""
+    return float(_load().or_bellman_penalty_exact(delta_e, delta_o, A, d))
+
+
+def normal_upper_quantile(q: float) -> float:
+    """x with 1 - Phi(x) = q (so Phi^-1(1 - q))."""
+    return float(_load().or_normal_upper_quantile(q))
+
+
+def search(roots, weights: np.ndarray, A: int, d: int, gamma: float, correction: float, exact_gev: bool = False):
+    """Full BCTS search (Eq. 7's penalty, or Lemma 2's exact bias gap when
+    exact_gev).  Returns dict(action [n], values [n][A], q0, v_uncorrected,
     delta, r0 [n][A], pi_o, delta_o, delta_e, B [n])."""
     lib = _load()
     r = _state_array(roots).reshape(-1)
@@ -115,8 +133,8 @@ def search(roots, weights: np.ndarray, A: int, d: int, gamma: float, correction:
     act = np.zeros(n, dtype=np.int32)
     val = np.zeros((n, A), dtype=np.float64)
     diag = np.zeros((n, 4 * A + 4), dtype=np.float64)
-    rc = lib.or_search(_ptr(r), n, _ptr(w), A, d, float(gamma), float(correction), _ptr(act), _ptr(val),
-                       _ptr(diag))
+    rc = lib.or_search_ex(_ptr(r), n, _ptr(w), A, d, float(gamma), float(correction), int(bool(exact_gev)),
+                          _ptr(act), _ptr(val), _ptr(diag))
     if rc != 0:
         raise ValueError("oracle search rejected its arguments")
     return {

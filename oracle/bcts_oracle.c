@@ -13,7 +13,8 @@
  *     (the max over the tail factorises level by level);
  *   - Prop. 1 / Sec. 3.3: the Bellman errors delta(a) = Q_1(s,a) - Q_0(s,a) from
  *     the root and the depth-1 nodes;
- *   - Eq. 7: the Bellman penalty B(delta_e, delta_o, A, d);
+ *   - Eq. 7: the Bellman penalty B(delta_e, delta_o, A, d), or (exact mode) the
+ *     bias gap B_e - B_o of Lemma 2 itself, with sigma = delta / sqrt(2);
  *   - Eq. 3 / Eq. 4: the corrected values and the BCTS action.
  * The environment is the synthetic sprite environment that stands in for the
  * paper's Atari games (Sec. 4 uses CuLE); the Q-network is Nature-DQN with
@@ -237,9 +238,54 @@ double or_bellman_penalty(double delta_e, double delta_o, int A, int d) {
 }
 
 /*
+ * Normal upper-tail quantile: the x with Q(x) = 1 - Phi(x) = q, 0 < q < 1, by
+ * bisection on Q(x) = erfc(x / sqrt 2) / 2 (monotone decreasing) until the
+ * bracket stops shrinking in double precision.  Phi^-1(1 - q) = this x.
+ */
+double or_normal_upper_quantile(double q) {
+    double lo = -40.0, hi = 40.0;
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (0.5 * erfc(mid / sqrt(2.0)) > q)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/*
+ * Lemma 2: the expected shift of the maximum of m iid standard normals as its
+ * GEV mean, Phi^-1(1 - 1/m) + gamma_EM * sigma_GEV with
+ * sigma_GEV = Phi^-1(1 - 1/(e m)) - Phi^-1(1 - 1/m) (the Lemma 1 parameters);
+ * 0 for a single element (m <= 1), as the lemma states for its d = 1 cases.
+ */
+static double or_gev_shift(double m) {
+    const double euler_gamma = 0.57721566490153286061;
+    if (m <= 1.0) return 0.0;
+    double x1 = or_normal_upper_quantile(1.0 / m);
+    double xe = or_normal_upper_quantile(1.0 / (exp(1.0) * m));
+    return x1 + euler_gamma * (xe - x1);
+}
+
+/*
+ * Exact bias gap of Eq. 3: B_e(sigma_e, A, d) - B_o(sigma_o, A, d) of Lemma 2,
+ * the maximum over A^d - A^(d-1) leaves (a_0 != pi_o) against A^(d-1) leaves
+ * (a_0 = pi_o), with the standard deviations estimated as delta / sqrt(2)
+ * (Prop. 1).
+ */
+double or_bellman_penalty_exact(double delta_e, double delta_o, int A, int d) {
+    double n_o = pow((double)A, (double)(d - 1));
+    double n_e = pow((double)A, (double)d) - n_o;
+    return delta_e / sqrt(2.0) * or_gev_shift(n_e) - delta_o / sqrt(2.0) * or_gev_shift(n_o);
+}
+
+/*
  * Full search from one root.
  *   values[A]  : corrected root values Q^BCTS_d(s0, a) (Eq. 3); for d = 0, Q_0(s0, a)
  *   *action    : lowest-index argmax of values (Eq. 4)
+ *   exact_gev: 0 = Eq. 7's penalty, 1 = Lemma 2's exact bias gap
  *   diag (may be NULL), 4*A + 4 doubles:
  *     [0,A)    Q_0(s0, a)                      root Q-values
  *     [A,2A)   V_d(s0, a)                      uncorrected Eq. 1 values
@@ -249,7 +295,7 @@ double or_bellman_penalty(double delta_e, double delta_o, int A, int d) {
  * Work is split over the A root actions (OpenMP) when `parallel` is set.
  */
 static void or_search_one(const or_state *root, const float *W, int A, int d, double gamma, double corr,
-                          int parallel, int *action, double *values, double *diag) {
+                          int exact_gev, int parallel, int *action, double *values, double *diag) {
     double q0[64], V[64], delta[64], r0[64];
     or_q_of_state(root, W, A, q0);
     int pi_o = or_argmax_lowest(q0, A);
@@ -283,7 +329,8 @@ static void or_search_one(const or_state *root, const float *W, int A, int d, do
             if (a != pi_o) delta_e += fabs(delta[a]);
         delta_e /= (double)(A - 1);
     }
-    double B = or_bellman_penalty(delta_e, delta_o, A, d);
+    double B = exact_gev ? or_bellman_penalty_exact(delta_e, delta_o, A, d)
+                         : or_bellman_penalty(delta_e, delta_o, A, d);
     double gd = pow(gamma, (double)d);
     for (int a = 0; a < A; ++a) values[a] = (a == pi_o) ? V[a] : V[a] - gd * corr * B;
     *action = or_argmax_lowest(values, A);
@@ -296,13 +343,18 @@ static void or_search_one(const or_state *root, const float *W, int A, int d, do
 }
 
 /* n roots; roots run one after another, each root's A subtrees in parallel. */
-int or_search(const or_state *roots, int n, const float *W, int A, int d, double gamma, double corr,
-              int *actions, double *values, double *diag) {
+int or_search_ex(const or_state *roots, int n, const float *W, int A, int d, double gamma, double corr,
+                 int exact_gev, int *actions, double *values, double *diag) {
     if (A < 1 || A > 64 || d < 0 || n < 0) return -1;
     for (int i = 0; i < n; ++i)
-        or_search_one(&roots[i], W, A, d, gamma, corr, 1, &actions[i], values + (size_t)i * A,
+        or_search_one(&roots[i], W, A, d, gamma, corr, exact_gev, 1, &actions[i], values + (size_t)i * A,
                       diag ? diag + (size_t)i * (4 * A + 4) : NULL);
     return 0;
+}
+
+int or_search(const or_state *roots, int n, const float *W, int A, int d, double gamma, double corr,
+              int *actions, double *values, double *diag) {
+    return or_search_ex(roots, n, W, A, d, gamma, corr, 0, actions, values, diag);
 }
 
 /* ---- tree enumeration in Alg. 1 order ------------------------------------ */

@@ -34,6 +34,7 @@ EXPORTED = ["bcts_qnet_numel", "bcts_create", "bcts_destroy", "bcts_last_error",
             "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait"]
 BCTS_STATIC_MAX_NODES = 128
 BCTS_FLAG_FRAMES = 1
+BCTS_FLAG_EXACT_GEV = 2
 KERNEL_CLASSES = ["expand", "render", "conv1", "conv2", "conv3", "fc1", "fc2", "backup", "conv1_partial",
                   "conv1_leaf"]
 

@@ -55,8 +55,9 @@ int tc_conv1_partial(const TcWeights *w, const bcts_state *states, int64_t n, fl
 int launch_segment_max(const float *R, const float *maxq, int64_t n_seg, int64_t seg_len, float gamma_pow,
                        float *V, cudaStream_t stream);
 // q0 rows are q_stride floats apart (root Q-values); r1, maxq1, V rows are A apart.
+// exact_gev: the penalty is Lemma 2's exact bias gap instead of Eq. 7.
 int launch_finalize(const float *q0, const float *maxq1, const float *r1, const float *V, int n, int A,
                     int depth, int A_stride, float gamma, float gamma_d, float corr, int32_t *action,
-                    float *values, cudaStream_t stream, int q_stride = 0);
+                    float *values, cudaStream_t stream, int q_stride = 0, int exact_gev = 0);
 
 }  // namespace bcts

@@ -205,7 +205,7 @@ static int mixed_enqueue(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_
     if ((rc = launch_segment_max(lR, lM, int64_t(g.n) * g.A, ipow(g.A, g.d - 1), float(gd), gV, st)) != BCTS_OK)
       return c->fail(rc, "backup launch failed");
     if ((rc = launch_finalize(gq0, maxq1 + g.l1_off, r1 + g.l1_off, gV, g.n, g.A, g.d, As, c->gamma, float(gd),
-                              c->corr, gact, gval, st, As)) != BCTS_OK)
+                              c->corr, gact, gval, st, As, c->exact_gev ? 1 : 0)) != BCTS_OK)
       return c->fail(rc, "finalize launch failed");
   }
   BCTS_CUDA_TRY(cudaMemcpyAsync(hs + in_b, act, size_t(pl.n) * 4, cudaMemcpyDeviceToHost, st), c->err);

@@ -54,10 +54,21 @@ __global__ void __launch_bounds__(128) segment_max_kernel(const float *__restric
 // One thread per root: pi_o = argmax Q_0 (Sec. 3.3), delta(a) from depths 0
 // and 1 (Prop. 1), delta_o = |delta(pi_o)|, delta_e = mean |delta(a)| over
 // a != pi_o, B by Eq. 7, corrected values (Eq. 3, scaled by c), action (Eq. 4).
+// Lemma 2: expected shift of the maximum of m iid standard normals, the mean of
+// its GEV limit, Phi^-1(1 - 1/m) + gamma_EM (Phi^-1(1 - 1/(e m)) - Phi^-1(1 - 1/m));
+// 0 for one element.  Upper quantiles via Phi^-1(1 - q) = -Phi^-1(q).
+__device__ double gev_shift(double m) {
+  if (m <= 1.0) return 0.0;
+  const double x1 = -normcdfinv(1.0 / m);
+  const double xe = -normcdfinv(1.0 / (2.718281828459045 * m));
+  return x1 + 0.5772156649015329 * (xe - x1);
+}
+
 __global__ void finalize_kernel(const float *__restrict__ q0, const float *__restrict__ maxq1,
                                 const float *__restrict__ r1, const float *__restrict__ V, int n, int A,
                                 int depth, int A_stride, float gamma, float gamma_d, float corr,
-                                int32_t *__restrict__ action, float *__restrict__ values, int q_stride) {
+                                int32_t *__restrict__ action, float *__restrict__ values, int q_stride,
+                                int exact_gev) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float *q = q0 + size_t(i) * q_stride;
@@ -80,8 +91,16 @@ __global__ void finalize_kernel(const float *__restrict__ q0, const float *__res
       d_e += fabsf(delta);
   }
   if (A > 1) d_e /= float(A - 1);
-  const float B = sqrtf(logf(float(A))) * (d_e * sqrtf(float(depth)) - d_o * sqrtf(float(depth - 1))) -
-                  (d_e - d_o) * 0.35355339059327373f;  // 1 / sqrt(8)
+  float B;
+  if (exact_gev) {
+    // Eq. 3's gap B_e - B_o itself (Lemma 2): A^d - A^(d-1) leaves under a != pi_o
+    // against A^(d-1) under pi_o, sigma = delta / sqrt(2) (Prop. 1)
+    const double n_o = pow(double(A), double(depth - 1)), n_e = pow(double(A), double(depth)) - n_o;
+    B = float(0.7071067811865476 * (double(d_e) * gev_shift(n_e) - double(d_o) * gev_shift(n_o)));
+  } else {
+    B = sqrtf(logf(float(A))) * (d_e * sqrtf(float(depth)) - d_o * sqrtf(float(depth - 1))) -
+        (d_e - d_o) * 0.35355339059327373f;  // Eq. 7; 1 / sqrt(8)
+  }
   const float pen = gamma_d * corr * B;
   int best = 0;
   float bestv = -INFINITY;
@@ -109,12 +128,12 @@ int launch_segment_max(const float *R, const float *maxq, int64_t n_seg, int64_t
 
 int launch_finalize(const float *q0, const float *maxq1, const float *r1, const float *V, int n, int A, int depth,
                     int A_stride, float gamma, float gamma_d, float corr, int32_t *action, float *values,
-                    cudaStream_t st, int q_stride) {
+                    cudaStream_t st, int q_stride, int exact_gev) {
   if (n <= 0) return BCTS_OK;
   ProfScope ps(K_BACKUP, st);
   finalize_kernel<<<unsigned((n + 127) / 128), 128, 0, st>>>(q0, maxq1, r1, V, n, A, depth, A_stride, gamma,
                                                               gamma_d, corr, action, values,
-                                                              q_stride > 0 ? q_stride : A);
+                                                              q_stride > 0 ? q_stride : A, exact_gev);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 
@@ -330,7 +349,7 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
       break;
     }
     if ((rc = launch_finalize(q0, maxq1, r1, V, n, A_, d_, A_stride, gamma, float(gd), corr, d_action, d_values,
-                              st)) != BCTS_OK) {
+                              st, 0, exact_gev ? 1 : 0)) != BCTS_OK) {
       rc = fail(rc, "finalize launch failed");
       break;
     }
@@ -456,6 +475,7 @@ extern "C" int bcts_create(const bcts_env_desc *env, const float *w, int A, int 
   if (opt) c->opt = *opt;
   c->precision = c->opt.precision;
   c->tc_fused_render = (c->opt.flags & BCTS_FLAG_FRAMES) == 0;
+  c->exact_gev = (c->opt.flags & BCTS_FLAG_EXACT_GEV) != 0;
   if (c->precision < BCTS_PREC_FP32 || c->precision > BCTS_PREC_FP32_SIMT) {
     delete c;
     set_thread_error("bcts_create: unknown precision");

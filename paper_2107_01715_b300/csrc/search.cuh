@@ -35,6 +35,7 @@ struct Ctx {
   SimtWeights simt{};
   TcWeights *tc = nullptr;
   bool tc_fused_render = false;
+  bool exact_gev = false;  // Lemma 2's exact bias gap instead of Eq. 7
   bool owns_weights = true;  // serving workers share their owner's weights
   int *d_err = nullptr;
 

@@ -76,6 +76,7 @@ Ctx *clone_ctx(const Ctx *o) {
   c->simt = o->simt;
   c->tc = o->tc;
   c->tc_fused_render = o->tc_fused_render;
+  c->exact_gev = o->exact_gev;
   c->owns_weights = false;
   c->prof = profiler_create();
   if (cudaSetDevice(o->device) != cudaSuccess || cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||

@@ -157,3 +157,52 @@ def test_fused_render_equals_materialised_frames(oracle_lib, dev, precision, d):
     else:
         assert value_close(out[0][1], out[1][1], TOL[precision] / 10).all()
         check_actions(out[0][0], out[1][1].astype(np.float64), TOL[precision] / 10)
+
+
+@pytest.mark.parametrize("precision", [p for p in PRECISIONS if p in ("fp32", "fp32_simt")])
+@pytest.mark.parametrize("A,d,n,c", [(6, 2, 3, 1.0), (4, 3, 2, 2.0), (2, 1, 4, 1.0), (9, 1, 3, 1.0),
+                                     (18, 2, 2, 1.0), (1, 2, 1, 1.0)])
+def test_exact_gev_search_matches_oracle(oracle_lib, dev, precision, A, d, n, c):
+    """BCTS_FLAG_EXACT_GEV: Lemma 2's exact bias gap in place of Eq. 7, against the
+    oracle's exact mode (its own normal quantile, pinned to the library's)."""
+    torch, bcts = dev
+    gamma = 0.99
+    ctx, W = _ctx(bcts, A, d, gamma, c, precision, flags=bcts.BCTS_FLAG_EXACT_GEV)
+    roots = inputs.root_states(range(200, 200 + n))
+    act, val = bcts.bcts_search(ctx, roots)
+    ref = oracle_lib.search(roots, W, A, d, float(np.float32(gamma)), c, exact_gev=True)
+    tol = TOL[precision]
+    ok = value_close(val, ref["values"], tol)
+    assert ok.all(), (np.abs(val - ref["values"]).max(), val, ref["values"])
+    check_actions(act, ref["values"], tol)
+    # the flag changes the answer wherever the two penalties differ
+    if d >= 1 and A >= 3 and c > 0:
+        eq7 = oracle_lib.search(roots, W, A, d, float(np.float32(gamma)), c)
+        assert not np.allclose(eq7["values"], ref["values"], rtol=0, atol=1e-6)
+    ctx.close()
+
+
+def test_exact_gev_batched_and_served(oracle_lib, dev):
+    """The flag reaches the batched form (mixed depths and action counts) and the
+    serving workers."""
+    torch, bcts = dev
+    A = 9
+    W = inputs.qnet_weights(A, seed=1234)
+    ctx = bcts.bcts_create(W, A, 3, 0.99, 1.0, precision="fp32", flags=bcts.BCTS_FLAG_EXACT_GEV)
+    roots = inputs.root_states(range(300, 306))
+    depths = np.array([1, 2, 3, 2, 0, 3], dtype=np.int32)
+    actions = np.array([9, 4, 9, 9, 9, 3], dtype=np.int32)
+    act, val = bcts.bcts_search_mixed(ctx, roots, depths, actions)
+    for i in range(len(roots)):
+        Ai = int(actions[i])
+        Wi = np.concatenate([W[:-(A * 512 + A)], W[-(A * 512 + A):-(A * 512 + A) + Ai * 512],
+                             W[-A:][:Ai]]).astype(np.float32)
+        ref = oracle_lib.search(roots[i:i + 1], Wi, Ai, int(depths[i]), float(np.float32(0.99)), 1.0,
+                                exact_gev=True)
+        assert value_close(val[i, :Ai], ref["values"][0], TOL["fp32"]).all(), (i, val[i, :Ai], ref["values"][0])
+        check_actions(act[i:i + 1], ref["values"], TOL["fp32"])
+        t = bcts.bcts_submit(ctx, roots[i:i + 1], int(depths[i]), Ai)
+        rc, a_s, v_s = bcts.bcts_poll(ctx, t, A, timeout_us=-1)
+        assert rc == bcts.BCTS_OK and a_s == act[i]
+        np.testing.assert_array_equal(v_s[:Ai], val[i, :Ai])
+    ctx.close()

@@ -74,3 +74,33 @@ def test_bias_ordering_lemma2():
                 assert b_o == b_e == 0.0
             else:
                 assert 0.0 <= b_o < b_e
+
+
+# ---- Lemma 2's exact bias gap (the exact-GEV correction) ------------------------
+
+@pytest.mark.parametrize("q", [0.5, 0.3, 0.9, 1e-3, 1 / 18, 1 / 324, 1 / (math.e * 18 ** 5), 1e-9])
+def test_normal_upper_quantile_matches_library(oracle_lib, q):
+    # Phi^-1(1 - q) = -Phi^-1(q): the lower-tail library quantile keeps full precision
+    assert oracle_lib.normal_upper_quantile(q) == pytest.approx(-_ppf(q), abs=1e-12)
+
+
+@pytest.mark.parametrize("de,do,A,d", CASES)
+def test_exact_penalty_equals_lemma2(oracle_lib, de, do, A, d):
+    s2 = math.sqrt(2.0)
+    assert oracle_lib.bellman_penalty_exact(de, do, A, d) == pytest.approx(
+        lemma2_gap(de / s2, do / s2, A, d), rel=1e-9, abs=1e-12)
+
+
+def test_exact_penalty_special_cases(oracle_lib):
+    # d = 1, A = 2: both sub-trees hold one leaf, no maximisation bias at all
+    assert oracle_lib.bellman_penalty_exact(3.0, 0.5, 2, 1) == 0.0
+    # d = 1: B_o = 0 (one leaf under pi_o); B_e is the shift of a max of A - 1 normals
+    assert oracle_lib.bellman_penalty_exact(2.0, 7.0, 18, 1) == pytest.approx(
+        2.0 / math.sqrt(2.0) * bias_n(17), rel=1e-12)
+    # A = 1: no other action, nothing to correct
+    assert oracle_lib.bellman_penalty_exact(1.0, 1.0, 1, 3) == 0.0
+    # linear in (delta_e, delta_o) and antisymmetric under swapping the leaf counts' roles
+    a = oracle_lib.bellman_penalty_exact(1.0, 0.0, 6, 3)
+    b = oracle_lib.bellman_penalty_exact(0.0, 1.0, 6, 3)
+    assert oracle_lib.bellman_penalty_exact(2.5, 0.75, 6, 3) == pytest.approx(2.5 * a + 0.75 * b, rel=1e-12)
+    assert a > 0.0 > b

@@ -159,3 +159,36 @@ def test_closed_form_corrected(oracle_lib):
     assert res["pi_o"][0] == pi_o
     np.testing.assert_allclose(res["values"][0], expect, rtol=1e-13)
     assert res["action"][0] == (pi_o if B > 0 else 0)
+
+
+@pytest.mark.parametrize("A,d", [(4, 3), (6, 2), (3, 1)])
+def test_exact_gev_correction(oracle_lib, A, d):
+    """Exact-GEV mode: the same uncorrected values, Bellman errors and pi_o, and the
+    off-policy actions lowered by gamma^d c (B_e - B_o) with Lemma 2's biases at
+    sigma = delta / sqrt(2), computed here from the normal quantile of Python's
+    standard library."""
+    from statistics import NormalDist
+    ppf = NormalDist().inv_cdf
+    em = 0.5772156649015329
+
+    def shift(m):
+        if m <= 1:
+            return 0.0
+        x1, xe = -ppf(1 / m), -ppf(1 / (math.e * m))
+        return x1 + em * (xe - x1)
+
+    W = inputs.qnet_weights(A, seed=5)
+    roots = inputs.root_states(range(40, 43))
+    gamma, c = 0.97, 1.5
+    eq7 = oracle_lib.search(roots, W, A, d, gamma, c)
+    ex = oracle_lib.search(roots, W, A, d, gamma, c, exact_gev=True)
+    np.testing.assert_array_equal(ex["v_uncorrected"], eq7["v_uncorrected"])
+    np.testing.assert_array_equal(ex["pi_o"], eq7["pi_o"])
+    for i in range(len(roots)):
+        de, do = ex["delta_e"][i], ex["delta_o"][i]
+        gap = (de * shift(A ** d - A ** (d - 1)) - do * shift(A ** (d - 1))) / math.sqrt(2.0)
+        assert ex["B"][i] == pytest.approx(gap, rel=1e-9, abs=1e-12)
+        for a in range(A):
+            want = ex["v_uncorrected"][i, a] - (0.0 if a == ex["pi_o"][i] else gamma ** d * c * gap)
+            assert ex["values"][i, a] == pytest.approx(want, rel=1e-12, abs=1e-12)
+        assert ex["action"][i] == int(np.argmax(ex["values"][i]))
