@@ -150,6 +150,29 @@ BCTS_API const char *bcts_last_error(const bcts_ctx *ctx);
  */
 BCTS_API int bcts_search(bcts_ctx *ctx, const bcts_state *roots, int n, int32_t *out_action, float *out_root_values);
 
+/*
+ * Per-node export (Sec. 4: since Batch-BFS advances the whole tree at once it
+ * exposes the cumulative reward and the estimated value of every tree node; the
+ * appendix's ablation trains DQN on values propagated from the tree nodes).
+ * The same search as bcts_search_device (device pointers, asynchronous on
+ * `stream`, the context's A and d), and for every node x at depth i = 1..d of
+ * every root, stored level by level (level i: n * A^i floats in Alg. 1's order,
+ * child of node k = k * A + a, after the n * (A + ... + A^(i-1)) floats of the
+ * levels above):
+ *   d_node_R[x] = sum over t < i of gamma^t r_t on the path from the root (Alg. 1's R)
+ *   d_node_V[x] = max over the d - i remaining actions of
+ *                 sum_t gamma^t r_t + gamma^(d-i) max_a Q(leaf, a),
+ *                 the (d - i)-step value of x's state (at i = d: max_a Q(x, a)),
+ * so R + gamma^i V is the best root-discounted return through x and the
+ * uncorrected root value of action a is R + gamma V of depth-1 node a.  Each
+ * array holds bcts_tree_nodes(n, A, d) floats (caller-owned device memory;
+ * d = 0: none, the pointers may be NULL).  bcts_tree_nodes returns -1 for
+ * invalid arguments or more than 2^40 nodes per level.
+ */
+BCTS_API int64_t bcts_tree_nodes(int n, int A, int d);
+BCTS_API int bcts_search_tree(bcts_ctx *ctx, const bcts_state *d_roots, int n, int32_t *d_out_action,
+                              float *d_out_root_values, float *d_node_R, float *d_node_V, void *stream);
+
 /* Same as bcts_search with device pointers, asynchronous on `stream`.  The
  * context's buffers are reused by the next search on the same context, so
  * searches on one context must not overlap (the library orders them on the

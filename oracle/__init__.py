@@ -59,6 +59,8 @@ def _load():
         lib.or_bellman_penalty_exact.restype = ctypes.c_double
         lib.or_normal_upper_quantile.argtypes = [ctypes.c_double]
         lib.or_normal_upper_quantile.restype = ctypes.c_double
+        lib.or_tree_node.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_longlong, P, P]
         lib.or_replay.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_double, P, P]
         lib.or_level.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                  ctypes.c_double, P, P]
@@ -143,6 +145,18 @@ def search(roots, weights: np.ndarray, A: int, d: int, gamma: float, correction:
         "r0": diag[:, 3 * A:4 * A], "pi_o": diag[:, 4 * A].astype(np.int64),
         "delta_o": diag[:, 4 * A + 1], "delta_e": diag[:, 4 * A + 2], "B": diag[:, 4 * A + 3],
     }
+
+
+def tree_node(root, weights: np.ndarray, A: int, d: int, gamma: float, level: int, idx: int):
+    """(R, V) of node idx at depth `level`: accumulated discounted reward from the
+    root and the node's (d - level)-step value."""
+    lib = _load()
+    r = _state_array(root).reshape(1)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    R = np.zeros(1, dtype=np.float64)
+    V = np.zeros(1, dtype=np.float64)
+    lib.or_tree_node(_ptr(r), _ptr(w), A, d, float(gamma), int(level), int(idx), _ptr(R), _ptr(V))
+    return float(R[0]), float(V[0])
 
 
 def replay(root, A: int, depth: int, idx: int, gamma: float):

@@ -362,6 +362,24 @@ int or_search(const or_state *roots, int n, const float *W, int A, int d, double
  * base-A digits of idx, most significant first (child = parent * A + a).
  * Returns the state and R = sum_t gamma^t r_t (Alg. 1's accumulated reward). */
 void or_replay(const or_state *root, int A, int depth, long long idx, double gamma, or_state *out,
+               double *R);
+
+/*
+ * One node of the tree export (Sec. 4: Batch-BFS exposes every node's cumulative
+ * reward and estimated value): node idx of depth `level` (Alg. 1 order) of the
+ * search from `root` to depth d.  *R = the discounted reward accumulated from the
+ * root (Alg. 1's R); *V = the node's (d - level)-step value, max over the
+ * remaining actions of the discounted return plus gamma^(d-level) max_a Q at the
+ * leaf (the same recursion as Eq. 1's tail).
+ */
+void or_tree_node(const or_state *root, const float *W, int A, int d, double gamma, int level, long long idx,
+                  double *R, double *V) {
+    or_state s;
+    or_replay(root, A, level, idx, gamma, &s, R);
+    *V = or_node_value(&s, level, d, W, A, gamma);
+}
+
+void or_replay(const or_state *root, int A, int depth, long long idx, double gamma, or_state *out,
                double *R) {
     int acts[32];
     long long x = idx;

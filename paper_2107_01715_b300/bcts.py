@@ -31,7 +31,8 @@ PRECISIONS = {"fp32": BCTS_PREC_FP32, "bf16": BCTS_PREC_BF16, "fp8": BCTS_PREC_F
 
 EXPORTED = ["bcts_qnet_numel", "bcts_create", "bcts_destroy", "bcts_last_error", "bcts_search",
             "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll", "bcts_expand",
-            "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait"]
+            "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait", "bcts_tree_nodes",
+            "bcts_search_tree"]
 BCTS_STATIC_MAX_NODES = 128
 BCTS_FLAG_FRAMES = 1
 BCTS_FLAG_EXACT_GEV = 2
@@ -71,8 +72,11 @@ lib.bcts_profile.argtypes = [_P, _I, _P, _P, _P]
 lib.bcts_qnet_static.argtypes = [_P, _I, _P, _I64, _P, _P]
 lib.bcts_env_step.argtypes = [_P, _I, _P, ctypes.POINTER(_I)]
 lib.bcts_selftest_wait.argtypes = [_I]
+lib.bcts_tree_nodes.argtypes = [_I, _I, _I]
+lib.bcts_tree_nodes.restype = ctypes.c_int64
+lib.bcts_search_tree.argtypes = [_P, _P, _I, _P, _P, _P, _P, _P]
 for _f in ("bcts_search", "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll",
-           "bcts_expand", "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait"):
+           "bcts_expand", "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait", "bcts_search_tree"):
     getattr(lib, _f).restype = _I
 
 
@@ -253,3 +257,15 @@ def bcts_env_step(state, a: int):
 def bcts_selftest_wait(timeout_us: int) -> int:
     """Run the bounded-wait self-test; returns the raw status (BCTS_ETIMEOUT expected)."""
     return int(lib.bcts_selftest_wait(int(timeout_us)))
+
+
+def bcts_tree_nodes(n: int, A: int, d: int) -> int:
+    """Floats per array of the per-node export: n * (A + A^2 + ... + A^d)."""
+    return int(lib.bcts_tree_nodes(int(n), int(A), int(d)))
+
+
+def bcts_search_tree(ctx: Context, d_roots, n: int, d_action, d_values, d_node_R, d_node_V, stream=None) -> int:
+    """Search plus the per-node export (accumulated reward R and propagated value V
+    of every node at depths 1..d, level-major, Alg. 1 order); device pointers."""
+    return _check(lib.bcts_search_tree(ctx.handle, _addr(d_roots), n, _addr(d_action), _addr(d_values),
+                                       _addr(d_node_R), _addr(d_node_V), _stream(stream)), ctx)

@@ -126,6 +126,28 @@ int launch_segment_max(const float *R, const float *maxq, int64_t n_seg, int64_t
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 
+// Per-node export.  U = R + gamma^i V is the best root-discounted return through a
+// node: at the leaves R + gamma^d max_a Q, above them the max over the A children
+// (Alg. 1 order: children of x are x*A .. x*A + A - 1), so the upward pass is a
+// pure max.  V = (U - R) / gamma^i is formed level by level afterwards.
+__global__ void tree_leaf_kernel(const float *__restrict__ R, const float *__restrict__ maxq, float gamma_d,
+                                 float *__restrict__ U, int64_t n) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) U[i] = R[i] + gamma_d * maxq[i];
+}
+__global__ void tree_up_kernel(const float *__restrict__ Uc, int A, float *__restrict__ U, int64_t n) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  float m = Uc[i * A];
+  for (int a = 1; a < A; ++a) m = fmaxf(m, Uc[i * A + a]);
+  U[i] = m;
+}
+__global__ void tree_value_kernel(const float *__restrict__ R, float inv_gamma_i, float *__restrict__ UV,
+                                  int64_t n) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) UV[i] = (UV[i] - R[i]) * inv_gamma_i;
+}
+
 int launch_finalize(const float *q0, const float *maxq1, const float *r1, const float *V, int n, int A, int depth,
                     int A_stride, float gamma, float gamma_d, float corr, int32_t *action, float *values,
                     cudaStream_t st, int q_stride, int exact_gev) {
@@ -247,6 +269,30 @@ int Ctx::qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt
   return BCTS_OK;
 }
 
+// Per-node export after the backup: U = R + gamma^d max Q at the leaves, a max over
+// the children upwards, then V = (U - R) / gamma^i per level; the leaves' V is
+// their max Q itself.
+int Ctx::export_tree(const std::vector<int64_t> &N, int A_, int d_, const float *leafMax, cudaStream_t st) {
+  if (d_ < 1) return BCTS_OK;
+  ProfScope ps(K_BACKUP, st);
+  std::vector<int64_t> off(d_ + 1, 0);  // first node of level i (off[1] = 0)
+  for (int i = 2; i <= d_; ++i) off[i] = off[i - 1] + N[i - 1];
+  std::vector<double> gpow(d_ + 1, 1.0);
+  for (int i = 1; i <= d_; ++i) gpow[i] = gpow[i - 1] * double(gamma);
+  auto blocks = [](int64_t n) { return unsigned((n + 255) / 256); };
+  tree_leaf_kernel<<<blocks(N[d_]), 256, 0, st>>>(tree_R + off[d_], leafMax, float(gpow[d_]), tree_V + off[d_],
+                                                  N[d_]);
+  for (int i = d_ - 1; i >= 1; --i)
+    tree_up_kernel<<<blocks(N[i]), 256, 0, st>>>(tree_V + off[i + 1], A_, tree_V + off[i], N[i]);
+  for (int i = 1; i < d_; ++i)
+    tree_value_kernel<<<blocks(N[i]), 256, 0, st>>>(tree_R + off[i], float(1.0 / gpow[i]), tree_V + off[i], N[i]);
+  if (cudaGetLastError() != cudaSuccess) return fail(BCTS_ECUDA, "tree export launch failed");
+  BCTS_CUDA_TRY(cudaMemcpyAsync(tree_V + off[d_], leafMax, size_t(N[d_]) * sizeof(float), cudaMemcpyDeviceToDevice,
+                                st),
+                err);
+  return BCTS_OK;
+}
+
 // Alg. 1 for n roots sharing (A_, d_): level-synchronous expansion, root and
 // depth-1 evaluation for the Bellman errors, leaf scoring, backup.
 int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d_action, float *d_values,
@@ -289,6 +335,8 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
       rc = fail(rc, "expand launch failed");
       break;
     }
+    if (tree_R)
+      BCTS_CUDA_TRY(cudaMemcpyAsync(tree_R, r1, size_t(N[1]) * sizeof(float), cudaMemcpyDeviceToDevice, st), err);
     // a3: depth-1 evaluation (for d = 1 these are the leaves)
     if ((rc = eval_nodes(L1, N[1], nullptr, maxq1, st)) != BCTS_OK) break;
     const float *leafR = r1;
@@ -305,6 +353,15 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
         if ((rc = launch_expand(cur, curR, N[i], A_, float(gp), nxt, nxtR, nullptr, st)) != BCTS_OK) {
           rc = fail(rc, "expand launch failed");
           break;
+        }
+        if (tree_R) {
+          int64_t off = 0;  // first node of level i + 1 in the export
+          for (int j = 1; j <= i; ++j) off += N[j];
+          if (cudaMemcpyAsync(tree_R + off, nxtR, size_t(N[i + 1]) * sizeof(float), cudaMemcpyDeviceToDevice,
+                              st) != cudaSuccess) {
+            rc = fail(BCTS_ECUDA, "tree export copy failed");
+            break;
+          }
         }
         cur = nxt;
         curR = nxtR;
@@ -353,6 +410,7 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
       rc = fail(rc, "finalize launch failed");
       break;
     }
+    if (tree_R && tree_V && (rc = export_tree(N, A_, d_, leafMax, st)) != BCTS_OK) break;
   } while (0);
   A = saved_A;
   return rc;
@@ -584,6 +642,31 @@ extern "C" int bcts_search_device(bcts_ctx *ctx, const bcts_state *d_roots, int 
     return c->fail(BCTS_EINVAL, "bcts_search_device: invalid argument");
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
   return c->run_search(d_roots, n, c->A_create, c->d, d_action, d_values, c->A_create, st);
+}
+
+extern "C" int64_t bcts_tree_nodes(int n, int A, int d) {
+  if (n < 0 || A < 1 || d < 0) return -1;
+  int64_t total = 0, level = n;
+  for (int i = 1; i <= d; ++i) {
+    if (level > (int64_t(1) << 40) / A) return -1;
+    level *= A;
+    total += level;
+  }
+  return total;
+}
+
+extern "C" int bcts_search_tree(bcts_ctx *ctx, const bcts_state *d_roots, int n, int32_t *d_action,
+                                float *d_values, float *d_node_R, float *d_node_V, void *stream) {
+  if (!ctx) return BCTS_EINVAL;
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  if (n < 0 || (n > 0 && (!d_roots || !d_action || !d_values || (c->d >= 1 && (!d_node_R || !d_node_V)))))
+    return c->fail(BCTS_EINVAL, "bcts_search_tree: invalid argument");
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  c->tree_R = d_node_R;
+  c->tree_V = d_node_V;
+  const int rc = c->run_search(d_roots, n, c->A_create, c->d, d_action, d_values, c->A_create, st);
+  c->tree_R = c->tree_V = nullptr;
+  return rc;
 }
 
 extern "C" int bcts_search(bcts_ctx *ctx, const bcts_state *roots, int n, int32_t *out_action, float *out_values) {

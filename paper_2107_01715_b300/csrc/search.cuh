@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -36,6 +37,8 @@ struct Ctx {
   TcWeights *tc = nullptr;
   bool tc_fused_render = false;
   bool exact_gev = false;  // Lemma 2's exact bias gap instead of Eq. 7
+  // per-node export of the current search (bcts_search_tree), level-major; null otherwise
+  float *tree_R = nullptr, *tree_V = nullptr;
   bool owns_weights = true;  // serving workers share their owner's weights
   int *d_err = nullptr;
 
@@ -59,6 +62,7 @@ struct Ctx {
                  const uint8_t *node_A = nullptr, const float *zmap = nullptr, uint32_t zbranch = 0);
   int qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
                  cudaStream_t st, const uint8_t *node_A = nullptr, const ZLeaf *zl = nullptr);
+  int export_tree(const std::vector<int64_t> &N, int A_, int d_, const float *leafMax, cudaStream_t st);
   int run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d_action, float *d_values,
                  int A_stride, cudaStream_t st);
   int run_mixed(const bcts_state *d_roots, const bcts_state *h_roots, const int32_t *depths,

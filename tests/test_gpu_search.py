@@ -206,3 +206,49 @@ def test_exact_gev_batched_and_served(oracle_lib, dev):
         assert rc == bcts.BCTS_OK and a_s == act[i]
         np.testing.assert_array_equal(v_s[:Ai], val[i, :Ai])
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [p for p in PRECISIONS if p in ("fp32", "fp32_simt")])
+@pytest.mark.parametrize("A,d,n,sample", [(4, 3, 2, None), (6, 1, 3, None), (18, 3, 2, 60), (9, 2, 2, None)])
+def test_tree_export_matches_oracle(oracle_lib, dev, precision, A, d, n, sample):
+    """bcts_search_tree: every node's R and V (or a seeded sample per level) against
+    the oracle's replay and recursive value; the search's own outputs unchanged."""
+    torch, bcts = dev
+    gamma = 0.99
+    ctx, W = _ctx(bcts, A, d, gamma, 1.0, precision)
+    roots = inputs.root_states(range(500, 500 + n))
+    total = bcts.bcts_tree_nodes(n, A, d)
+    assert total == sum(n * A ** i for i in range(1, d + 1))
+    d_roots = torch.from_numpy(roots.view(np.uint8).copy()).cuda()
+    d_act = torch.empty(n, dtype=torch.int32, device="cuda")
+    d_val = torch.empty(n * A, dtype=torch.float32, device="cuda")
+    d_R = torch.full((total,), float("nan"), dtype=torch.float32, device="cuda")
+    d_V = torch.full((total,), float("nan"), dtype=torch.float32, device="cuda")
+    bcts.bcts_search_tree(ctx, d_roots, n, d_act, d_val, d_R, d_V)
+    torch.cuda.synchronize()
+    R, V = d_R.cpu().numpy(), d_V.cpu().numpy()
+    assert np.isfinite(R).all() and np.isfinite(V).all()
+    act, val = bcts.bcts_search(ctx, roots)
+    np.testing.assert_array_equal(d_act.cpu().numpy(), act)
+    np.testing.assert_array_equal(d_val.cpu().numpy().reshape(n, A), val)
+    g32 = float(np.float32(gamma))
+    rng = np.random.default_rng(7)
+    off = 0
+    tol = TOL[precision]
+    for level in range(1, d + 1):
+        cnt = n * A ** level
+        # the oracle's value of a depth-i node costs A^(d-i) Q-network evaluations:
+        # fewer samples where the subtrees are large
+        k_lvl = None if sample is None else max(2, sample // A ** (d - level))
+        idx = np.arange(cnt) if k_lvl is None else rng.choice(cnt, size=min(k_lvl, cnt), replace=False)
+        for k in idx:
+            root, j = divmod(int(k), A ** level)
+            r_ref, v_ref = oracle_lib.tree_node(roots[root], W, A, d, g32, level, j)
+            assert abs(R[off + k] - r_ref) <= 1e-6 * max(abs(r_ref), 1.0), (level, k, R[off + k], r_ref)
+            assert abs(V[off + k] - v_ref) <= tol * max(abs(v_ref), 1.0), (level, k, V[off + k], v_ref)
+        off += cnt
+    # depth-1 nodes: R + gamma V are the uncorrected root values
+    ref = oracle_lib.search(roots, W, A, d, g32, 1.0)
+    v1 = R[:n * A] + g32 * V[:n * A]
+    assert value_close(v1.reshape(n, A), ref["v_uncorrected"], tol).all()
+    ctx.close()

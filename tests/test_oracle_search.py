@@ -192,3 +192,32 @@ def test_exact_gev_correction(oracle_lib, A, d):
             want = ex["v_uncorrected"][i, a] - (0.0 if a == ex["pi_o"][i] else gamma ** d * c * gap)
             assert ex["values"][i, a] == pytest.approx(want, rel=1e-12, abs=1e-12)
         assert ex["action"][i] == int(np.argmax(ex["values"][i]))
+
+
+def test_tree_node_export_brute_force(oracle_lib):
+    """The per-node export: R is the replayed accumulated discounted reward, V the
+    node's (d - level)-step value, checked by enumerating every remaining action
+    sequence with the flat sum of Eq. 1's tail."""
+    A, d, gamma = 3, 3, 0.9
+    W = inputs.qnet_weights(A, seed=11)
+    root = inputs.root_states([77])[0]
+    for level in range(1, d + 1):
+        for idx in range(A ** level):
+            R, V = oracle_lib.tree_node(root, W, A, d, gamma, level, idx)
+            s, Rr = oracle_lib.replay(root, A, level, idx, gamma)
+            assert R == Rr
+            best = -math.inf
+            for acts in itertools.product(range(A), repeat=d - level):
+                x, ret, g = s, 0.0, 1.0
+                for a in acts:
+                    x, r = oracle_lib.env_step(x, a)
+                    ret += g * r
+                    g *= gamma
+                q = oracle_lib.qnet(oracle_lib.render(x)[None], W, A)[0]
+                best = max(best, ret + g * q.max())
+            assert V == pytest.approx(best, rel=1e-12, abs=1e-12)
+    # the depth-1 nodes carry the uncorrected root values: R + gamma V
+    ref = oracle_lib.search(root, W, A, d, gamma, 0.0)
+    for a in range(A):
+        R, V = oracle_lib.tree_node(root, W, A, d, gamma, 1, a)
+        assert R + gamma * V == pytest.approx(ref["v_uncorrected"][0, a], rel=1e-12)
