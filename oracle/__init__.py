@@ -61,6 +61,14 @@ def _load():
         lib.or_normal_upper_quantile.restype = ctypes.c_double
         lib.or_tree_node.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                      ctypes.c_longlong, P, P]
+        lib.or_dnn_numel.argtypes = [ctypes.c_int]
+        lib.or_dnn_numel.restype = ctypes.c_size_t
+        lib.or_dnn_step.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P]
+        lib.or_dnn_step.restype = ctypes.c_double
+        lib.or_dnn_q.argtypes = [P, P, ctypes.c_int, P]
+        lib.or_dnn_search.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, P, P, P]
+        lib.or_dnn_search.restype = ctypes.c_int
         lib.or_replay.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_double, P, P]
         lib.or_level.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                  ctypes.c_double, P, P]
@@ -185,3 +193,50 @@ def threads() -> int:
     """OpenMP threads the oracle uses (OMP_NUM_THREADS or all cores)."""
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v else (os.cpu_count() or 1)
+
+
+# ---- DNN forward-model workload ---------------------------------------------------
+DNN_D = 100
+
+
+def dnn_step(state: np.ndarray, a: int, weights: np.ndarray, A: int):
+    """One forward-model step in FP64: (next_state [100] float64, reward)."""
+    lib = _load()
+    s = np.ascontiguousarray(state, dtype=np.float64).reshape(DNN_D)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    assert w.size == lib.or_dnn_numel(A)
+    out = np.zeros(DNN_D, dtype=np.float64)
+    r = lib.or_dnn_step(_ptr(s), int(a), _ptr(w), A, _ptr(out))
+    return out, float(r)
+
+
+def dnn_q(state: np.ndarray, weights: np.ndarray, A: int) -> np.ndarray:
+    lib = _load()
+    s = np.ascontiguousarray(state, dtype=np.float64).reshape(DNN_D)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    q = np.zeros(A, dtype=np.float64)
+    lib.or_dnn_q(_ptr(s), _ptr(w), A, _ptr(q))
+    return q
+
+
+def dnn_search(roots: np.ndarray, weights: np.ndarray, A: int, d: int, gamma: float, correction: float,
+               exact_gev: bool = False):
+    """BCTS search over the DNN model; same result dict as search()."""
+    lib = _load()
+    r = np.ascontiguousarray(roots, dtype=np.float32).reshape(-1, DNN_D)
+    n = r.shape[0]
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    assert w.size == lib.or_dnn_numel(A)
+    act = np.zeros(n, dtype=np.int32)
+    val = np.zeros((n, A), dtype=np.float64)
+    diag = np.zeros((n, 4 * A + 4), dtype=np.float64)
+    rc = lib.or_dnn_search(_ptr(r), n, _ptr(w), A, d, float(gamma), float(correction), int(bool(exact_gev)),
+                           _ptr(act), _ptr(val), _ptr(diag))
+    if rc != 0:
+        raise ValueError("oracle DNN search rejected its arguments")
+    return {
+        "action": act, "values": val,
+        "q0": diag[:, 0:A], "v_uncorrected": diag[:, A:2 * A], "delta": diag[:, 2 * A:3 * A],
+        "r0": diag[:, 3 * A:4 * A], "pi_o": diag[:, 4 * A].astype(np.int64),
+        "delta_o": diag[:, 4 * A + 1], "delta_e": diag[:, 4 * A + 2], "B": diag[:, 4 * A + 3],
+    }

@@ -406,3 +406,148 @@ void or_level(const or_state *root, int A, int depth, long long first, long long
 #pragma omp parallel for schedule(static)
     for (long long i = 0; i < count; ++i) or_replay(root, A, depth, first + i, gamma, &out[i], &R[i]);
 }
+
+/* ==========================================================================
+ * DNN forward-model workload (Sec. 4, runtime experiments: a randomly
+ * initialised network standing in for a learned forward model; three hidden
+ * layers of width 100 on a 100-wide state and a one-hot action).
+ * Parameter order (PyTorch [out][in]): fm1.w [100][100+A], fm1.b, fm2.w
+ * [100][100], fm2.b, fm3.w [100][100], fm3.b, fmo.w [101][100], fmo.b [101],
+ * q.w [A][100], q.b [A].  Step: x = [s; onehot(a)], h_k = ReLU(W_k h_{k-1} + b_k)
+ * for k = 1..3, o = W_o h_3 + b_o, s' = tanh(o[0..99]), r = o[100].  The leaf
+ * value network is the linear head Q(s) = W_q s + b_q.
+ * ========================================================================== */
+enum { OR_DNN_D = 100, OR_DNN_H = 100 };
+
+typedef struct {
+    const float *w1, *b1, *w2, *b2, *w3, *b3, *wo, *bo, *wq, *bq;
+} or_dnn_w;
+
+static or_dnn_w or_dnn_view(const float *W, int A) {
+    or_dnn_w v;
+    const int D = OR_DNN_D, H = OR_DNN_H;
+    v.w1 = W; v.b1 = v.w1 + (size_t)H * (D + A);
+    v.w2 = v.b1 + H; v.b2 = v.w2 + (size_t)H * H;
+    v.w3 = v.b2 + H; v.b3 = v.w3 + (size_t)H * H;
+    v.wo = v.b3 + H; v.bo = v.wo + (size_t)(D + 1) * H;
+    v.wq = v.bo + D + 1; v.bq = v.wq + (size_t)A * D;
+    return v;
+}
+
+size_t or_dnn_numel(int A) {
+    const size_t D = OR_DNN_D, H = OR_DNN_H;
+    return H * (D + A) + H + 2 * (H * H + H) + (D + 1) * H + (D + 1) + (size_t)A * D + (size_t)A;
+}
+
+/* One forward-model step from s with action a: next state into out, returns r. */
+double or_dnn_step(const double *s, int a, const float *W, int A, double *out) {
+    const int D = OR_DNN_D, H = OR_DNN_H;
+    or_dnn_w w = or_dnn_view(W, A);
+    double h1[OR_DNN_H], h2[OR_DNN_H], h3[OR_DNN_H];
+    for (int j = 0; j < H; ++j) {
+        double acc = w.b1[j];
+        for (int k = 0; k < D; ++k) acc += (double)w.w1[(size_t)j * (D + A) + k] * s[k];
+        acc += (double)w.w1[(size_t)j * (D + A) + D + a]; /* the one-hot action input */
+        h1[j] = acc > 0.0 ? acc : 0.0;
+    }
+    for (int j = 0; j < H; ++j) {
+        double acc = w.b2[j];
+        for (int k = 0; k < H; ++k) acc += (double)w.w2[(size_t)j * H + k] * h1[k];
+        h2[j] = acc > 0.0 ? acc : 0.0;
+    }
+    for (int j = 0; j < H; ++j) {
+        double acc = w.b3[j];
+        for (int k = 0; k < H; ++k) acc += (double)w.w3[(size_t)j * H + k] * h2[k];
+        h3[j] = acc > 0.0 ? acc : 0.0;
+    }
+    double r = 0.0;
+    for (int j = 0; j <= D; ++j) {
+        double acc = w.bo[j];
+        for (int k = 0; k < H; ++k) acc += (double)w.wo[(size_t)j * H + k] * h3[k];
+        if (j < D)
+            out[j] = tanh(acc);
+        else
+            r = acc;
+    }
+    return r;
+}
+
+/* Q(s, .) = W_q s + b_q. */
+void or_dnn_q(const double *s, const float *W, int A, double *q) {
+    const int D = OR_DNN_D;
+    or_dnn_w w = or_dnn_view(W, A);
+    for (int a = 0; a < A; ++a) {
+        double acc = w.bq[a];
+        for (int k = 0; k < D; ++k) acc += (double)w.wq[(size_t)a * D + k] * s[k];
+        q[a] = acc;
+    }
+}
+
+/* Eq. 1's tail from a depth-k node, as for the sprite world. */
+static double or_dnn_value(const double *s, int k, int d, const float *W, int A, double gamma) {
+    double q[64];
+    if (k == d) {
+        or_dnn_q(s, W, A, q);
+        return or_maxv(q, A);
+    }
+    double best = -INFINITY;
+    for (int a = 0; a < A; ++a) {
+        double n[OR_DNN_D];
+        double r = or_dnn_step(s, a, W, A, n);
+        double v = r + gamma * or_dnn_value(n, k + 1, d, W, A, gamma);
+        if (v > best) best = v;
+    }
+    return best;
+}
+
+/*
+ * BCTS search over the DNN model from n float32 roots [n][100]; outputs and
+ * diag layout as or_search_ex (Eq. 1, Prop. 1, Eq. 3, Eq. 4; Eq. 7 or Lemma 2).
+ */
+int or_dnn_search(const float *roots, int n, const float *W, int A, int d, double gamma, double corr,
+                  int exact_gev, int *actions, double *values, double *diag) {
+    if (A < 1 || A > 64 || d < 0 || n < 0) return -1;
+    for (int i = 0; i < n; ++i) {
+        double s0[OR_DNN_D], q0[64], V[64], delta[64], r0[64];
+        for (int k = 0; k < OR_DNN_D; ++k) s0[k] = (double)roots[(size_t)i * OR_DNN_D + k];
+        or_dnn_q(s0, W, A, q0);
+        int pi_o = or_argmax_lowest(q0, A);
+        double *val = values + (size_t)i * A;
+        double *dg = diag ? diag + (size_t)i * (4 * A + 4) : NULL;
+        if (d == 0) {
+            for (int a = 0; a < A; ++a) val[a] = q0[a];
+            actions[i] = pi_o;
+            if (dg) {
+                for (int a = 0; a < A; ++a) { dg[a] = q0[a]; dg[A + a] = q0[a]; dg[2 * A + a] = 0; dg[3 * A + a] = 0; }
+                dg[4 * A] = pi_o; dg[4 * A + 1] = 0; dg[4 * A + 2] = 0; dg[4 * A + 3] = 0;
+            }
+            continue;
+        }
+#pragma omp parallel for schedule(dynamic)
+        for (int a = 0; a < A; ++a) {
+            double s1[OR_DNN_D], q1[64];
+            double r = or_dnn_step(s0, a, W, A, s1);
+            or_dnn_q(s1, W, A, q1);
+            r0[a] = r;
+            delta[a] = r + gamma * or_maxv(q1, A) - q0[a];
+            double tail = (d == 1) ? or_maxv(q1, A) : or_dnn_value(s1, 1, d, W, A, gamma);
+            V[a] = r + gamma * tail;
+        }
+        double delta_o = fabs(delta[pi_o]), delta_e = 0.0;
+        if (A > 1) {
+            for (int a = 0; a < A; ++a)
+                if (a != pi_o) delta_e += fabs(delta[a]);
+            delta_e /= (double)(A - 1);
+        }
+        double B = exact_gev ? or_bellman_penalty_exact(delta_e, delta_o, A, d)
+                             : or_bellman_penalty(delta_e, delta_o, A, d);
+        double gd = pow(gamma, (double)d);
+        for (int a = 0; a < A; ++a) val[a] = (a == pi_o) ? V[a] : V[a] - gd * corr * B;
+        actions[i] = or_argmax_lowest(val, A);
+        if (dg) {
+            for (int a = 0; a < A; ++a) { dg[a] = q0[a]; dg[A + a] = V[a]; dg[2 * A + a] = delta[a]; dg[3 * A + a] = r0[a]; }
+            dg[4 * A] = pi_o; dg[4 * A + 1] = delta_o; dg[4 * A + 2] = delta_e; dg[4 * A + 3] = B;
+        }
+    }
+    return 0;
+}

@@ -138,3 +138,58 @@ def mixed_roots(n: int, seed: int = 7, depths=(1, 2, 3, 4), actions=(4, 9, 18)):
     ds = np.array([depths[next(g) % len(depths)] for _ in range(n)], dtype=np.int32)
     As = np.array([actions[next(g) % len(actions)] for _ in range(n)], dtype=np.int32)
     return root_states(range(1000 + seed * 100000, 1000 + seed * 100000 + n)), ds, As
+
+
+# ---- DNN forward-model workload (a learned forward model stand-in) -------------
+DNN_D = 100  # state width
+DNN_H = 100  # hidden width
+
+
+def dnn_shapes(A: int):
+    """Flat parameter order of the DNN forward model and its Q head, PyTorch [out][in]:
+    three hidden layers of width 100 on [state (100); one-hot action (A)], an output
+    layer giving the next state's 100 pre-activations and the reward, and a linear
+    Q head on the state."""
+    D, H = DNN_D, DNN_H
+    return [("fm1.w", (H, D + A)), ("fm1.b", (H,)), ("fm2.w", (H, H)), ("fm2.b", (H,)),
+            ("fm3.w", (H, H)), ("fm3.b", (H,)), ("fmo.w", (D + 1, H)), ("fmo.b", (D + 1,)),
+            ("q.w", (A, D)), ("q.b", (A,))]
+
+
+def dnn_numel(A: int) -> int:
+    return int(sum(np.prod(s) for _, s in dnn_shapes(A)))
+
+
+def dnn_weights(A: int, seed: int = 4321) -> np.ndarray:
+    """Random initialisation: He-normal (std sqrt(2 / fan_in)) for the ReLU layers,
+    std sqrt(1 / fan_in) for the output layer and the Q head, biases 0.01."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shape in dnn_shapes(A):
+        if name.endswith(".w"):
+            gain = 2.0 if name in ("fm1.w", "fm2.w", "fm3.w") else 1.0
+            parts.append(rng.normal(0.0, np.sqrt(gain / shape[1]), size=shape).astype(np.float32).ravel())
+        else:
+            parts.append(np.full(shape, 0.01, dtype=np.float32))
+    return np.concatenate(parts)
+
+
+def dnn_split(flat: np.ndarray, A: int) -> dict:
+    out, off = {}, 0
+    for name, shape in dnn_shapes(A):
+        n = int(np.prod(shape))
+        out[name] = flat[off:off + n].reshape(shape)
+        off += n
+    assert off == flat.size
+    return out
+
+
+def dnn_root_states(seeds) -> np.ndarray:
+    """float32 [n][100], uniform in [-1, 1), one splitmix64 stream per seed."""
+    seeds = list(seeds)
+    out = np.zeros((len(seeds), DNN_D), dtype=np.float32)
+    for i, s in enumerate(seeds):
+        g = splitmix64(0xD1B54A32D192ED03 ^ int(s))
+        for j in range(DNN_D):
+            out[i, j] = np.float32((next(g) >> 11) / float(1 << 53) * 2.0 - 1.0)
+    return out
