@@ -234,7 +234,9 @@ BCTS_API int bcts_env_step(const bcts_state *s, int a, bcts_state *out, int *rew
 BCTS_API int bcts_render(const bcts_state *d_states, int64_t n, uint8_t *d_frames, void *stream);
 
 /* ---- measurement ------------------------------------------------------------ */
-/* Kernel classes timed by bcts_profile.  BCTS_KERN_CONV1 is conv1 over whole
+/* Kernel classes timed by bcts_profile (and bcts_dnn_profile: the DNN
+ * workload's forward-model layers are BCTS_KERN_DNN_MLP, its Q head
+ * BCTS_KERN_DNN_Q, its per-child epilogues BCTS_KERN_EXPAND).  BCTS_KERN_CONV1 is conv1 over whole
  * frame stacks; when a search scores its leaves from their parents' partial
  * conv1 maps (frame-stacking linearity: the three older history slots of a
  * leaf are its parent's three newest), the parents' maps are
@@ -242,7 +244,7 @@ BCTS_API int bcts_render(const bcts_state *d_states, int64_t n, uint8_t *d_frame
 enum {
     BCTS_KERN_EXPAND = 0, BCTS_KERN_RENDER, BCTS_KERN_CONV1, BCTS_KERN_CONV2, BCTS_KERN_CONV3,
     BCTS_KERN_FC1, BCTS_KERN_FC2, BCTS_KERN_BACKUP, BCTS_KERN_CONV1_PARTIAL, BCTS_KERN_CONV1_LEAF,
-    BCTS_KERN_COUNT
+    BCTS_KERN_DNN_MLP, BCTS_KERN_DNN_Q, BCTS_KERN_COUNT
 };
 
 /*
@@ -267,6 +269,35 @@ BCTS_API int bcts_qnet(bcts_ctx *ctx, const uint8_t *d_frames, int64_t n, float 
  * BCTS_ETIMEOUT when it did (the expected outcome) and BCTS_OK if no time-out
  * was reported.  Nothing faults, traps or hangs; the device stays usable. */
 BCTS_API int bcts_selftest_wait(int timeout_us);
+
+/* ---- DNN forward-model workload ----------------------------------------------
+ * Sec. 4's second runtime workload: Batch-BFS over a randomly initialised
+ * network standing in for a learned forward model (three hidden layers of
+ * width 100 on a 100-wide state and a one-hot action).  Model, in the weights'
+ * PyTorch order (FP32, flat, bcts_dnn_numel(A) floats):
+ *   fm1.w [100][100 + A], fm1.b [100], fm2.w [100][100], fm2.b [100],
+ *   fm3.w [100][100], fm3.b [100], fmo.w [101][100], fmo.b [101],
+ *   q.w [A][100], q.b [A];
+ *   x = [s; onehot(a)], h_k = ReLU(W_k h_(k-1) + b_k) (k = 1..3),
+ *   o = fmo.w h_3 + fmo.b, s' = tanh(o[0..99]), r = o[100]   (the simulator G),
+ *   Q(s, .) = q.w s + q.b                                     (the value network).
+ * States are BCTS_DNN_STATE floats.  The search is the same as bcts_search
+ * (Alg. 1, Prop. 1, Eq. 3/4 with Eq. 7, or Lemma 2 with BCTS_FLAG_EXACT_GEV in
+ * flags), in FP32 on CUDA cores: A in [1, 32], d in [0, 16], n * A^d < 2^31.
+ * Values: n x A floats.  Errors as for bcts_create / bcts_search; the context's
+ * message is returned by bcts_dnn_last_error. */
+#define BCTS_DNN_STATE 100
+typedef struct bcts_dnn_ctx bcts_dnn_ctx;
+BCTS_API size_t bcts_dnn_numel(int A);
+BCTS_API int bcts_dnn_create(const float *weights, int A, int d, float gamma, float correction, int flags,
+                             bcts_dnn_ctx **out);
+BCTS_API void bcts_dnn_destroy(bcts_dnn_ctx *ctx);
+BCTS_API int bcts_dnn_search(bcts_dnn_ctx *ctx, const float *roots, int n, int32_t *out_action, float *out_values);
+BCTS_API int bcts_dnn_search_device(bcts_dnn_ctx *ctx, const float *d_roots, int n, int32_t *d_out_action,
+                                    float *d_out_values, void *stream);
+BCTS_API int bcts_dnn_profile(bcts_dnn_ctx *ctx, int enable, double *out_ms, int64_t *out_launches,
+                              int64_t *out_total_launches);
+BCTS_API const char *bcts_dnn_last_error(const bcts_dnn_ctx *ctx);
 
 /* ---- allocation-free Q-network evaluation ------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that

@@ -32,12 +32,13 @@ PRECISIONS = {"fp32": BCTS_PREC_FP32, "bf16": BCTS_PREC_BF16, "fp8": BCTS_PREC_F
 EXPORTED = ["bcts_qnet_numel", "bcts_create", "bcts_destroy", "bcts_last_error", "bcts_search",
             "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll", "bcts_expand",
             "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait", "bcts_tree_nodes",
-            "bcts_search_tree"]
+            "bcts_search_tree", "bcts_dnn_numel", "bcts_dnn_create", "bcts_dnn_destroy", "bcts_dnn_search",
+            "bcts_dnn_search_device", "bcts_dnn_profile", "bcts_dnn_last_error"]
 BCTS_STATIC_MAX_NODES = 128
 BCTS_FLAG_FRAMES = 1
 BCTS_FLAG_EXACT_GEV = 2
 KERNEL_CLASSES = ["expand", "render", "conv1", "conv2", "conv3", "fc1", "fc2", "backup", "conv1_partial",
-                  "conv1_leaf"]
+                  "conv1_leaf", "dnn_mlp", "dnn_q"]
 
 
 class bcts_options(ctypes.Structure):
@@ -75,6 +76,20 @@ lib.bcts_selftest_wait.argtypes = [_I]
 lib.bcts_tree_nodes.argtypes = [_I, _I, _I]
 lib.bcts_tree_nodes.restype = ctypes.c_int64
 lib.bcts_search_tree.argtypes = [_P, _P, _I, _P, _P, _P, _P, _P]
+lib.bcts_dnn_numel.argtypes = [_I]
+lib.bcts_dnn_numel.restype = ctypes.c_size_t
+lib.bcts_dnn_create.argtypes = [_P, _I, _I, ctypes.c_float, ctypes.c_float, _I, ctypes.POINTER(_P)]
+lib.bcts_dnn_create.restype = _I
+lib.bcts_dnn_destroy.argtypes = [_P]
+lib.bcts_dnn_destroy.restype = None
+lib.bcts_dnn_search.argtypes = [_P, _P, _I, _P, _P]
+lib.bcts_dnn_search.restype = _I
+lib.bcts_dnn_search_device.argtypes = [_P, _P, _I, _P, _P, _P]
+lib.bcts_dnn_search_device.restype = _I
+lib.bcts_dnn_profile.argtypes = [_P, _I, _P, _P, _P]
+lib.bcts_dnn_profile.restype = _I
+lib.bcts_dnn_last_error.argtypes = [_P]
+lib.bcts_dnn_last_error.restype = ctypes.c_char_p
 for _f in ("bcts_search", "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll",
            "bcts_expand", "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait", "bcts_search_tree"):
     getattr(lib, _f).restype = _I
@@ -269,3 +284,73 @@ def bcts_search_tree(ctx: Context, d_roots, n: int, d_action, d_values, d_node_R
     of every node at depths 1..d, level-major, Alg. 1 order); device pointers."""
     return _check(lib.bcts_search_tree(ctx.handle, _addr(d_roots), n, _addr(d_action), _addr(d_values),
                                        _addr(d_node_R), _addr(d_node_V), _stream(stream)), ctx)
+
+
+# ---- DNN forward-model workload ---------------------------------------------------
+DNN_STATE = 100
+
+
+class DnnContext:
+    """Owns one `bcts_dnn_ctx` (Batch-BFS over the DNN forward model)."""
+
+    def __init__(self, handle, A, d):
+        self.handle, self.A, self.d = handle, A, d
+
+    def close(self):
+        if self.handle:
+            lib.bcts_dnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _dnn_check(rc: int, ctx=None):
+    if rc < 0:
+        msg = lib.bcts_dnn_last_error(ctx.handle if ctx is not None else None)
+        raise BctsError(rc, (msg or b"").decode())
+    return rc
+
+
+def bcts_dnn_numel(A: int) -> int:
+    return int(lib.bcts_dnn_numel(A))
+
+
+def bcts_dnn_create(weights: np.ndarray, A: int, d: int, gamma: float, correction: float,
+                    flags: int = 0) -> DnnContext:
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    if w.size != bcts_dnn_numel(A):
+        raise ValueError(f"expected {bcts_dnn_numel(A)} weights for A={A}, got {w.size}")
+    h = _P()
+    _dnn_check(lib.bcts_dnn_create(w.ctypes.data, A, d, gamma, correction, flags, ctypes.byref(h)))
+    return DnnContext(h, A, d)
+
+
+def bcts_dnn_search(ctx: DnnContext, roots: np.ndarray):
+    """Host roots float32 [n][100] -> (actions [n] int32, values [n][A] float32)."""
+    r = np.ascontiguousarray(roots, dtype=np.float32).reshape(-1, DNN_STATE)
+    n = r.shape[0]
+    act = np.zeros(n, dtype=np.int32)
+    val = np.zeros((n, ctx.A), dtype=np.float32)
+    _dnn_check(lib.bcts_dnn_search(ctx.handle, r.ctypes.data, n, act.ctypes.data, val.ctypes.data), ctx)
+    return act, val
+
+
+def bcts_dnn_search_device(ctx: DnnContext, d_roots, n: int, d_action, d_values, stream=None) -> int:
+    return _dnn_check(lib.bcts_dnn_search_device(ctx.handle, _addr(d_roots), n, _addr(d_action), _addr(d_values),
+                                                 _stream(stream)), ctx)
+
+
+def bcts_dnn_profile(ctx: DnnContext, enable: bool):
+    """As bcts_profile, for a DNN context: (ms dict, launches dict, total launches)."""
+    k = len(KERNEL_CLASSES)
+    ms = np.zeros(k, dtype=np.float64)
+    cnt = np.zeros(k, dtype=np.int64)
+    tot = np.zeros(1, dtype=np.int64)
+    _dnn_check(lib.bcts_dnn_profile(ctx.handle, int(bool(enable)), ms.ctypes.data, cnt.ctypes.data, tot.ctypes.data),
+               ctx)
+    return ({c: float(ms[i]) for i, c in enumerate(KERNEL_CLASSES)},
+            {c: int(cnt[i]) for i, c in enumerate(KERNEL_CLASSES)}, int(tot[0]))

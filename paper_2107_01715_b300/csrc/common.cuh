@@ -43,7 +43,8 @@ const char *thread_error();
 // ---- per-kernel-class timing (CUDA events on the launching stream) ----------
 // Kernel classes, same numbering as BCTS_KERN_* in bcts.h.
 enum KernelKind {
-  K_EXPAND = 0, K_RENDER, K_CONV1, K_CONV2, K_CONV3, K_FC1, K_FC2, K_BACKUP, K_CONV1_PARTIAL, K_CONV1_LEAF, K_COUNT
+  K_EXPAND = 0, K_RENDER, K_CONV1, K_CONV2, K_CONV3, K_FC1, K_FC2, K_BACKUP, K_CONV1_PARTIAL, K_CONV1_LEAF,
+  K_DNN_MLP, K_DNN_Q, K_COUNT
 };
 
 struct Profiler;

@@ -85,14 +85,13 @@ void profiler_destroy(Profiler *p) { delete p; }
 
 }  // namespace bcts
 
-extern "C" int bcts_profile(bcts_ctx *ctx, int enable, double *out_ms, int64_t *out_launches,
-                            int64_t *out_total) {
-  if (!ctx) return BCTS_EINVAL;
-  bcts::Ctx *c = reinterpret_cast<bcts::Ctx *>(ctx);
-  bcts::Profiler *p = c->prof;
-  cudaStreamSynchronize(c->stream);
+namespace bcts {
+// Totals since the last read (then reset), recording switched on or off.
+int profiler_read(Profiler *p, cudaStream_t st, int enable, double *out_ms, int64_t *out_launches,
+                  int64_t *out_total) {
+  cudaStreamSynchronize(st);
   p->drain();
-  for (int k = 0; k < bcts::K_COUNT; ++k) {
+  for (int k = 0; k < K_COUNT; ++k) {
     if (out_ms) out_ms[k] = p->ms[k];
     if (out_launches) out_launches[k] = p->launches[k];
     p->ms[k] = 0.0;
@@ -103,3 +102,12 @@ extern "C" int bcts_profile(bcts_ctx *ctx, int enable, double *out_ms, int64_t *
   p->on = enable != 0;
   return BCTS_OK;
 }
+}  // namespace bcts
+
+extern "C" int bcts_profile(bcts_ctx *ctx, int enable, double *out_ms, int64_t *out_launches,
+                            int64_t *out_total) {
+  if (!ctx) return BCTS_EINVAL;
+  bcts::Ctx *c = reinterpret_cast<bcts::Ctx *>(ctx);
+  return bcts::profiler_read(c->prof, c->stream, enable, out_ms, out_launches, out_total);
+}
+

@@ -77,6 +77,8 @@ Profiler *profiler_create();
 void profiler_destroy(Profiler *p);
 int64_t profiler_total(const Profiler *p);
 void profiler_add(Profiler *p, int64_t launches);
+int profiler_read(Profiler *p, cudaStream_t st, int enable, double *out_ms, int64_t *out_launches,
+                  int64_t *out_total);
 void mixed_destroy(MixedState *m);
 
 }  // namespace bcts
