@@ -46,6 +46,8 @@ WORKLOADS = {
                       name="precision form: 8 roots, |A|=18, d=4, leaf Q-net in reduced precision"),
     "batched": dict(n=256, A=18, d=4, gamma=0.99, c=1.0, precision="bf16",
                     name="batched form: 256 roots, d uniform in {1,2,3,4}, |A| in {4,9,18}, BF16, graph-replayed"),
+    "dnn": dict(n=16, A=10, d=5, gamma=0.99, c=1.0, precision="fp32",
+                name="DNN forward model (Sec. 4): 16 roots, |A|=10, d=5, 100-wide state, 3 hidden layers of 100, FP32"),
     "serving": dict(n=1024, A=18, d=4, gamma=0.99, c=1.0, precision="bf16", rate=500.0, seconds=4.0,
                     budget=120 << 30,
                     name="serving form: Poisson requests from 1024 episodes, d in {2,3,4}, |A|=18, BF16, "
@@ -259,6 +261,103 @@ def cpu_baseline(W, wl, target_s=15.0):
     return {"value": leaves / dt, "unit": "leaf nodes/s", "cores": oracle.threads(), "kind": "oracle",
             "sample": f"1 root (seed 0) of the workload: {leaves} leaves + {1 + wl['A']} root/depth-1 "
                       f"Q evaluations, FP64, {dt:.1f} s"}
+
+
+def run_dnn(args, wl):
+    """Batch-BFS over the DNN forward model: device-resident roots, per-kernel
+    events, ALU roofline of the forward-model layers (FP32 CUDA cores)."""
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2107_01715_b300 import bcts
+    n, A, d = wl["n"], wl["A"], wl["d"]
+    W = inputs.dnn_weights(A)
+    ctx = bcts.bcts_dnn_create(W, A, d, wl["gamma"], wl["c"])
+    roots = inputs.dnn_root_states(range(rank * n, rank * n + n))
+    d_roots = torch.from_numpy(roots).to(dev)
+    d_act = torch.empty(n, dtype=torch.int32, device=dev)
+    d_val = torch.empty(n * A, dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    leaves = n * A ** d
+    expanded = sum(n * A ** i for i in range(1, d + 1))  # children produced by the forward model
+
+    def step():
+        bcts.bcts_dnn_search_device(ctx, d_roots, n, d_act, d_val, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        bcts.bcts_dnn_profile(ctx, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+            stream.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+    prof_ms, prof_cnt, launches = bcts.bcts_dnn_profile(ctx, False)
+    total_s = max_over_ranks(world, sum(a.elapsed_time(b) for a, b in ev) / 1e3, dev)
+    value = world * leaves * args.steps / total_s
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        bcts.bcts_dnn_search(ctx, roots)
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_value = world * leaves * args.steps / max_over_ranks(world, sum(e2e_times), dev)
+    if rank != 0:
+        ctx.close()
+        return
+    pk, pk_kind = peaks()
+    # forward-model MACs per child: W1's state part once per parent (shared by A
+    # children), layers 2 and 3, and the 101-row output layer
+    macs_child = 100 * 100 / A + 2 * 100 * 100 + 101 * 100
+    flops = 2.0 * macs_child * expanded * args.steps
+    mlp_s = prof_ms["dnn_mlp"] / 1e3
+    peak = pk.get("sm_max_mhz", 2032.0) * 1e6 * 148 * 128 * 2 / 1e12
+    achieved = flops / mlp_s / 1e12 if mlp_s > 0 else None
+    roofline = {"kernel": "dnn_mlp", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "traffic_note": "no ncu capture of this kernel class",
+                "peak_note": "FP32 FMA: 148 SMs x 128 lanes x 2 FLOP x max SM clock (of " + pk_kind + " clock)",
+                "algorithmic_flops_per_launch": flops / max(prof_cnt["dnn_mlp"], 1),
+                "avg_launch_ms": prof_ms["dnn_mlp"] / max(prof_cnt["dnn_mlp"], 1), "launches": prof_cnt["dnn_mlp"]}
+    cb = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        # a bounded sample: the workload's roots one by one until about 10 s of CPU work
+        t0 = time.perf_counter()
+        k = 0
+        while k < n and time.perf_counter() - t0 < 10.0:
+            oracle.dnn_search(roots[k:k + 1], W, A, d, float(np.float32(wl["gamma"])), wl["c"])
+            k += 1
+        dt = time.perf_counter() - t0
+        cb = {"value": k * A ** d / dt, "unit": "leaf nodes/s", "cores": oracle.threads(), "kind": "oracle",
+              "sample": f"{k} roots of the workload: {k * A ** d} leaves, "
+                        f"{k * sum(A ** i for i in range(1, d + 1))} forward-model steps, FP64, {dt:.1f} s"}
+    line = {"metric": METRIC, "value": value, "unit": "leaf nodes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "roots_per_step": n, "A": A, "d": d, "leaves_per_step": leaves,
+                       "forward_model_steps_per_step": expanded,
+                       "l2": "flushed between steps (256 MB write)"},
+            "decisions_per_s": world * n * args.steps / total_s,
+            "e2e": {"value": e2e_value, "unit": "leaf nodes/s", "h2d_bytes_per_step": n * 400,
+                    "d2h_bytes_per_step": n * 4 + n * A * 4},
+            "gpu_launches": launches,
+            "kernel_ms": prof_ms, "kernel_launches": prof_cnt, "roofline": roofline, "cpu_baseline": cb,
+            "clocks": _clock_line(clk, pk)}
+    print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 def run_reference(args, wl):
@@ -611,6 +710,8 @@ def main():
         run_batched(args, wl)
     elif args.workload == "serving":
         run_serving(args, wl)
+    elif args.workload == "dnn":
+        run_dnn(args, wl)
     else:
         run_ours(args, wl)
 

@@ -284,8 +284,9 @@ BCTS_API int bcts_selftest_wait(int timeout_us);
  * States are BCTS_DNN_STATE floats.  The search is the same as bcts_search
  * (Alg. 1, Prop. 1, Eq. 3/4 with Eq. 7, or Lemma 2 with BCTS_FLAG_EXACT_GEV in
  * flags), in FP32 on CUDA cores: A in [1, 32], d in [0, 16], n * A^d < 2^31.
- * Values: n x A floats.  Errors as for bcts_create / bcts_search; the context's
- * message is returned by bcts_dnn_last_error. */
+ * Values: n x A floats.  Device roots (bcts_dnn_search_device) must be 16-byte
+ * aligned.  Errors as for bcts_create / bcts_search; the context's message is
+ * returned by bcts_dnn_last_error. */
 #define BCTS_DNN_STATE 100
 typedef struct bcts_dnn_ctx bcts_dnn_ctx;
 BCTS_API size_t bcts_dnn_numel(int A);

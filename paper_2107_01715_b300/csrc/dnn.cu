@@ -29,96 +29,137 @@ constexpr int kMaxDnnDepth = 16;
 constexpr int64_t kChunkRows = int64_t(1) << 21;  // children per forward-model pass
 
 // ---------------------------------------------------------------------------
-// out[m][n] = act(in[m][0..K) . W[n][0..K) + b[n]), m < M, n < N (N <= 112, K <= 112).
-// Persistent blocks: W in shared memory once per block (row stride K + 1 words,
-// so the 16 column owners of a warp hit distinct banks), then 128-row tiles of
-// `in`; thread t owns rows 8 (t / 16) .. + 7 and columns t % 16 + 16 j, j < 7.
+// out[m][n] = act(in[m][0..K) . W[n][0..K) + b[n]), m < M, n < N <= 128,
+// K <= kXS and a multiple of 4 (rows of `in` are K floats, 16-byte aligned).
+// Persistent blocks: W transposed into shared memory once per block, [k][128]
+// (so lane l reads columns 4l..4l+3 of a k with one 16-byte load, conflict
+// free); then 64-row tiles of `in`, double-buffered with cp.async so the next
+// tile lands while this one is multiplied.  Warp w owns rows 8w..8w+7 (its
+// activations are broadcasts), lane l columns 4l..4l+3: 32 FMAs per three
+// 16-byte shared loads.
 // ---------------------------------------------------------------------------
-constexpr int kTileRows = 128;
-constexpr int kMaxN = 112;
+constexpr int kTileRows = 64;
+constexpr int kNC = 128;  // output columns per tile (N padded)
+constexpr int kXS = 104;  // activation row stride in shared memory (floats, 16-byte multiple)
 
-template <bool RELU>
+__device__ __forceinline__ void cp_async16_zfill(float *dst, const float *src, bool valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+// What a dense launch reads and writes besides in / W / b / out.
+struct DenseIO {
+  // IN_H1: input row c is ReLU(P[c / A] + W1a[c % A] + b1) (layer 1 of child c)
+  const float *P = nullptr, *w1a = nullptr, *b1 = nullptr;
+  int A = 1;
+  // EPI_STATE: columns 0..99 -> s_next = tanh, column 100 -> R_child = R_parent[c / A] + gp r
+  float *s_next = nullptr, *R_child = nullptr;
+  const float *Rp = nullptr;
+  float gp = 1.f;
+};
+enum { IN_ROWS = 0, IN_H1 = 1 };
+enum { EPI_LINEAR = 0, EPI_RELU = 1, EPI_STATE = 2 };
+
+template <int IN, int EPI>
 __global__ void __launch_bounds__(256) dense_kernel(const float *__restrict__ in, int64_t M, int K,
                                                     const float *__restrict__ W, const float *__restrict__ b, int N,
-                                                    float *__restrict__ out, int ldo) {
-  extern __shared__ float sm[];
-  // both tiles have odd row strides (K + 1 words): the column owners of a warp,
-  // and its two row groups (8 rows apart), then fall into distinct banks
-  const int ks = K + 1;
-  float *Ws = sm;                // [kMaxN][K + 1]
-  float *Xs = sm + kMaxN * ks;   // [kTileRows][K + 1]
-  for (int i = threadIdx.x; i < kMaxN * (K + 1); i += blockDim.x) {
-    const int n = i / (K + 1), k = i - n * (K + 1);
-    Ws[i] = (n < N && k < K) ? W[size_t(n) * K + k] : 0.f;
-  }
-  const int rg = threadIdx.x >> 4, cg = threadIdx.x & 15;
-  float bias[7];
-#pragma unroll
-  for (int j = 0; j < 7; ++j) bias[j] = (b && cg + 16 * j < N) ? b[cg + 16 * j] : 0.f;
-  for (int64_t m0 = int64_t(blockIdx.x) * kTileRows; m0 < M; m0 += int64_t(gridDim.x) * kTileRows) {
-    __syncthreads();  // the previous tile is consumed (and W is in place)
-    const int64_t rows = M - m0 < kTileRows ? M - m0 : kTileRows;
-    for (int i = threadIdx.x; i < kTileRows * K; i += blockDim.x) {
-      const int r = i / K, k = i - r * K;
-      Xs[r * ks + k] = i < rows * K ? in[m0 * K + i] : 0.f;
+                                                    float *__restrict__ out, int ldo, const DenseIO io) {
+  extern __shared__ __align__(16) float sm[];
+  float *Wt = sm;                     // [K][kNC]
+  float *Xs = sm + K * kNC;           // [2][kTileRows][kXS]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (M + kTileRows - 1) / kTileRows;
+  const int kq = K / 4;  // 16-byte chunks per row
+  // rows of a tile: copied with cp.async (IN_ROWS), or formed from the parent's
+  // layer-1 product and the action column (IN_H1, synchronous)
+  auto issue = [&](int64_t tile, int buf) {
+    float *dst = Xs + buf * (kTileRows * kXS);
+    const int64_t m0 = tile * kTileRows;
+    for (int i = threadIdx.x; i < kTileRows * kq; i += blockDim.x) {
+      const int r = i / kq, q = i - r * kq;
+      const bool ok = m0 + r < M;
+      if (IN == IN_ROWS) {
+        cp_async16_zfill(dst + r * kXS + 4 * q, in + (ok ? (m0 + r) * K + 4 * q : 0), ok);
+      } else {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ok) {
+          const int64_t c = m0 + r, par = c / io.A;
+          const int a = int(c - par * io.A);
+          const float4 p = *reinterpret_cast<const float4 *>(io.P + par * K + 4 * q);
+          const float4 w = *reinterpret_cast<const float4 *>(io.w1a + a * K + 4 * q);
+          const float4 bb = *reinterpret_cast<const float4 *>(io.b1 + 4 * q);
+          v = make_float4(fmaxf(p.x + w.x + bb.x, 0.f), fmaxf(p.y + w.y + bb.y, 0.f), fmaxf(p.z + w.z + bb.z, 0.f),
+                          fmaxf(p.w + w.w + bb.w, 0.f));
+        }
+        *reinterpret_cast<float4 *>(dst + r * kXS + 4 * q) = v;
+      }
     }
-    __syncthreads();
-    float acc[8][7];
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  int64_t tile = blockIdx.x;
+  if (tile < ntiles) issue(tile, 0);
+  // W, read in its own row order (coalesced), stored transposed
+  for (int i = threadIdx.x; i < kNC * K; i += blockDim.x) {
+    const int n = i / K, k = i - n * K;
+    Wt[k * kNC + n] = n < N ? W[i] : 0.f;
+  }
+  float bias[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) bias[c] = (b && 4 * lane + c < N) ? b[4 * lane + c] : 0.f;
+  for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+    const int64_t next = tile + gridDim.x;
+    if (next < ntiles)
+      issue(next, (it + 1) & 1);
+    else
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncthreads();  // this tile (and W) visible to every warp
+    const float *xs = Xs + (it & 1) * (kTileRows * kXS) + warp * 8 * kXS;
+    float acc[8][4];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int j = 0; j < 7; ++j) acc[r][j] = bias[j];
-    const float *xr = Xs + (rg * 8) * ks;
-    const float *wc = Ws + cg * (K + 1);
-    for (int k = 0; k < K; ++k) {
-      float x[8], w[7];
+      for (int c = 0; c < 4; ++c) acc[r][c] = bias[c];
+    for (int k0 = 0; k0 < K; k0 += 4) {
+      float4 x[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) x[r] = xr[r * ks + k];
+      for (int r = 0; r < 8; ++r) x[r] = *reinterpret_cast<const float4 *>(xs + r * kXS + k0);
 #pragma unroll
-      for (int j = 0; j < 7; ++j) w[j] = wc[16 * j * (K + 1) + k];
+      for (int kk = 0; kk < 4; ++kk) {
+        const float4 w = *reinterpret_cast<const float4 *>(Wt + (k0 + kk) * kNC + 4 * lane);
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int j = 0; j < 7; ++j) acc[r][j] = fmaf(x[r], w[j], acc[r][j]);
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int64_t m = m0 + rg * 8 + r;
-      if (m >= M) break;
-#pragma unroll
-      for (int j = 0; j < 7; ++j) {
-        const int n = cg + 16 * j;
-        if (n < N) out[m * ldo + n] = RELU ? fmaxf(acc[r][j], 0.f) : acc[r][j];
+        for (int r = 0; r < 8; ++r) {
+          const float xv = kk == 0 ? x[r].x : (kk == 1 ? x[r].y : (kk == 2 ? x[r].z : x[r].w));
+          acc[r][0] = fmaf(xv, w.x, acc[r][0]);
+          acc[r][1] = fmaf(xv, w.y, acc[r][1]);
+          acc[r][2] = fmaf(xv, w.z, acc[r][2]);
+          acc[r][3] = fmaf(xv, w.w, acc[r][3]);
+        }
       }
     }
+    const int64_t m0 = tile * kTileRows + warp * 8;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t m = m0 + r;
+      if (m >= M) break;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int n = 4 * lane + c;
+        if (n >= N) continue;
+        if (EPI == EPI_STATE) {
+          if (n < kD)
+            io.s_next[m * kD + n] = tanhf(acc[r][c]);
+          else
+            io.R_child[m] = (io.Rp ? io.Rp[m / io.A] : 0.f) + io.gp * acc[r][c];
+        } else {
+          out[m * ldo + n] = EPI == EPI_RELU ? fmaxf(acc[r][c], 0.f) : acc[r][c];
+        }
+      }
+    }
+    __syncthreads();  // every warp is done with this buffer before it is refilled
   }
-}
-
-// h1[c][j] = ReLU(P[c / A][j] + W1a[c % A][j] + b1[j]) for every child c.
-__global__ void child_h1_kernel(const float *__restrict__ P, const float *__restrict__ w1a,
-                                const float *__restrict__ b1, int A, int64_t n_child, float *__restrict__ h1) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (i >= n_child * kH) return;
-  const int64_t c = i / kH;
-  const int j = int(i - c * kH);
-  const int64_t p = c / A;
-  const int a = int(c - p * A);
-  h1[i] = fmaxf(P[p * kH + j] + w1a[a * kH + j] + b1[j], 0.f);
-}
-
-// s'[c] = tanh(o[c][0..99]); R_child[c] = R_parent[c / A] + gamma^i o[c][100].
-__global__ void step_out_kernel(const float *__restrict__ o, const float *__restrict__ Rp, int A, float gp,
-                                int64_t n_child, float *__restrict__ s_next, float *__restrict__ R_child) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (i >= n_child * (kD + 1)) return;
-  const int64_t c = i / (kD + 1);
-  const int j = int(i - c * (kD + 1));
-  if (j < kD) {
-    s_next[c * kD + j] = tanhf(o[i]);
-  } else {
-    const float r = o[i];
-    R_child[c] = (Rp ? Rp[c / A] : 0.f) + gp * r;
-  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Q(s) = W_q s + b_q per node (one warp per node, lane l holds s[l + 32 m]); a
@@ -195,7 +236,7 @@ struct DnnCtx {
   // weights: W1s [H][D], W1a [A][H], b1, W2, b2, W3, b3, Wo [D+1][H], bo, Wq [A][D], bq
   float *wbuf = nullptr;
   const float *w1s, *w1a, *b1, *w2, *b2, *w3, *b3, *wo, *bo, *wq, *bq;
-  DevBuf lvl[2], Rl[2], q0, maxq1, r1, V, leafmax, P, hA, hB, o, io_roots, io_act, io_val;
+  DevBuf lvl[2], Rl[2], q0, maxq1, r1, V, leafmax, P, hA, hB, io_roots, io_act, io_val;
   void *host = nullptr;
   size_t host_cap = 0;
 
@@ -222,7 +263,7 @@ struct DnnCtx {
   }
   ~DnnCtx() {
     DevBuf *bufs[] = {&lvl[0], &lvl[1], &Rl[0], &Rl[1], &q0,  &maxq1, &r1,      &V,      &leafmax,
-                      &P,      &hA,     &hB,     &o,      &io_roots, &io_act, &io_val};
+                      &P,      &hA,     &hB,     &io_roots, &io_act, &io_val};
     for (DevBuf *b : bufs)
       if (b->p) cudaFree(b->p);
     if (wbuf) cudaFree(wbuf);
@@ -231,20 +272,20 @@ struct DnnCtx {
     if (prof) profiler_destroy(prof);
   }
 
-  template <bool RELU>
+  template <int IN, int EPI>
   int dense(const float *in, int64_t M, int K, const float *W, const float *b, int N, float *out, int ldo,
-            cudaStream_t st) {
+            const DenseIO &io, cudaStream_t st) {
     if (M <= 0) return BCTS_OK;
-    const size_t smem = size_t(kMaxN + kTileRows) * (K + 1) * sizeof(float);
+    const size_t smem = size_t(K * kNC + 2 * kTileRows * kXS) * sizeof(float);
     static bool attr_done = false;
     if (!attr_done) {
-      cudaFuncSetAttribute(dense_kernel<RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      cudaFuncSetAttribute(dense_kernel<IN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       attr_done = true;
     }
     const int64_t tiles = (M + kTileRows - 1) / kTileRows;
     const unsigned grid = unsigned(tiles < int64_t(2) * sm_count() ? tiles : int64_t(2) * sm_count());
     ProfScope ps(K_DNN_MLP, st);
-    dense_kernel<RELU><<<grid, 256, smem, st>>>(in, M, K, W, b, N, out, ldo);
+    dense_kernel<IN, EPI><<<grid, 256, smem, st>>>(in, M, K, W, b, N, out, ldo, io);
     return cudaGetLastError() == cudaSuccess ? BCTS_OK : fail(BCTS_ECUDA, "DNN dense layer launch failed");
   }
 
@@ -265,26 +306,27 @@ struct DnnCtx {
     if ((rc = ensure(P, size_t(cp) * kH * 4)) != BCTS_OK) return rc;
     if ((rc = ensure(hA, size_t(cc) * kH * 4)) != BCTS_OK) return rc;
     if ((rc = ensure(hB, size_t(cc) * kH * 4)) != BCTS_OK) return rc;
-    if ((rc = ensure(o, size_t(cc) * (kD + 1) * 4)) != BCTS_OK) return rc;
     float *Pp = static_cast<float *>(P.p), *ha = static_cast<float *>(hA.p), *hb = static_cast<float *>(hB.p);
-    float *op = static_cast<float *>(o.p);
     for (int64_t off = 0; off < np; off += chunk_p) {
       const int64_t cnt = np - off < chunk_p ? np - off : chunk_p, nc = cnt * A;
-      if ((rc = dense<false>(parents + off * kD, cnt, kD, w1s, nullptr, kH, Pp, kH, st)) != BCTS_OK) return rc;
-      {
-        ProfScope ps(K_EXPAND, st);
-        child_h1_kernel<<<elem_blocks(nc * kH), 256, 0, st>>>(Pp, w1a, b1, A, nc, ha);
-        if (cudaGetLastError() != cudaSuccess) return fail(BCTS_ECUDA, "DNN layer-1 launch failed");
-      }
-      if ((rc = dense<true>(ha, nc, kH, w2, b2, kH, hb, kH, st)) != BCTS_OK) return rc;
-      if ((rc = dense<true>(hb, nc, kH, w3, b3, kH, ha, kH, st)) != BCTS_OK) return rc;
-      if ((rc = dense<false>(ha, nc, kH, wo, bo, kD + 1, op, kD + 1, st)) != BCTS_OK) return rc;
-      {
-        ProfScope ps(K_EXPAND, st);
-        step_out_kernel<<<elem_blocks(nc * (kD + 1)), 256, 0, st>>>(op, Rp ? Rp + off : nullptr, A, gp, nc,
-                                                                   child + off * A * kD, Rc + off * A);
-        if (cudaGetLastError() != cudaSuccess) return fail(BCTS_ECUDA, "DNN step launch failed");
-      }
+      const DenseIO none;
+      if ((rc = dense<IN_ROWS, EPI_LINEAR>(parents + off * kD, cnt, kD, w1s, nullptr, kH, Pp, kH, none, st)) !=
+          BCTS_OK)
+        return rc;
+      DenseIO l2;  // layer 2 reads each child's layer-1 activations straight from P
+      l2.P = Pp;
+      l2.w1a = w1a;
+      l2.b1 = b1;
+      l2.A = A;
+      if ((rc = dense<IN_H1, EPI_RELU>(nullptr, nc, kH, w2, b2, kH, hb, kH, l2, st)) != BCTS_OK) return rc;
+      if ((rc = dense<IN_ROWS, EPI_RELU>(hb, nc, kH, w3, b3, kH, ha, kH, none, st)) != BCTS_OK) return rc;
+      DenseIO so;  // the output layer writes the child's state and accumulated reward
+      so.s_next = child + off * A * kD;
+      so.R_child = Rc + off * A;
+      so.Rp = Rp ? Rp + off : nullptr;
+      so.gp = gp;
+      so.A = A;
+      if ((rc = dense<IN_ROWS, EPI_STATE>(ha, nc, kH, wo, bo, kD + 1, nullptr, 0, so, st)) != BCTS_OK) return rc;
     }
     return BCTS_OK;
   }
@@ -437,6 +479,8 @@ extern "C" int bcts_dnn_search_device(bcts_dnn_ctx *ctx, const float *d_roots, i
   DnnCtx *c = reinterpret_cast<DnnCtx *>(ctx);
   if (n < 0 || (n > 0 && (!d_roots || !d_action || !d_values)))
     return c->fail(BCTS_EINVAL, "bcts_dnn_search_device: invalid argument");
+  if (reinterpret_cast<uintptr_t>(d_roots) % 16 != 0)  // rows are copied to shared memory in 16-byte pieces
+    return c->fail(BCTS_EINVAL, "bcts_dnn_search_device: d_roots must be 16-byte aligned");
   cudaSetDevice(c->device);
   return c->run(d_roots, n, d_action, d_values, stream ? (cudaStream_t)stream : c->stream);
 }

@@ -75,3 +75,15 @@ def test_dnn_bad_arguments(dev):
     act, val = bcts.bcts_dnn_search(ctx, np.zeros((0, 100), dtype=np.float32))
     assert act.size == 0
     ctx.close()
+
+
+def test_dnn_misaligned_device_roots_rejected(dev):
+    torch, bcts = dev
+    W = inputs.dnn_weights(2)
+    ctx = bcts.bcts_dnn_create(W, 2, 2, 0.99, 1.0)
+    buf = torch.zeros(2 * 100 + 1, dtype=torch.float32, device="cuda")
+    d_act = torch.empty(2, dtype=torch.int32, device="cuda")
+    d_val = torch.empty(4, dtype=torch.float32, device="cuda")
+    with pytest.raises(bcts.BctsError):
+        bcts.bcts_dnn_search_device(ctx, buf.data_ptr() + 4, 2, d_act, d_val)
+    ctx.close()
