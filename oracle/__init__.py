@@ -61,6 +61,9 @@ def _load():
         lib.or_normal_upper_quantile.restype = ctypes.c_double
         lib.or_tree_node.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                      ctypes.c_longlong, P, P]
+        lib.or_search_pruned.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P, P]
+        lib.or_search_pruned.restype = ctypes.c_int
         lib.or_dnn_numel.argtypes = [ctypes.c_int]
         lib.or_dnn_numel.restype = ctypes.c_size_t
         lib.or_dnn_step.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P]
@@ -152,6 +155,29 @@ def search(roots, weights: np.ndarray, A: int, d: int, gamma: float, correction:
         "q0": diag[:, 0:A], "v_uncorrected": diag[:, A:2 * A], "delta": diag[:, 2 * A:3 * A],
         "r0": diag[:, 3 * A:4 * A], "pi_o": diag[:, 4 * A].astype(np.int64),
         "delta_o": diag[:, 4 * A + 1], "delta_e": diag[:, 4 * A + 2], "B": diag[:, 4 * A + 3],
+    }
+
+
+def search_pruned(roots, weights: np.ndarray, A: int, d: int, gamma: float, correction: float, keep: int,
+                  exact_gev: bool = False):
+    """Pruned Batch-BFS: per root action, levels 2..d-1 keep the `keep` nodes with the
+    highest R + gamma^i max Q.  Same dict as search() plus "gap" [n]: the smallest
+    margin between a kept and a dropped score (inf when nothing was dropped)."""
+    lib = _load()
+    r = _state_array(roots).reshape(-1)
+    n = r.shape[0]
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    act = np.zeros(n, dtype=np.int32)
+    val = np.zeros((n, A), dtype=np.float64)
+    diag = np.zeros((n, 4 * A + 5), dtype=np.float64)
+    rc = lib.or_search_pruned(_ptr(r), n, _ptr(w), A, d, float(gamma), float(correction), int(bool(exact_gev)),
+                              int(keep), _ptr(act), _ptr(val), _ptr(diag))
+    if rc != 0:
+        raise ValueError("oracle pruned search rejected its arguments")
+    return {
+        "action": act, "values": val, "q0": diag[:, 0:A], "v_uncorrected": diag[:, A:2 * A],
+        "delta": diag[:, 2 * A:3 * A], "pi_o": diag[:, 4 * A].astype(np.int64), "B": diag[:, 4 * A + 3],
+        "gap": diag[:, 4 * A + 4],
     }
 
 

@@ -551,3 +551,151 @@ int or_dnn_search(const float *roots, int n, const float *W, int A, int d, doubl
     }
     return 0;
 }
+
+/* ==========================================================================
+ * Pruned Batch-BFS (Sec. 4: pruning by an index array of unpruned states,
+ * updated at each pruning step and used to trace the best root action).  The
+ * criterion is the cumulative reward plus the estimated value the same passage
+ * points to: within the subtree of each root action a_0, the nodes of every
+ * level i = 2 .. d-1 are ranked by R + gamma^i max_a Q(s, a) and only the
+ * `keep` best (lowest candidate index among equal scores) are expanded further;
+ * a level's candidates are the children of the previous level's survivors in
+ * the order survivor-index x A + a, survivors kept in increasing index order.
+ * V(a_0) = max over the surviving leaves of R + gamma^d max_a Q; pi_o, the
+ * Bellman errors and the penalty (Eq. 7, or Lemma 2) are the full search's.
+ * diag: 4*A + 5 doubles, as or_search_ex plus [4A+4] = the smallest gap between
+ * a kept and a dropped score over all selections of the root (+inf if none).
+ * ========================================================================== */
+typedef struct {
+    double score;
+    int idx;
+} or_cand;
+
+static int or_cand_cmp(const void *pa, const void *pb) {
+    const or_cand *a = (const or_cand *)pa, *b = (const or_cand *)pb;
+    if (a->score != b->score) return a->score > b->score ? -1 : 1; /* higher score first */
+    return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);       /* then lower index */
+}
+
+static int or_int_cmp(const void *pa, const void *pb) {
+    int a = *(const int *)pa, b = *(const int *)pb;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* V(a_0) of one root-action subtree under the pruning rule; *gap <- min margin. */
+static double or_pruned_subtree(const or_state *s1, double R1, const float *W, int A, int d, double gamma,
+                                int keep, double *gap) {
+    int cnt = 1;
+    or_state *lvl = (or_state *)malloc(sizeof(or_state));
+    double *R = (double *)malloc(sizeof(double));
+    lvl[0] = *s1;
+    R[0] = R1;
+    double gprev = 1.0, gp = gamma; /* gamma^(i-1), gamma^i at level i */
+    for (int i = 2; i <= d; ++i) {
+        gprev = gp;
+        gp *= gamma;
+        int nc = cnt * A;
+        or_state *ch = (or_state *)malloc(sizeof(or_state) * (size_t)nc);
+        double *Rc = (double *)malloc(sizeof(double) * (size_t)nc);
+        double *mq = (double *)malloc(sizeof(double) * (size_t)nc);
+#pragma omp parallel for schedule(dynamic)
+        for (int j = 0; j < nc; ++j) {
+            int r = or_env_step(&lvl[j / A], j % A, &ch[j]);
+            Rc[j] = R[j / A] + gprev * (double)r; /* the reward of step i-1 carries gamma^(i-1) */
+            double q[64];
+            or_q_of_state(&ch[j], W, A, q);
+            mq[j] = or_maxv(q, A);
+        }
+        free(lvl);
+        free(R);
+        if (i == d) {
+            double best = -INFINITY;
+            for (int j = 0; j < nc; ++j) {
+                double v = Rc[j] + gp * mq[j];
+                if (v > best) best = v;
+            }
+            free(ch);
+            free(Rc);
+            free(mq);
+            return best;
+        }
+        int k = nc < keep ? nc : keep;
+        or_cand *c = (or_cand *)malloc(sizeof(or_cand) * (size_t)nc);
+        for (int j = 0; j < nc; ++j) {
+            c[j].score = Rc[j] + gp * mq[j];
+            c[j].idx = j;
+        }
+        qsort(c, (size_t)nc, sizeof(or_cand), or_cand_cmp);
+        if (k < nc && c[k - 1].score - c[k].score < *gap) *gap = c[k - 1].score - c[k].score;
+        int *kept = (int *)malloc(sizeof(int) * (size_t)k);
+        for (int j = 0; j < k; ++j) kept[j] = c[j].idx;
+        qsort(kept, (size_t)k, sizeof(int), or_int_cmp);
+        lvl = (or_state *)malloc(sizeof(or_state) * (size_t)k);
+        R = (double *)malloc(sizeof(double) * (size_t)k);
+        for (int j = 0; j < k; ++j) {
+            lvl[j] = ch[kept[j]];
+            R[j] = Rc[kept[j]];
+        }
+        cnt = k;
+        free(kept);
+        free(c);
+        free(ch);
+        free(Rc);
+        free(mq);
+    }
+    /* d == 1: the depth-1 node is the leaf */
+    double q[64];
+    or_q_of_state(&lvl[0], W, A, q);
+    double v = R[0] + gamma * or_maxv(q, A);
+    free(lvl);
+    free(R);
+    return v;
+}
+
+int or_search_pruned(const or_state *roots, int n, const float *W, int A, int d, double gamma, double corr,
+                     int exact_gev, int keep, int *actions, double *values, double *diag) {
+    if (A < 1 || A > 64 || d < 0 || n < 0 || keep < 1) return -1;
+    for (int i = 0; i < n; ++i) {
+        double q0[64], V[64], delta[64], r0[64];
+        double *val = values + (size_t)i * A;
+        double *dg = diag ? diag + (size_t)i * (4 * A + 5) : NULL;
+        or_q_of_state(&roots[i], W, A, q0);
+        int pi_o = or_argmax_lowest(q0, A);
+        double gap = INFINITY;
+        if (d == 0) {
+            for (int a = 0; a < A; ++a) val[a] = q0[a];
+            actions[i] = pi_o;
+            if (dg) {
+                for (int a = 0; a < A; ++a) { dg[a] = q0[a]; dg[A + a] = q0[a]; dg[2 * A + a] = 0; dg[3 * A + a] = 0; }
+                dg[4 * A] = pi_o; dg[4 * A + 1] = 0; dg[4 * A + 2] = 0; dg[4 * A + 3] = 0; dg[4 * A + 4] = gap;
+            }
+            continue;
+        }
+        for (int a = 0; a < A; ++a) {
+            or_state s1;
+            int r = or_env_step(&roots[i], a, &s1);
+            double q1[64];
+            or_q_of_state(&s1, W, A, q1);
+            r0[a] = (double)r;
+            delta[a] = (double)r + gamma * or_maxv(q1, A) - q0[a];
+            V[a] = or_pruned_subtree(&s1, (double)r, W, A, d, gamma, keep, &gap);
+        }
+        double delta_o = fabs(delta[pi_o]), delta_e = 0.0;
+        if (A > 1) {
+            for (int a = 0; a < A; ++a)
+                if (a != pi_o) delta_e += fabs(delta[a]);
+            delta_e /= (double)(A - 1);
+        }
+        double B = exact_gev ? or_bellman_penalty_exact(delta_e, delta_o, A, d)
+                             : or_bellman_penalty(delta_e, delta_o, A, d);
+        double gd = pow(gamma, (double)d);
+        for (int a = 0; a < A; ++a) val[a] = (a == pi_o) ? V[a] : V[a] - gd * corr * B;
+        actions[i] = or_argmax_lowest(val, A);
+        if (dg) {
+            for (int a = 0; a < A; ++a) { dg[a] = q0[a]; dg[A + a] = V[a]; dg[2 * A + a] = delta[a]; dg[3 * A + a] = r0[a]; }
+            dg[4 * A] = pi_o; dg[4 * A + 1] = delta_o; dg[4 * A + 2] = delta_e; dg[4 * A + 3] = B;
+            dg[4 * A + 4] = gap;
+        }
+    }
+    return 0;
+}
