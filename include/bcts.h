@@ -173,6 +173,22 @@ BCTS_API int64_t bcts_tree_nodes(int n, int A, int d);
 BCTS_API int bcts_search_tree(bcts_ctx *ctx, const bcts_state *d_roots, int n, int32_t *d_out_action,
                               float *d_out_root_values, float *d_node_R, float *d_node_V, void *stream);
 
+/*
+ * Pruned search (Sec. 4: an index array of unpruned states, updated at each
+ * pruning step, traces the best root action; the paper leaves the criterion to
+ * future work).  Host pointers, as bcts_search.  Within the subtree of each root
+ * action a_0, the nodes of every level i = 2 .. d-1 are ranked by their
+ * cumulative reward plus estimated value R + gamma^i max_a Q(s, a) (Alg. 1's R,
+ * the context's Q-network) and only the `keep` best (lowest index among equal
+ * scores, keep in [1, 256]) are expanded further; V(a_0) is the maximum of
+ * R + gamma^d max_a Q over the surviving leaves.  Root Q, pi_o, the Bellman
+ * errors and the penalty (Eq. 7, or Lemma 2 with BCTS_FLAG_EXACT_GEV) are the
+ * full search's.  With d <= 2, or keep at least every level's candidate count,
+ * it is bcts_search.  Work per root: A (keep A)^(d-2) A leaves instead of A^d.
+ */
+BCTS_API int bcts_search_pruned(bcts_ctx *ctx, const bcts_state *roots, int n, int keep, int32_t *out_action,
+                                float *out_root_values);
+
 /* Same as bcts_search with device pointers, asynchronous on `stream`.  The
  * context's buffers are reused by the next search on the same context, so
  * searches on one context must not overlap (the library orders them on the

@@ -563,8 +563,10 @@ int or_dnn_search(const float *roots, int n, const float *W, int A, int d, doubl
  * the order survivor-index x A + a, survivors kept in increasing index order.
  * V(a_0) = max over the surviving leaves of R + gamma^d max_a Q; pi_o, the
  * Bellman errors and the penalty (Eq. 7, or Lemma 2) are the full search's.
- * diag: 4*A + 5 doubles, as or_search_ex plus [4A+4] = the smallest gap between
- * a kept and a dropped score over all selections of the root (+inf if none).
+ * diag: 4*A + 5 doubles, as or_search_ex plus [4A+4] = the smallest positive gap
+ * between a kept and a dropped score over all selections of the root (+inf if
+ * none; scores that are exactly equal belong to identical states and tie the
+ * same way in any precision).
  * ========================================================================== */
 typedef struct {
     double score;
@@ -626,7 +628,22 @@ static double or_pruned_subtree(const or_state *s1, double R1, const float *W, i
             c[j].idx = j;
         }
         qsort(c, (size_t)nc, sizeof(or_cand), or_cand_cmp);
-        if (k < nc && c[k - 1].score - c[k].score < *gap) *gap = c[k - 1].score - c[k].score;
+        if (k < nc) {
+            /* the smallest positive difference between a kept and a dropped score:
+             * exactly equal scores (identical states) tie in any precision and
+             * are resolved by index on both sides */
+            double a = c[k - 1].score, b = c[k].score;
+            for (int m = k; m < nc; ++m)
+                if (c[m].score < a) {
+                    if (a - c[m].score < *gap) *gap = a - c[m].score;
+                    break;
+                }
+            for (int j = k - 1; j >= 0; --j)
+                if (c[j].score > b) {
+                    if (c[j].score - b < *gap) *gap = c[j].score - b;
+                    break;
+                }
+        }
         int *kept = (int *)malloc(sizeof(int) * (size_t)k);
         for (int j = 0; j < k; ++j) kept[j] = c[j].idx;
         qsort(kept, (size_t)k, sizeof(int), or_int_cmp);

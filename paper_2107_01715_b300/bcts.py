@@ -33,7 +33,7 @@ EXPORTED = ["bcts_qnet_numel", "bcts_create", "bcts_destroy", "bcts_last_error",
             "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll", "bcts_expand",
             "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait", "bcts_tree_nodes",
             "bcts_search_tree", "bcts_dnn_numel", "bcts_dnn_create", "bcts_dnn_destroy", "bcts_dnn_search",
-            "bcts_dnn_search_device", "bcts_dnn_profile", "bcts_dnn_last_error"]
+            "bcts_dnn_search_device", "bcts_dnn_profile", "bcts_dnn_last_error", "bcts_search_pruned"]
 BCTS_STATIC_MAX_NODES = 128
 BCTS_FLAG_FRAMES = 1
 BCTS_FLAG_EXACT_GEV = 2
@@ -76,6 +76,8 @@ lib.bcts_selftest_wait.argtypes = [_I]
 lib.bcts_tree_nodes.argtypes = [_I, _I, _I]
 lib.bcts_tree_nodes.restype = ctypes.c_int64
 lib.bcts_search_tree.argtypes = [_P, _P, _I, _P, _P, _P, _P, _P]
+lib.bcts_search_pruned.argtypes = [_P, _P, _I, _I, _P, _P]
+lib.bcts_search_pruned.restype = _I
 lib.bcts_dnn_numel.argtypes = [_I]
 lib.bcts_dnn_numel.restype = ctypes.c_size_t
 lib.bcts_dnn_create.argtypes = [_P, _I, _I, ctypes.c_float, ctypes.c_float, _I, ctypes.POINTER(_P)]
@@ -354,3 +356,14 @@ def bcts_dnn_profile(ctx: DnnContext, enable: bool):
                ctx)
     return ({c: float(ms[i]) for i, c in enumerate(KERNEL_CLASSES)},
             {c: int(cnt[i]) for i, c in enumerate(KERNEL_CLASSES)}, int(tot[0]))
+
+
+def bcts_search_pruned(ctx: Context, roots, keep: int):
+    """Pruned search (per root action, levels 2..d-1 keep the `keep` nodes with the
+    highest R + gamma^i max Q): (actions [n], values [n][A]); host arrays."""
+    r = _roots(roots)
+    n = r.shape[0]
+    act = np.zeros(n, dtype=np.int32)
+    val = np.zeros((n, ctx.A), dtype=np.float32)
+    _check(lib.bcts_search_pruned(ctx.handle, r.ctypes.data, n, int(keep), act.ctypes.data, val.ctypes.data), ctx)
+    return act, val

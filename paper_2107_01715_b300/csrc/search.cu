@@ -298,6 +298,8 @@ int Ctx::export_tree(const std::vector<int64_t> &N, int A_, int d_, const float 
 int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d_action, float *d_values,
                     int A_stride, cudaStream_t st) {
   if (n <= 0) return BCTS_OK;
+  if (prune_keep > 0 && d_ >= 3 && A_ == A_create && d_ == d)
+    return run_search_pruned(d_roots, n, prune_keep, d_action, d_values, A_stride, st);
   ProfilerGuard pg(prof);
   std::vector<int64_t> N(d_ + 1);
   N[0] = n;
@@ -420,7 +422,7 @@ Ctx::~Ctx() {
   if (stream) cudaStreamSynchronize(stream);
   DevBuf *bufs[] = {&frames_buf, &scratch_buf, &q0_buf, &maxq1_buf, &V_buf, &r1_buf, &leafmax_buf,
                     &lvl_buf[0], &lvl_buf[1], &R_buf[0], &R_buf[1], &io_roots, &io_action, &io_values,
-                    &simt_w, &mixed_buf, &z_buf};
+                    &simt_w, &mixed_buf, &z_buf, &pr_cand, &pr_candR, &pr_candQ, &pr_par, &pr_parR, &pr_idx};
   for (DevBuf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (host_stage.p) cudaFreeHost(host_stage.p);

@@ -45,6 +45,8 @@ struct Ctx {
   DevBuf simt_w, frames_buf, scratch_buf, q0_buf, maxq1_buf, V_buf, r1_buf, leafmax_buf;
   DevBuf lvl_buf[2], R_buf[2];
   DevBuf io_roots, io_action, io_values, mixed_buf, z_buf;
+  DevBuf pr_cand, pr_candR, pr_candQ, pr_par, pr_parR, pr_idx;  // pruned search
+  int prune_keep = 0;  // > 0: run_search keeps this many nodes per root action and level (d >= 3)
   HostBuf host_stage;
 
   ServeState *serve = nullptr;
@@ -65,6 +67,8 @@ struct Ctx {
   int export_tree(const std::vector<int64_t> &N, int A_, int d_, const float *leafMax, cudaStream_t st);
   int run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d_action, float *d_values,
                  int A_stride, cudaStream_t st);
+  int run_search_pruned(const bcts_state *d_roots, int n, int keep, int32_t *d_action, float *d_values,
+                        int A_stride, cudaStream_t st);
   int run_mixed(const bcts_state *d_roots, const bcts_state *h_roots, const int32_t *depths,
                 const int32_t *actions, int n, int32_t *d_action, float *d_values);
   int search_host(const bcts_state *roots, int n, const int32_t *depths, const int32_t *actions,
