@@ -46,6 +46,8 @@ WORKLOADS = {
                       name="precision form: 8 roots, |A|=18, d=4, leaf Q-net in reduced precision"),
     "batched": dict(n=256, A=18, d=4, gamma=0.99, c=1.0, precision="bf16",
                     name="batched form: 256 roots, d uniform in {1,2,3,4}, |A| in {4,9,18}, BF16, graph-replayed"),
+    "pruned": dict(n=32, A=18, d=4, keep=32, gamma=0.99, c=1.0, precision="fp32",
+                   name="pruned search: 32 roots, |A|=18, d=4, 32 nodes kept per root action and level, FP32"),
     "dnn": dict(n=16, A=10, d=5, gamma=0.99, c=1.0, precision="fp32",
                 name="DNN forward model (Sec. 4): 16 roots, |A|=10, d=5, 100-wide state, 3 hidden layers of 100, FP32"),
     "serving": dict(n=1024, A=18, d=4, gamma=0.99, c=1.0, precision="bf16", rate=500.0, seconds=4.0,
@@ -54,6 +56,7 @@ WORKLOADS = {
                          "120 GB frame budget"),
 }
 L2_BYTES = 126 * 2 ** 20
+DTYPES = {"fp32": "f32 (bf16x3 split products, f32 accumulate)", "bf16": "bf16", "fp8": "e4m3", "fp32_simt": "f32"}
 # Multiply-accumulates per node each kernel class executes (Nature-DQN layers; conv1 over a
 # whole 4-frame stack, over three stack slots for a parent's partial map, over the one new
 # slot for a leaf scored from its parent's partial map).
@@ -360,6 +363,86 @@ def run_dnn(args, wl):
     ctx.close()
 
 
+def run_pruned(args, wl):
+    """Pruned search at a depth the full tree would not reach in the same time:
+    device-resident roots, per-kernel events; the unit is scored leaves."""
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2107_01715_b300 import bcts
+    n, A, d, keep = wl["n"], wl["A"], wl["d"], wl["keep"]
+    precision = args.precision or wl["precision"]
+    W = inputs.qnet_weights(A, seed=1234)
+    ctx = bcts.bcts_create(W, A, d, wl["gamma"], wl["c"], precision=precision)
+    roots = inputs.root_states(range(rank * n, rank * n + n))
+    d_roots = torch.from_numpy(roots.view(np.uint8).copy()).to(dev)
+    d_act = torch.empty(n, dtype=torch.int32, device=dev)
+    d_val = torch.empty(n * A, dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    # candidates per group and level: A at level 2, min(keep, C) * A afterwards
+    cands, S = [], 1
+    for i in range(2, d + 1):
+        C = S * A
+        cands.append(C)
+        S = min(keep, C)
+    leaves = n * A * cands[-1]
+    scored = n + n * A + n * A * sum(cands)  # Q-network evaluations per search
+
+    def step():
+        bcts.bcts_search_pruned_device(ctx, d_roots, n, keep, d_act, d_val, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        bcts.bcts_profile(ctx, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+            stream.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+    prof_ms, prof_cnt, launches = bcts.bcts_profile(ctx, False)
+    total_s = max_over_ranks(world, sum(a.elapsed_time(b) for a, b in ev) / 1e3, dev)
+    value = world * leaves * args.steps / total_s
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        bcts.bcts_search_pruned(ctx, roots, keep)
+        if i >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+    e2e_value = world * leaves * args.steps / max_over_ranks(world, sum(e2e), dev)
+    if rank != 0:
+        ctx.close()
+        return
+    pk, pk_kind = peaks()
+    dom = max(prof_ms, key=lambda k: prof_ms[k])
+    roofline = None
+    if dom in EXEC_MACS and prof_ms[dom] > 0:
+        roofline = roofline_for(dom, precision, A, scored * args.steps, prof_ms[dom], prof_cnt[dom], pk, pk_kind)
+    line = {"metric": METRIC, "value": value, "unit": "leaf nodes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES.get(precision, precision), "data": "synthetic",
+            "config": {"workload": wl["name"], "roots_per_step": n, "A": A, "d": d, "keep": keep,
+                       "leaves_per_step": leaves, "q_evaluations_per_step": scored, "full_tree_leaves": n * A ** d,
+                       "precision": precision, "l2": "flushed between steps (256 MB write)"},
+            "decisions_per_s": world * n * args.steps / total_s,
+            "e2e": {"value": e2e_value, "unit": "leaf nodes/s", "h2d_bytes_per_step": n * 80,
+                    "d2h_bytes_per_step": n * 4 + n * A * 4},
+            "gpu_launches": launches, "kernel_ms": prof_ms, "kernel_launches": prof_cnt, "roofline": roofline,
+            "cpu_baseline": None, "clocks": _clock_line(clk, pk)}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_reference(args, wl):
     world, rank, _ = dist_setup(args.gpus)
     if rank != 0:
@@ -520,8 +603,7 @@ def run_ours(args, wl):
         "metric": METRIC, "value": value, "unit": "leaf nodes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32 (bf16x3 split products, f32 accumulate)", "bf16": "bf16", "fp8": "e4m3",
-                  "fp32_simt": "f32"}.get(precision, precision),
+        "dtype": DTYPES.get(precision, precision),
         "data": "synthetic",
         "config": {"workload": wl["name"], "roots_per_step": n, "A": A, "d": d, "gamma": wl["gamma"],
                    "correction": wl["c"], "leaves_per_step": leaves, "precision": precision,
@@ -712,6 +794,8 @@ def main():
         run_serving(args, wl)
     elif args.workload == "dnn":
         run_dnn(args, wl)
+    elif args.workload == "pruned":
+        run_pruned(args, wl)
     else:
         run_ours(args, wl)
 

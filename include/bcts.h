@@ -188,6 +188,9 @@ BCTS_API int bcts_search_tree(bcts_ctx *ctx, const bcts_state *d_roots, int n, i
  */
 BCTS_API int bcts_search_pruned(bcts_ctx *ctx, const bcts_state *roots, int n, int keep, int32_t *out_action,
                                 float *out_root_values);
+/* The same with device pointers, asynchronous on `stream` (as bcts_search_device). */
+BCTS_API int bcts_search_pruned_device(bcts_ctx *ctx, const bcts_state *d_roots, int n, int keep,
+                                       int32_t *d_out_action, float *d_out_root_values, void *stream);
 
 /* Same as bcts_search with device pointers, asynchronous on `stream`.  The
  * context's buffers are reused by the next search on the same context, so

@@ -33,7 +33,8 @@ EXPORTED = ["bcts_qnet_numel", "bcts_create", "bcts_destroy", "bcts_last_error",
             "bcts_search_device", "bcts_search_mixed", "bcts_submit", "bcts_poll", "bcts_expand",
             "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait", "bcts_tree_nodes",
             "bcts_search_tree", "bcts_dnn_numel", "bcts_dnn_create", "bcts_dnn_destroy", "bcts_dnn_search",
-            "bcts_dnn_search_device", "bcts_dnn_profile", "bcts_dnn_last_error", "bcts_search_pruned"]
+            "bcts_dnn_search_device", "bcts_dnn_profile", "bcts_dnn_last_error", "bcts_search_pruned",
+            "bcts_search_pruned_device"]
 BCTS_STATIC_MAX_NODES = 128
 BCTS_FLAG_FRAMES = 1
 BCTS_FLAG_EXACT_GEV = 2
@@ -78,6 +79,8 @@ lib.bcts_tree_nodes.restype = ctypes.c_int64
 lib.bcts_search_tree.argtypes = [_P, _P, _I, _P, _P, _P, _P, _P]
 lib.bcts_search_pruned.argtypes = [_P, _P, _I, _I, _P, _P]
 lib.bcts_search_pruned.restype = _I
+lib.bcts_search_pruned_device.argtypes = [_P, _P, _I, _I, _P, _P, _P]
+lib.bcts_search_pruned_device.restype = _I
 lib.bcts_dnn_numel.argtypes = [_I]
 lib.bcts_dnn_numel.restype = ctypes.c_size_t
 lib.bcts_dnn_create.argtypes = [_P, _I, _I, ctypes.c_float, ctypes.c_float, _I, ctypes.POINTER(_P)]
@@ -367,3 +370,8 @@ def bcts_search_pruned(ctx: Context, roots, keep: int):
     val = np.zeros((n, ctx.A), dtype=np.float32)
     _check(lib.bcts_search_pruned(ctx.handle, r.ctypes.data, n, int(keep), act.ctypes.data, val.ctypes.data), ctx)
     return act, val
+
+
+def bcts_search_pruned_device(ctx: Context, d_roots, n: int, keep: int, d_action, d_values, stream=None) -> int:
+    return _check(lib.bcts_search_pruned_device(ctx.handle, _addr(d_roots), n, int(keep), _addr(d_action),
+                                                _addr(d_values), _stream(stream)), ctx)

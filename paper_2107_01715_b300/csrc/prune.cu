@@ -132,6 +132,20 @@ int Ctx::run_search_pruned(const bcts_state *d_roots, int n, int keep, int32_t *
 
 }  // namespace bcts
 
+extern "C" int bcts_search_pruned_device(bcts_ctx *ctx, const bcts_state *d_roots, int n, int keep, int32_t *d_action,
+                                         float *d_values, void *stream) {
+  if (!ctx) return BCTS_EINVAL;
+  bcts::Ctx *c = reinterpret_cast<bcts::Ctx *>(ctx);
+  if (n < 0 || keep < 1 || keep > 256 || (n > 0 && (!d_roots || !d_action || !d_values)))
+    return c->fail(BCTS_EINVAL, "bcts_search_pruned_device: invalid argument");
+  if (n == 0) return BCTS_OK;
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  c->prune_keep = keep;
+  const int rc = c->run_search(d_roots, n, c->A_create, c->d, d_action, d_values, c->A_create, st);
+  c->prune_keep = 0;
+  return rc;
+}
+
 extern "C" int bcts_search_pruned(bcts_ctx *ctx, const bcts_state *roots, int n, int keep, int32_t *out_action,
                                   float *out_values) {
   if (!ctx) return BCTS_EINVAL;
