@@ -447,10 +447,17 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       // The fetch is issued after the tile's proxy fence so the fence never waits
       // for it.
       const uint32_t ring = smem_u32(dirty + 8 * kProd);
-      auto prefetch_states = [&](int t, int slot) {
+      // The leaf variant (one K block per tile, contiguous tiles) renders two
+      // consecutive tiles per round: 256 rows still touch at most two nodes, so
+      // the same candidates cover both, and the round's barriers, fence and
+      // arrivals are paid once for two tiles.
+      constexpr int TPR = (V == 2 && C::CONTIG) ? 2 : 1;  // tiles per producer round
+      static_assert(TPR == 1 || (C::RING >= 4 && C::RING % 2 == 0), "two tiles per round need a ring of >= 4");
+      auto prefetch_states = [&](int t, int slot) {  // t: the round's first tile
         if (pt < 10) {
           const uint32_t m0 = uint32_t(t) * 128u;
-          const uint32_t mlast = (m0 + 127u < p.M - 1u) ? m0 + 127u : p.M - 1u;
+          const uint32_t span = 128u * TPR - 1u;
+          const uint32_t mlast = (m0 + span < p.M - 1u) ? m0 + span : p.M - 1u;
           const uint32_t leaf0 = m0 / uint32_t(kP1), leaf_last = mlast / uint32_t(kP1);
           const uint32_t l = (leaf0 + uint32_t(pt / 5) <= leaf_last) ? leaf0 + uint32_t(pt / 5) : leaf_last;
           cp_async16(ring + uint32_t(slot * 160 + pt * 16),
@@ -460,35 +467,39 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       };
       if (T0 < TE) prefetch_states(T0, 0);
       else cp_commit();
-      if (T0 + TS < TE) prefetch_states(T0 + TS, 1);
+      if (T0 + TPR * TS < TE) prefetch_states(T0 + TPR * TS, 1);
       else cp_commit();
-      int c = 0;
-      for (int t = T0; t < TE; t += TS, ++c) {
-        const int g = c * KB;
+      int c = 0, rd = 0;  // tiles and rounds so far
+      for (int t = T0; t < TE; t += TPR * TS, c += TPR, ++rd) {
+        const int nt = (TPR == 2 && t + TS < TE) ? 2 : 1;  // tiles in this round
         {
           // the MMA thread commits once per tile, to the tile's last stage: its
-          // completion frees all KB stages
-          const int s = (g + KB - 1) % S;
-          const uint32_t round = uint32_t((g + KB - 1) / S);
+          // completion frees all KB stages (and those of every earlier tile)
+          const int gl = (c + nt - 1) * KB + KB - 1;
+          const int s = gl % S;
+          const uint32_t round = uint32_t(gl / S);
           wait_bar(empty_bar(s), (round & 1u) ^ 1u, abort_flag, p.d_err, 1);
         }
         named_bar_sync(1, kProd);  // every producer decides together
         if (*abort_flag) break;
-        cp_wait<1>();  // this tile's node states (the next tile's may still be in flight)
-        uint32_t *dj = dirty + (c % C::RING) * (KB * kProd);
+        cp_wait<1>();  // this round's node states (the next round's may still be in flight)
+        for (int tt = 0; tt < nt; ++tt) {
+          const uint32_t *dj = dirty + ((c + tt) % C::RING) * (KB * kProd);
 #pragma unroll
-        for (int j = 0; j < KB; ++j) {
-          const uint32_t a = dj[j * kProd + pt];
-          if (a) st_shared16(a, make_uint4(0u, 0u, 0u, 0u));
+          for (int j = 0; j < KB; ++j) {
+            const uint32_t a = dj[j * kProd + pt];
+            if (a) st_shared16(a, make_uint4(0u, 0u, 0u, 0u));
+          }
         }
         named_bar_sync(1, kProd);  // states visible, re-zeroing done
         uint4 P[4];
         const uint4 *Ps = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(dirty + 8 * kProd) +
-                                                          (c % 3) * 160 + li * 80);
+                                                          (rd % 3) * 160 + li * 80);
 #pragma unroll
         for (int j = 0; j < 4; ++j) P[j] = Ps[j];
         const uint32_t m0 = uint32_t(t) * 128u;
-        const uint32_t mlast = (m0 + 127u < p.M - 1u) ? m0 + 127u : p.M - 1u;
+        const uint32_t span = 128u * uint32_t(nt) - 1u;
+        const uint32_t mlast = (m0 + span < p.M - 1u) ? m0 + span : p.M - 1u;
         const uint32_t leaf0 = m0 / uint32_t(kP1), leaf_last = mlast / uint32_t(kP1);
         // bf16: K block j = history slot j, chunk cc = kernel row cc (8 pixels);
         // E4M3: K block j = slots 2j, 2j+1, chunk cc = slot 2j + cc/4, kernel rows
@@ -496,6 +507,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
 #pragma unroll
         for (int j = 0; j < KB; ++j) {
           uint32_t wrote = 0u;
+          int wt = 0;  // the round's tile the candidate row falls in
           const uint32_t leaf = leaf0 + uint32_t(li);
           const int slot = FP8 ? C::SLOT0 + 2 * j + (cc >> 2) : C::SLOT0 + j;
           // E4M3 partial-map variants leave the halves their MMAs skip unrendered
@@ -519,16 +531,20 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
               const int y = 4 * oy + cc;
               v = pixels8_to_bf16(render_word(oxs, oys, ox, y), render_word(oxs, oys, ox + 1, y));
             }
-            wrote = sA_of((g + j) % S) + sw128_off(int(m - m0), cc);
+            const uint32_t off = m - m0;
+            wt = int(off >> 7);
+            wrote = sA_of(((c + wt) * KB + j) % S) + sw128_off(int(off & 127u), cc);
             st_shared16(wrote, v);
           }
-          dj[j * kProd + pt] = wrote;
+          for (int tt = 0; tt < nt; ++tt)
+            dirty[((c + tt) % C::RING) * (KB * kProd) + j * kProd + pt] = tt == wt ? wrote : 0u;
         }
         fence_proxy_async();
+        for (int tt = 0; tt < nt; ++tt)
 #pragma unroll
-        for (int kb = 0; kb < KB; ++kb) mbar_arrive(full_bar((g + kb) % S));
-        const int t2 = t + 2 * TS;
-        if (t2 < TE) prefetch_states(t2, (c + 2) % 3);
+          for (int kb = 0; kb < KB; ++kb) mbar_arrive(full_bar(((c + tt) * KB + kb) % S));
+        const int t2 = t + 2 * TPR * TS;
+        if (t2 < TE) prefetch_states(t2, (rd + 2) % 3);
         else cp_commit();
       }
       asm volatile("cp.async.wait_all;" ::: "memory");
