@@ -65,9 +65,9 @@ EXEC_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 400 * 32 * 192, "conv1_le
 # DRAM bytes per node of each tensor-core kernel class, read + write, from the ncu captures
 # of the current kernels summarised in profiles/tc_gemm_layers_4roots_a18_d3.md (launches
 # over 23,328 leaves; traffic grows in proportion to the nodes a launch processes).
-TRAFFIC_PER_NODE = {"fp32/conv1_leaf": 51538.5, "fp32/conv2": 70863.0,
-                    "bf16/conv1_leaf": 25957.4, "bf16/conv2": 34907.3,
-                    "fp8/conv1": 10289.1, "fp8/conv2": 16963.0, "fp8/conv3": 7030.6, "fp8/fc1": 3549.4}
+TRAFFIC_PER_NODE = {"fp32/conv1_leaf": 51959.0, "fp32/conv2": 70891.0,
+                    "bf16/conv1_leaf": 26356.0, "bf16/conv2": 34932.0,
+                    "fp8/conv1_leaf": 13621.0, "fp8/conv2": 16968.0}
 
 
 def layer_model(cls, precision, A):

@@ -447,12 +447,12 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       // The fetch is issued after the tile's proxy fence so the fence never waits
       // for it.
       const uint32_t ring = smem_u32(dirty + 8 * kProd);
-      // The leaf variant (one K block per tile, contiguous tiles) renders two
-      // consecutive tiles per round: 256 rows still touch at most two nodes, so
-      // the same candidates cover both, and the round's barriers, fence and
-      // arrivals are paid once for two tiles.
-      constexpr int TPR = (V == 2 && C::CONTIG) ? 2 : 1;  // tiles per producer round
-      static_assert(TPR == 1 || (C::RING >= 4 && C::RING % 2 == 0), "two tiles per round need a ring of >= 4");
+      // The leaf variant (one K block per tile, contiguous tiles) renders three
+      // consecutive tiles per round: 384 rows still touch at most two nodes, so
+      // the same candidates cover all three, and the round's barriers, fence and
+      // arrivals are paid once for three tiles.
+      constexpr int TPR = (V == 2 && C::CONTIG) ? 3 : 1;  // tiles per producer round
+      static_assert(TPR == 1 || C::RING >= 2 * TPR, "a round's tiles need a ring of at least two rounds");
       auto prefetch_states = [&](int t, int slot) {  // t: the round's first tile
         if (pt < 10) {
           const uint32_t m0 = uint32_t(t) * 128u;
@@ -471,7 +471,8 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       else cp_commit();
       int c = 0, rd = 0;  // tiles and rounds so far
       for (int t = T0; t < TE; t += TPR * TS, c += TPR, ++rd) {
-        const int nt = (TPR == 2 && t + TS < TE) ? 2 : 1;  // tiles in this round
+        const int left = (TE - t + TS - 1) / TS;
+        const int nt = left < TPR ? left : TPR;  // tiles in this round
         {
           // the MMA thread commits once per tile, to the tile's last stage: its
           // completion frees all KB stages (and those of every earlier tile)
