@@ -44,6 +44,7 @@ void tc_weights_destroy(TcWeights *w);
 struct ZLeaf {
   const float *zmap;
   uint32_t leaf0, branch;
+  const uint32_t *parent = nullptr;  // if set: parent of leaf i = parent[leaf0 + i] (mixed branching)
 };
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
                     float *maxq, void *scratch, cudaStream_t stream, int *d_err, const uint8_t *node_A = nullptr,

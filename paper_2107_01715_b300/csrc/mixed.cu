@@ -32,6 +32,7 @@ struct MixedGroup {
   int64_t leaf_off = 0;   // first leaf in the union leaf buffer (d >= 2)
   int64_t nleaf = 0;      // n * A^d for d >= 2
   int64_t mid_max = 0;    // largest intermediate level (depths 2 .. d-1)
+  int64_t zoff = 0;       // first of its leaves' parents in the union partial-map buffer (d >= 2)
 };
 
 struct MixedPlan {
@@ -39,8 +40,14 @@ struct MixedPlan {
   std::vector<int> order;  // sorted position -> caller's root index
   std::vector<MixedGroup> groups;
   int64_t n1 = 0, nleaf = 0, mid = 0;
+  int64_t nz = 0;       // leaves' parents of all groups (one partial conv1 map each)
+  bool use_z = false;   // leaves' conv1 from the parents' partial maps
   std::string key;
 };
+
+// The union partial maps take 51.2 KB per parent; above this the batched form
+// scores its leaves with whole-stack conv1 instead.
+constexpr size_t kMaxZBytes = size_t(16) << 30;
 
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
@@ -55,7 +62,8 @@ constexpr size_t kMaxGraphs = 64;
 constexpr size_t kMaxSeen = 4096;
 
 struct MixedState {
-  DevBuf roots, q0, L1, r1, maxq1, nodeA1, mid[2], Rmid[2], leaves, Rleaf, maxq_leaf, nodeA_leaf, V, act, val;
+  DevBuf roots, q0, L1, r1, maxq1, nodeA1, mid[2], Rmid[2], leaves, Rleaf, maxq_leaf, nodeA_leaf, V, act, val, zbuf,
+      zparent;
   HostBuf host;
   std::map<std::string, int> seen;
   std::map<std::string, GraphEntry> graphs;
@@ -66,7 +74,7 @@ struct MixedState {
     for (auto &kv : graphs)
       if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     DevBuf *b[] = {&roots, &q0, &L1, &r1, &maxq1, &nodeA1, &mid[0], &mid[1], &Rmid[0], &Rmid[1],
-                   &leaves, &Rleaf, &maxq_leaf, &nodeA_leaf, &V, &act, &val};
+                   &leaves, &Rleaf, &maxq_leaf, &nodeA_leaf, &V, &act, &val, &zbuf, &zparent};
     for (DevBuf *x : b)
       if (x->p) cudaFree(x->p);
     if (host.p) cudaFreeHost(host.p);
@@ -120,6 +128,8 @@ static int mixed_ensure(Ctx *c, MixedState *m, const MixedPlan &pl) {
       {&m->V, size_t(pl.n) * As * 4},
       {&m->act, size_t(pl.n) * 4},
       {&m->val, size_t(pl.n) * As * 4},
+      {&m->zbuf, pl.use_z ? size_t(pl.nz) * kP1 * kC1 * 4 : 1},
+      {&m->zparent, pl.use_z ? size_t(std::max<int64_t>(pl.nleaf, 1)) * 4 : 1},
   };
   for (auto &x : need) {
     const int rc = c->ensure(*x.b, x.bytes);  // bumps the context's buffer generation when it moves
@@ -132,6 +142,12 @@ static int mixed_ensure(Ctx *c, MixedState *m, const MixedPlan &pl) {
     c->buf_generation++;
   }
   return BCTS_OK;
+}
+
+// Parent (in the union partial-map buffer) of each of a group's leaves.
+__global__ void zparent_fill_kernel(uint32_t *__restrict__ zp, int64_t n, int A, uint32_t zoff) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) zp[i] = zoff + uint32_t(i / A);
 }
 
 // Every device step of one pass, in stream order (capturable: no allocation,
@@ -171,6 +187,19 @@ static int mixed_enqueue(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_
     for (int i = 1; i < g.d; ++i) {
       gp *= double(c->gamma);
       const bool last = i == g.d - 1;
+      if (last && pl.use_z) {
+        // the leaves' parents: their partial conv1 maps, and each leaf's parent index
+        float *z = static_cast<float *>(m->zbuf.p) + size_t(g.zoff) * kP1 * kC1;
+        const int64_t chunk = c->chunk_nodes();
+        for (int64_t off = 0; off < cnt; off += chunk) {
+          const int64_t k = cnt - off < chunk ? cnt - off : chunk;
+          if ((rc = tc_conv1_partial(c->tc, cur + off, k, z + size_t(off) * kP1 * kC1, st, c->d_err)) != BCTS_OK)
+            return c->fail(rc, "conv1 partial launch failed");
+        }
+        zparent_fill_kernel<<<unsigned((g.nleaf + 255) / 256), 256, 0, st>>>(
+            static_cast<uint32_t *>(m->zparent.p) + g.leaf_off, g.nleaf, g.A, uint32_t(g.zoff));
+        if (cudaGetLastError() != cudaSuccess) return c->fail(BCTS_ECUDA, "parent table launch failed");
+      }
       bcts_state *nxt = last ? leaves + g.leaf_off : static_cast<bcts_state *>(m->mid[i & 1].p);
       float *nxtR = last ? Rleaf + g.leaf_off : static_cast<float *>(m->Rmid[i & 1].p);
       if ((rc = launch_expand(cur, curR, cnt, g.A, float(gp), nxt, nxtR, nullptr, st)) != BCTS_OK)
@@ -182,7 +211,11 @@ static int mixed_enqueue(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_
     BCTS_CUDA_TRY(cudaMemsetAsync(nAl + g.leaf_off, g.A, size_t(g.nleaf), st), c->err);
   }
   float *maxq_leaf = static_cast<float *>(m->maxq_leaf.p);
-  if (pl.nleaf > 0 && (rc = c->eval_nodes(leaves, pl.nleaf, nullptr, maxq_leaf, st, nAl)) != BCTS_OK) return rc;
+  if (pl.nleaf > 0 &&
+      (rc = c->eval_nodes(leaves, pl.nleaf, nullptr, maxq_leaf, st, nAl,
+                          pl.use_z ? static_cast<const float *>(m->zbuf.p) : nullptr, 0,
+                          pl.use_z ? static_cast<const uint32_t *>(m->zparent.p) : nullptr)) != BCTS_OK)
+    return rc;
   // backup per group
   float *V = static_cast<float *>(m->V.p);
   int32_t *act = static_cast<int32_t *>(m->act.p);
@@ -312,6 +345,8 @@ int Ctx::run_mixed(const bcts_state *, const bcts_state *h_roots, const int32_t 
       g.nleaf = int64_t(g.n) * ipow(g.A, g.d);
       g.leaf_off = pl.nleaf;
       pl.nleaf += g.nleaf;
+      g.zoff = pl.nz;
+      pl.nz += int64_t(g.n) * ipow(g.A, g.d - 1);
       if (g.d >= 3) pl.mid = std::max<int64_t>(pl.mid, int64_t(g.n) * ipow(g.A, g.d - 1));
     }
     if (pl.nleaf > 0x7FFFFFFFLL) return fail(BCTS_EINVAL, "batched search too large: more than 2^31 - 1 leaves");
@@ -321,6 +356,8 @@ int Ctx::run_mixed(const bcts_state *, const bcts_state *h_roots, const int32_t 
   }
   key << "p" << precision;
   pl.key = key.str();
+  pl.use_z = tc && tc_fused_render && tc_has_partial(tc) && pl.nleaf > 0 &&
+             size_t(pl.nz) * kP1 * kC1 * sizeof(float) <= kMaxZBytes;
   int rc;
   if ((rc = mixed_ensure(this, m, pl)) != BCTS_OK) return rc;
   char *hs = static_cast<char *>(m->host.p);

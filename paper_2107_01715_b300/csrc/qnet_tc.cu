@@ -329,6 +329,7 @@ struct GemmParams {
   const float *zmap;      // conv1 leaf variant: parent partial maps [parent][400][32] FP32
   uint32_t z_leaf0;       // global index (within the level) of this launch's first leaf
   uint32_t z_branch;      // A: parent of leaf i = (z_leaf0 + i) / A
+  const uint32_t *z_parent;  // or, when set, parent of leaf i = z_parent[z_leaf0 + i]
   void *out_hi;  // bf16 NHWC (layers 1-3) or FP32 [M][512] (layer 4)
   void *out_lo;  // bf16 remainders (split mode, layers 1-3)
   uint32_t M;  // rows, < 2^31 (checked by the launcher)
@@ -778,8 +779,16 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
         const uint32_t mw0 = uint32_t(t / NT) * 128u + uint32_t(q * 32);
         const uint32_t mwc = mw0 < p.M ? mw0 : p.M - 1u;  // a warp past the end reads row M - 1
         const uint32_t leafA = mwc / uint32_t(kP1), pxA = mwc - leafA * uint32_t(kP1);
-        const uint32_t gA = p.z_leaf0 + leafA, parA = gA / p.z_branch;
-        const uint32_t parB = parA + ((gA - parA * p.z_branch + 1u == p.z_branch) ? 1u : 0u);
+        const uint32_t gA = p.z_leaf0 + leafA;
+        uint32_t parA, parB;
+        if (p.z_parent) {  // groups of different branching (batched form): per-leaf table
+          const uint32_t lastLeaf = (p.M - 1u) / uint32_t(kP1);
+          parA = __ldg(p.z_parent + gA);
+          parB = __ldg(p.z_parent + p.z_leaf0 + (leafA + 1u <= lastLeaf ? leafA + 1u : lastLeaf));
+        } else {
+          parA = gA / p.z_branch;
+          parB = parA + ((gA - parA * p.z_branch + 1u == p.z_branch) ? 1u : 0u);
+        }
         const float *zA = p.zmap + size_t(parA) * (kP1 * kC1);
         const float *zB = p.zmap + size_t(parB) * (kP1 * kC1);
 #pragma unroll
@@ -1167,6 +1176,7 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
     p.zmap = zl->zmap;
     p.z_leaf0 = zl->leaf0;
     p.z_branch = zl->branch;
+    p.z_parent = zl->parent;
     rc = tc::launch<1, MODE, true, 2>(p, (long long)n * kP1, K_CONV1_LEAF, st);
   } else {
     rc = states ? tc::launch<1, MODE, true>(p, (long long)n * kP1, K_CONV1, st)

@@ -223,12 +223,12 @@ int64_t Ctx::chunk_nodes() const {
 // Score `count` nodes: render + Q-network, chunked.  q (count x A) and maxq
 // (count) may each be NULL.
 int Ctx::eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st,
-                    const uint8_t *node_A, const float *zmap, uint32_t zbranch) {
+                    const uint8_t *node_A, const float *zmap, uint32_t zbranch, const uint32_t *zparent) {
   const int64_t chunk = chunk_nodes();
   int rc;
   for (int64_t off = 0; off < count; off += chunk) {
     const int64_t cnt = count - off < chunk ? count - off : chunk;
-    const ZLeaf zl{zmap, uint32_t(off), zbranch};
+    const ZLeaf zl{zmap, uint32_t(off), zbranch, zparent};
     if ((rc = qnet_nodes(states + off, nullptr, cnt, q ? q + off * A : nullptr, maxq ? maxq + off : nullptr, st,
                          node_A ? node_A + off : nullptr, zmap ? &zl : nullptr)) != BCTS_OK)
       return rc;

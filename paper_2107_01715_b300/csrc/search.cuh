@@ -61,7 +61,8 @@ struct Ctx {
   int ensure_host(HostBuf &b, size_t bytes);
   int64_t chunk_nodes() const;
   int eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st,
-                 const uint8_t *node_A = nullptr, const float *zmap = nullptr, uint32_t zbranch = 0);
+                 const uint8_t *node_A = nullptr, const float *zmap = nullptr, uint32_t zbranch = 0,
+                 const uint32_t *zparent = nullptr);
   int qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
                  cudaStream_t st, const uint8_t *node_A = nullptr, const ZLeaf *zl = nullptr);
   int export_tree(const std::vector<int64_t> &N, int A_, int d_, const float *leafMax, cudaStream_t st);
