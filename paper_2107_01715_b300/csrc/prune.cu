@@ -97,12 +97,29 @@ int Ctx::run_search_pruned(const bcts_state *d_roots, int n, int keep, int32_t *
   const float *curR = r1;
   int64_t S = 1;  // survivors per group
   double gprev = double(gamma);
+  // candidates are survivor-index x A + a, so their conv1 can come from the
+  // survivors' partial maps (frame stacking), as for the full search's leaves
+  const bool use_z = tc && tc_fused_render && tc_has_partial(tc) &&
+                     size_t(G) * std::max<int64_t>(1, std::min<int64_t>(keep, cmax)) * kP1 * kC1 * 4 <=
+                         (size_t(8) << 30);
   for (int i = 2; i <= d_; ++i) {
     const double gi = gprev * double(gamma);
     const int64_t C = S * A_;
+    const float *zmap = nullptr;
+    if (use_z) {
+      if ((rc = ensure(z_buf, size_t(G * S) * kP1 * kC1 * 4)) != BCTS_OK) return rc;
+      const int64_t chunk = chunk_nodes();
+      for (int64_t off = 0; off < G * S; off += chunk) {
+        const int64_t k = G * S - off < chunk ? G * S - off : chunk;
+        if ((rc = tc_conv1_partial(tc, par + off, k, static_cast<float *>(z_buf.p) + size_t(off) * kP1 * kC1, st,
+                                   d_err)) != BCTS_OK)
+          return fail(rc, "conv1 partial launch failed");
+      }
+      zmap = static_cast<const float *>(z_buf.p);
+    }
     if ((rc = launch_expand(par, curR, G * S, A_, float(gprev), cand, candR, nullptr, st)) != BCTS_OK)
       return fail(rc, "expand launch failed");
-    if ((rc = eval_nodes(cand, G * C, nullptr, candQ, st)) != BCTS_OK) return rc;
+    if ((rc = eval_nodes(cand, G * C, nullptr, candQ, st, nullptr, zmap, uint32_t(A_))) != BCTS_OK) return rc;
     if (i == d_) {
       // V(a_0): the maximum of R + gamma^d max Q over the group's leaves
       if ((rc = launch_segment_max(candR, candQ, G, C, float(gi), V, st)) != BCTS_OK)
