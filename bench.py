@@ -46,6 +46,9 @@ WORKLOADS = {
                       name="precision form: 8 roots, |A|=18, d=4, leaf Q-net in reduced precision"),
     "batched": dict(n=256, A=18, d=4, gamma=0.99, c=1.0, precision="bf16",
                     name="batched form: 256 roots, d uniform in {1,2,3,4}, |A| in {4,9,18}, BF16, graph-replayed"),
+    "sweep": dict(n=1, A=18, d=0, gamma=0.99, c=1.0, precision="fp32",
+                  name="time per tree-search operation vs depth (one root per search), as in Sec. 4's runtime "
+                       "experiment: sprite world A=18 d=1..5, DNN forward model A=2 d=2..16 and A=10 d=1..6"),
     "pruned": dict(n=32, A=18, d=4, keep=32, gamma=0.99, c=1.0, precision="fp32",
                    name="pruned search: 32 roots, |A|=18, d=4, 32 nodes kept per root action and level, FP32"),
     "dnn": dict(n=16, A=10, d=5, gamma=0.99, c=1.0, precision="fp32",
@@ -443,6 +446,76 @@ def run_pruned(args, wl):
     ctx.close()
 
 
+def run_sweep(args, wl):
+    """Device time of one decision (one root, whole Batch-BFS search) per depth, for the
+    sprite world (FP32-class) and the DNN forward model (FP32), with the FP64 oracle's
+    depth-first search on the host cores where it finishes in seconds."""
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2107_01715_b300 import bcts
+    import oracle
+    oracle.build()
+    stream = torch.cuda.Stream(device=dev)
+    reps = max(args.steps, 3)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                fn()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rows = []
+    A = 18
+    W = inputs.qnet_weights(A, seed=1234)
+    roots = inputs.root_states([0])
+    d_roots = torch.from_numpy(roots.view(np.uint8).copy()).to(dev)
+    d_act = torch.empty(1, dtype=torch.int32, device=dev)
+    d_val = torch.empty(64, dtype=torch.float32, device=dev)
+    for d in range(1, 6):
+        ctx = bcts.bcts_create(W, A, d, 0.99, 1.0, precision="fp32")
+        ms = timed(lambda: bcts.bcts_search_device(ctx, d_roots, 1, d_act, d_val, stream))
+        ctx.close()
+        cpu = None
+        if d <= 3:
+            t0 = time.perf_counter()
+            oracle.search(roots, W, A, d, float(np.float32(0.99)), 1.0)
+            cpu = 1e3 * (time.perf_counter() - t0)
+        rows.append({"env": "sprite", "A": A, "d": d, "leaves": A ** d, "gpu_ms": ms, "oracle_dfs_ms": cpu})
+    for A, depths in ((2, range(2, 17, 2)), (10, range(1, 7))):
+        Wd = inputs.dnn_weights(A)
+        r = inputs.dnn_root_states([0])
+        d_r = torch.from_numpy(r).to(dev)
+        for d in depths:
+            ctx = bcts.bcts_dnn_create(Wd, A, d, 0.99, 1.0)
+            ms = timed(lambda: bcts.bcts_dnn_search_device(ctx, d_r, 1, d_act, d_val, stream))
+            ctx.close()
+            cpu = None
+            if A ** d <= 20000:
+                t0 = time.perf_counter()
+                oracle.dnn_search(r, Wd, A, d, float(np.float32(0.99)), 1.0)
+                cpu = 1e3 * (time.perf_counter() - t0)
+            rows.append({"env": "dnn", "A": A, "d": d, "leaves": A ** d, "gpu_ms": ms, "oracle_dfs_ms": cpu})
+    if rank != 0:
+        return
+    big = rows[4]  # sprite world, d = 5: the largest single-root search of the sweep
+    line = {"metric": METRIC, "value": big["leaves"] / (big["gpu_ms"] / 1e3), "unit": "leaf nodes/s",
+            "n_gpus": world, "steps": reps, "warmup": 2, "ms_per_step": big["gpu_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES["fp32"], "data": "synthetic",
+            "config": {"workload": wl["name"], "value_is": "sprite world, A=18, d=5, one root"},
+            "sweep": rows, "cpu_baseline": {"kind": "oracle", "cores": oracle.threads(),
+                                            "sample": "the oracle's DFS per depth where it finishes in seconds"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, wl):
     world, rank, _ = dist_setup(args.gpus)
     if rank != 0:
@@ -796,6 +869,8 @@ def main():
         run_dnn(args, wl)
     elif args.workload == "pruned":
         run_pruned(args, wl)
+    elif args.workload == "sweep":
+        run_sweep(args, wl)
     else:
         run_ours(args, wl)
 
