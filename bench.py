@@ -778,6 +778,7 @@ def run_serving(args, wl):
         tks = [bcts.bcts_submit(ctx, episodes[i:i + 1], (2, 3, 4)[i % 3], A) for i in range(256)]
         for t in tks:
             bcts.bcts_poll(ctx, t, A, timeout_us=-1)
+    bcts.bcts_profile(ctx, False)  # reset the launch counters (owner and serving workers)
     busy = set()
     pending = {}  # ticket -> (episode, submit time)
     lat, done_leaves, completed = [], 0, 0
@@ -820,6 +821,7 @@ def run_serving(args, wl):
                 break
             time.sleep(0.0002)
         wall = time.perf_counter() - t0
+    _, _, served_launches = bcts.bcts_profile(ctx, False)
     # plain FP32 sequential baseline on a bounded sample of the same kind of requests
     pctx = bcts.bcts_create(W, A, 4, wl["gamma"], wl["c"], precision="fp32_simt")
     seq_roots = inputs.root_states(range(20000, 20012))
@@ -848,7 +850,7 @@ def run_serving(args, wl):
                                           "how": "one request at a time, FP32 CUDA-core Q-network, d cycling 2,3,4"},
                 "e2e": {"value": completed / wall, "unit": "decisions/s", "h2d_bytes_per_step": 80,
                         "d2h_bytes_per_step": 4 + A * 4},
-                "gpu_launches": None, "clocks": _clock_line(clk, pk)}
+                "gpu_launches": served_launches, "clocks": _clock_line(clk, pk)}
         print(json.dumps(line), flush=True)
     ctx.close()
 

@@ -272,8 +272,10 @@ enum {
  * 0 stops.  On each call the totals since the previous call are returned and
  * reset: out_ms[BCTS_KERN_COUNT] milliseconds and out_launches[BCTS_KERN_COUNT]
  * launches per class (either may be NULL); *out_total_launches (may be NULL)
- * counts every kernel launch of the context, recorded or not.  Synchronises
- * the context's pending work.  Not for use while a search runs on another thread.
+ * counts every kernel launch of the context, recorded or not, including those
+ * of its serving workers (bcts_submit).  Synchronises the context's pending
+ * work.  Not for use while a search runs on another thread or served requests
+ * are in flight.
  */
 BCTS_API int bcts_profile(bcts_ctx *ctx, int enable, double *out_ms, int64_t *out_launches,
                           int64_t *out_total_launches);

@@ -108,6 +108,8 @@ extern "C" int bcts_profile(bcts_ctx *ctx, int enable, double *out_ms, int64_t *
                             int64_t *out_total) {
   if (!ctx) return BCTS_EINVAL;
   bcts::Ctx *c = reinterpret_cast<bcts::Ctx *>(ctx);
-  return bcts::profiler_read(c->prof, c->stream, enable, out_ms, out_launches, out_total);
+  const int rc = bcts::profiler_read(c->prof, c->stream, enable, out_ms, out_launches, out_total);
+  if (out_total) *out_total += bcts::serve_launches(c);  // the serving workers' launches too
+  return rc;
 }
 

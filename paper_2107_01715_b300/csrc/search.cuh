@@ -78,6 +78,7 @@ struct Ctx {
 };
 
 void serve_shutdown(Ctx *c);
+int64_t serve_launches(Ctx *c);
 Profiler *profiler_create();
 void profiler_destroy(Profiler *p);
 int64_t profiler_total(const Profiler *p);

@@ -168,6 +168,20 @@ void worker_loop(ServeState *s, int w) {
 
 }  // namespace
 
+// Kernel launches of the serving workers since the last call (their counters reset).
+int64_t serve_launches(Ctx *c) {
+  ServeState *s = c->serve;
+  if (!s) return 0;
+  int64_t total = 0;
+  for (Ctx *w : s->wctx) {
+    if (!w || !w->prof) continue;
+    int64_t t = 0;
+    profiler_read(w->prof, w->stream, 0, nullptr, nullptr, &t);
+    total += t;
+  }
+  return total;
+}
+
 void serve_shutdown(Ctx *c) {
   ServeState *s = c->serve;
   if (!s) return;

@@ -252,3 +252,35 @@ def test_tree_export_matches_oracle(oracle_lib, dev, precision, A, d, n, sample)
     v1 = R[:n * A] + g32 * V[:n * A]
     assert value_close(v1.reshape(n, A), ref["v_uncorrected"], tol).all()
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [p for p in PRECISIONS if p in ("fp32", "fp32_simt", "bf16")])
+@pytest.mark.parametrize("A,n", [(2, 3), (3, 2)])
+def test_maximum_depth_matches_oracle(oracle_lib, dev, precision, A, n):
+    """d = 6, the deepest search the library accepts, on branching small enough for
+    the oracle's exhaustive DFS (3^6 = 729 leaves)."""
+    torch, bcts = dev
+    d, gamma = 6, 0.99
+    ctx, W = _ctx(bcts, A, d, gamma, 1.0, precision)
+    roots = inputs.root_states(range(900, 900 + n))
+    act, val = bcts.bcts_search(ctx, roots)
+    ref = oracle_lib.search(roots, W, A, d, float(np.float32(gamma)), 1.0)
+    tol = TOL[precision]
+    strict = precision in ("fp32", "fp32_simt")
+    keep = [i for i in range(n) if strict or pi_o_decided(ref["q0"][i], tol)]
+    assert value_close(val[keep], ref["values"][keep], tol).all(), np.abs(val[keep] - ref["values"][keep]).max()
+    check_actions(act[keep], ref["values"][keep], tol)
+    ctx.close()
+
+
+def test_oversized_tree_rejected(dev):
+    """n * A^d above 2^31 - 1 nodes in one level is refused before any allocation."""
+    torch, bcts = dev
+    A = 18
+    ctx = bcts.bcts_create(inputs.qnet_weights(A), A, 6, 0.99, 1.0, precision="bf16")
+    with pytest.raises(bcts.BctsError) as e:
+        bcts.bcts_search(ctx, inputs.root_states(range(64)))  # 64 * 18^6 = 2.2e9 leaves
+    assert e.value.code == bcts.BCTS_EINVAL
+    act, val = bcts.bcts_search(ctx, inputs.root_states(range(0)))
+    assert act.size == 0
+    ctx.close()

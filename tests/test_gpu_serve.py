@@ -95,3 +95,20 @@ def test_ticket_errors(dev):
         bcts.bcts_poll(ctx, t, 6)
     assert e.value.code == bcts.BCTS_ENOTICKET
     ctx.close()
+
+
+def test_served_launches_are_counted(dev):
+    """bcts_profile's total includes the serving workers' kernel launches."""
+    torch, bcts = dev
+    A = 6
+    ctx = bcts.bcts_create(inputs.qnet_weights(A), A, 2, 0.99, 1.0, precision="bf16")
+    bcts.bcts_profile(ctx, False)
+    roots = inputs.root_states(range(4))
+    tickets = [bcts.bcts_submit(ctx, roots[i:i + 1], 2, A) for i in range(4)]
+    for t in tickets:
+        assert bcts.bcts_poll(ctx, t, A, timeout_us=-1)[0] == bcts.BCTS_OK
+    _, _, total = bcts.bcts_profile(ctx, False)
+    assert total > 0
+    _, _, again = bcts.bcts_profile(ctx, False)  # read and reset
+    assert again == 0
+    ctx.close()
