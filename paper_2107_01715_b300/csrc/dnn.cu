@@ -13,6 +13,7 @@
 // simulator, whose arithmetic the search must not change.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -214,11 +215,12 @@ __global__ void __launch_bounds__(256) dnn_q_kernel(const float *__restrict__ s,
 
 int sm_count() {
   static int sms = 0;
-  if (!sms) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
-  }
+  });
   return sms;
 }
 
@@ -277,11 +279,12 @@ struct DnnCtx {
             const DenseIO &io, cudaStream_t st) {
     if (M <= 0) return BCTS_OK;
     const size_t smem = size_t(K * kNC + 2 * kTileRows * kXS) * sizeof(float);
-    static bool attr_done = false;
-    if (!attr_done) {
-      cudaFuncSetAttribute(dense_kernel<IN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      attr_done = true;
-    }
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [smem] {
+      attr_err = cudaFuncSetAttribute(dense_kernel<IN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    });
+    if (attr_err != cudaSuccess) return fail(BCTS_ECUDA, "DNN dense layer: shared-memory attribute refused");
     const int64_t tiles = (M + kTileRows - 1) / kTileRows;
     const unsigned grid = unsigned(tiles < int64_t(2) * sm_count() ? tiles : int64_t(2) * sm_count());
     ProfScope ps(K_DNN_MLP, st);

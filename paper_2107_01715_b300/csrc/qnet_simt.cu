@@ -8,6 +8,7 @@
 // are stored NHWC, so a GEMM row-major output is already the next layer's input.
 // FC2 and the max over actions (Alg. 1's leaf term max_a Q) run in one warp per node.
 #include <cstdio>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -231,11 +232,12 @@ int launch_fc2_max(const float *h, const float *W2, const float *b2, int A, int6
   if (n <= 0) return BCTS_OK;
   const int warps = 8;
   static int sms = 0;
-  if (!sms) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
-  }
+  });
   // persistent: four blocks per SM (36 KB of W2 each), never more blocks than node groups
   const int64_t groups = (n + warps - 1) / warps;
   const unsigned grid = unsigned(groups < int64_t(4) * sms ? groups : int64_t(4) * sms);
