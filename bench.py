@@ -480,16 +480,26 @@ def run_sweep(args, wl):
     d_roots = torch.from_numpy(roots.view(np.uint8).copy()).to(dev)
     d_act = torch.empty(1, dtype=torch.int32, device=dev)
     d_val = torch.empty(64, dtype=torch.float32, device=dev)
+    def host_ms(fn):
+        for _ in range(3):  # eager, captured, replayed
+            fn()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        return 1e3 * (time.perf_counter() - t0) / reps
+
     for d in range(1, 6):
         ctx = bcts.bcts_create(W, A, d, 0.99, 1.0, precision="fp32")
         ms = timed(lambda: bcts.bcts_search_device(ctx, d_roots, 1, d_act, d_val, stream))
+        hms = host_ms(lambda: bcts.bcts_search(ctx, roots))
         ctx.close()
         cpu = None
         if d <= 3:
             t0 = time.perf_counter()
             oracle.search(roots, W, A, d, float(np.float32(0.99)), 1.0)
             cpu = 1e3 * (time.perf_counter() - t0)
-        rows.append({"env": "sprite", "A": A, "d": d, "leaves": A ** d, "gpu_ms": ms, "oracle_dfs_ms": cpu})
+        rows.append({"env": "sprite", "A": A, "d": d, "leaves": A ** d, "gpu_ms": ms, "host_api_ms": hms,
+                     "oracle_dfs_ms": cpu})
     for A, depths in ((2, range(2, 17, 2)), (10, range(1, 7))):
         Wd = inputs.dnn_weights(A)
         r = inputs.dnn_root_states([0])

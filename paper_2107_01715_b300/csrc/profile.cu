@@ -79,6 +79,7 @@ void prof_end(int kind, cudaStream_t st) {
 }
 
 Profiler *profiler_create() { return new Profiler(); }
+bool profiler_on(const Profiler *p) { return p && p->on; }
 int64_t profiler_total(const Profiler *p) { return p->total; }
 void profiler_add(Profiler *p, int64_t launches) { p->total += launches; }
 void profiler_destroy(Profiler *p) { delete p; }

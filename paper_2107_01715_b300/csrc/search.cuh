@@ -1,6 +1,7 @@
 // search.cuh -- the search context shared by search.cu, mixed.cu and serve.cu.
 #pragma once
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -47,6 +48,15 @@ struct Ctx {
   DevBuf io_roots, io_action, io_values, mixed_buf, z_buf;
   DevBuf pr_cand, pr_candR, pr_candQ, pr_par, pr_parR, pr_idx;  // pruned search
   int prune_keep = 0;  // > 0: run_search keeps this many nodes per root action and level (d >= 3)
+  // host-API searches replayed from CUDA graphs, keyed by root count
+  struct SearchGraph {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t generation = 0;  // buffer generation the graph was captured with
+    int64_t launches = 0;     // kernel launches one replay makes
+    int calls = 0;
+    uint64_t last_generation = 0;  // generation after the previous eager call
+  };
+  std::map<int, SearchGraph> sgraphs;
   HostBuf host_stage;
 
   ServeState *serve = nullptr;
@@ -85,6 +95,7 @@ int64_t profiler_total(const Profiler *p);
 void profiler_add(Profiler *p, int64_t launches);
 int profiler_read(Profiler *p, cudaStream_t st, int enable, double *out_ms, int64_t *out_launches,
                   int64_t *out_total);
+bool profiler_on(const Profiler *p);
 void mixed_destroy(MixedState *m);
 
 }  // namespace bcts

@@ -284,3 +284,35 @@ def test_oversized_tree_rejected(dev):
     act, val = bcts.bcts_search(ctx, inputs.root_states(range(0)))
     assert act.size == 0
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [p for p in PRECISIONS if p in ("fp32", "bf16", "fp32_simt")])
+def test_graph_replayed_searches_are_identical(dev, precision):
+    """The host API captures a repeated root count into a CUDA graph on its second
+    call and replays it afterwards: every call gives the same bits, other root
+    counts in between still work, and replays count their launches."""
+    torch, bcts = dev
+    A, d = 9, 3
+    ctx, W = _ctx(bcts, A, d, 0.99, 1.0, precision)
+    roots = inputs.root_states(range(300, 305))
+    other = inputs.root_states(range(310, 313))
+    first = bcts.bcts_search(ctx, roots)
+    ref_other = bcts.bcts_search(ctx, other)
+    bcts.bcts_profile(ctx, False)
+    for i in range(4):  # eager, capture, replay, replay
+        act, val = bcts.bcts_search(ctx, roots)
+        np.testing.assert_array_equal(act, first[0])
+        np.testing.assert_array_equal(val, first[1])
+        _, _, launches = bcts.bcts_profile(ctx, False)
+        assert launches > 0
+        a2, v2 = bcts.bcts_search(ctx, other)
+        np.testing.assert_array_equal(v2, ref_other[1])
+    # other roots of the same count replay the same graph with new inputs
+    fresh = inputs.root_states(range(400, 405))
+    act, val = bcts.bcts_search(ctx, fresh)
+    ctx2, _ = _ctx(bcts, A, d, 0.99, 1.0, precision)
+    act2, val2 = bcts.bcts_search(ctx2, fresh)  # a fresh context's eager answer
+    np.testing.assert_array_equal(act, act2)
+    np.testing.assert_array_equal(val, val2)
+    ctx.close()
+    ctx2.close()
