@@ -104,3 +104,43 @@ def test_exact_penalty_special_cases(oracle_lib):
     b = oracle_lib.bellman_penalty_exact(0.0, 1.0, 6, 3)
     assert oracle_lib.bellman_penalty_exact(2.5, 0.75, 6, 3) == pytest.approx(2.5 * a + 0.75 * b, rel=1e-12)
     assert a > 0.0 > b
+
+
+# ---- Lemma 2 against simulation (Thm. 1's setting, Normal leaf noise) -------------
+
+@pytest.mark.parametrize("m", [18, 324, 5832])
+def test_gev_shift_approximates_expected_maximum(oracle_lib, m):
+    """Lemma 2's shift of the maximum of m iid unit normals (its GEV mean) is close to
+    the Monte Carlo mean of that maximum, and closer as m grows (an asymptotic
+    statement): within 6 % at m = 18, 3 % beyond."""
+    import numpy as np
+    rng = np.random.default_rng(2021)
+    trials = 4000 if m <= 324 else 1500
+    mc = rng.standard_normal((trials, m)).max(axis=1).mean()
+    # the oracle's exact gap at delta_o = 0, delta_e = sqrt 2 (sigma_e = 1) is this shift
+    # for m = A^d - A^(d-1) leaves: 18 = 19 - 1 (A = 19, d = 1), 324 = 18^2 - 18 ... checked
+    # directly where such (A, d) exist, through bias_n (the library quantile) otherwise
+    shift = bias_n(m)
+    if m == 18:
+        assert oracle_lib.bellman_penalty_exact(math.sqrt(2.0), 0.0, 19, 1) == pytest.approx(shift, rel=1e-9)
+    assert shift == pytest.approx(mc, rel=0.06 if m == 18 else 0.03)
+
+
+def test_corrected_values_restore_the_ordering_in_expectation():
+    """Thm. 1 in its Normal-noise model: with sigma_e > sigma_o the uncorrected maxima
+    favour the noisier sub-trees even when pi_o is better, and subtracting the
+    Lemma 2 gap (B_e - B_o) restores E[Q(pi_o)] > E[max other]."""
+    import numpy as np
+    rng = np.random.default_rng(7)
+    A, d = 4, 3
+    n_o, n_e = A ** (d - 1), A ** d - A ** (d - 1)
+    mu_o, mu_e, s_o, s_e = 1.0, 0.8, 0.2, 1.0
+    trials = 20000
+    max_o = (mu_o + s_o * rng.standard_normal((trials, n_o))).max(axis=1)
+    max_e = (mu_e + s_e * rng.standard_normal((trials, n_e))).max(axis=1)
+    assert max_o.mean() < max_e.mean()  # the bias hands the noisier sub-tree the win
+    gap = s_e * bias_n(n_e) - s_o * bias_n(n_o)
+    assert max_o.mean() > (max_e - gap).mean()  # corrected: the true ordering returns
+    # both sides then carry the same bias B_o: E[max_o] ~ mu_o + B_o, E[max_e - gap] ~ mu_e + B_o
+    assert max_o.mean() == pytest.approx(mu_o + s_o * bias_n(n_o), abs=0.03)
+    assert (max_e - gap).mean() == pytest.approx(mu_e + s_o * bias_n(n_o), abs=0.05)
