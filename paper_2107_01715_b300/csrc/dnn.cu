@@ -30,18 +30,21 @@ constexpr int kMaxDnnDepth = 16;
 constexpr int64_t kChunkRows = int64_t(1) << 21;  // children per forward-model pass
 
 // ---------------------------------------------------------------------------
-// out[m][n] = act(in[m][0..K) . W[n][0..K) + b[n]), m < M, n < N <= 128,
+// out[m][n] = act(in[m][0..K) . W[n][0..K) + b[n]), m < M, n < N <= 104,
 // K <= kXS and a multiple of 4 (rows of `in` are K floats, 16-byte aligned).
-// Persistent blocks: W transposed into shared memory once per block, [k][128]
-// (so lane l reads columns 4l..4l+3 of a k with one 16-byte load, conflict
-// free); then 64-row tiles of `in`, double-buffered with cp.async so the next
-// tile lands while this one is multiplied.  Warp w owns rows 8w..8w+7 (its
-// activations are broadcasts), lane l columns 4l..4l+3: 32 FMAs per three
-// 16-byte shared loads.
+// Persistent blocks: W transposed into shared memory once per block, [k][104];
+// then 64-row tiles of `in`, double-buffered with cp.async so the next tile
+// lands while this one is multiplied.  208 threads: thread (rg, cg) owns rows
+// rg + 8 i (i < 8) and columns 4 cg .. 4 cg + 3 (26 column groups cover the
+// 100 / 101 outputs of these layers with 4 % padding); a warp's threads share
+// at most two row groups one row apart (different banks) and read each k's
+// weights with one 16-byte load: 32 FMAs per three 16-byte shared loads.
 // ---------------------------------------------------------------------------
 constexpr int kTileRows = 64;
-constexpr int kNC = 128;  // output columns per tile (N padded)
-constexpr int kXS = 104;  // activation row stride in shared memory (floats, 16-byte multiple)
+constexpr int kCG = 26;             // column groups of 4
+constexpr int kNC = 4 * kCG;        // output columns per tile (N padded to 104)
+constexpr int kDenseThreads = 8 * kCG;
+constexpr int kXS = 108;  // activation row stride (floats): 16-byte multiple, consecutive rows 12 banks apart
 
 __device__ __forceinline__ void cp_async16_zfill(float *dst, const float *src, bool valid) {
   const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
@@ -63,13 +66,13 @@ enum { IN_ROWS = 0, IN_H1 = 1 };
 enum { EPI_LINEAR = 0, EPI_RELU = 1, EPI_STATE = 2 };
 
 template <int IN, int EPI>
-__global__ void __launch_bounds__(256) dense_kernel(const float *__restrict__ in, int64_t M, int K,
+__global__ void __launch_bounds__(kDenseThreads) dense_kernel(const float *__restrict__ in, int64_t M, int K,
                                                     const float *__restrict__ W, const float *__restrict__ b, int N,
                                                     float *__restrict__ out, int ldo, const DenseIO io) {
   extern __shared__ __align__(16) float sm[];
   float *Wt = sm;                     // [K][kNC]
   float *Xs = sm + K * kNC;           // [2][kTileRows][kXS]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rg = threadIdx.x / kCG, cg = threadIdx.x - rg * kCG;
   const int64_t ntiles = (M + kTileRows - 1) / kTileRows;
   const int kq = K / 4;  // 16-byte chunks per row
   // rows of a tile: copied with cp.async (IN_ROWS), or formed from the parent's
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(256) dense_kernel(const float *__restrict__ in
   }
   float bias[4];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) bias[c] = (b && 4 * lane + c < N) ? b[4 * lane + c] : 0.f;
+  for (int c = 0; c < 4; ++c) bias[c] = (b && 4 * cg + c < N) ? b[4 * cg + c] : 0.f;
   for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
     const int64_t next = tile + gridDim.x;
     if (next < ntiles)
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(256) dense_kernel(const float *__restrict__ in
       asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncthreads();  // this tile (and W) visible to every warp
-    const float *xs = Xs + (it & 1) * (kTileRows * kXS) + warp * 8 * kXS;
+    const float *xs = Xs + (it & 1) * (kTileRows * kXS) + rg * kXS;
     float acc[8][4];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
@@ -125,10 +128,10 @@ __global__ void __launch_bounds__(256) dense_kernel(const float *__restrict__ in
     for (int k0 = 0; k0 < K; k0 += 4) {
       float4 x[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) x[r] = *reinterpret_cast<const float4 *>(xs + r * kXS + k0);
+      for (int r = 0; r < 8; ++r) x[r] = *reinterpret_cast<const float4 *>(xs + 8 * r * kXS + k0);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
-        const float4 w = *reinterpret_cast<const float4 *>(Wt + (k0 + kk) * kNC + 4 * lane);
+        const float4 w = *reinterpret_cast<const float4 *>(Wt + (k0 + kk) * kNC + 4 * cg);
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
           const float xv = kk == 0 ? x[r].x : (kk == 1 ? x[r].y : (kk == 2 ? x[r].z : x[r].w));
@@ -139,14 +142,14 @@ __global__ void __launch_bounds__(256) dense_kernel(const float *__restrict__ in
         }
       }
     }
-    const int64_t m0 = tile * kTileRows + warp * 8;
+    const int64_t m0 = tile * kTileRows + rg;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const int64_t m = m0 + r;
+      const int64_t m = m0 + 8 * r;
       if (m >= M) break;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int n = 4 * lane + c;
+        const int n = 4 * cg + c;
         if (n >= N) continue;
         if (EPI == EPI_STATE) {
           if (n < kD)
@@ -288,7 +291,7 @@ struct DnnCtx {
     const int64_t tiles = (M + kTileRows - 1) / kTileRows;
     const unsigned grid = unsigned(tiles < int64_t(2) * sm_count() ? tiles : int64_t(2) * sm_count());
     ProfScope ps(K_DNN_MLP, st);
-    dense_kernel<IN, EPI><<<grid, 256, smem, st>>>(in, M, K, W, b, N, out, ldo, io);
+    dense_kernel<IN, EPI><<<grid, kDenseThreads, smem, st>>>(in, M, K, W, b, N, out, ldo, io);
     return cudaGetLastError() == cudaSuccess ? BCTS_OK : fail(BCTS_ECUDA, "DNN dense layer launch failed");
   }
 
