@@ -645,7 +645,10 @@ extern "C" int bcts_search_device(bcts_ctx *ctx, const bcts_state *d_roots, int 
   if (n < 0 || (n > 0 && (!d_roots || !d_action || !d_values)))
     return c->fail(BCTS_EINVAL, "bcts_search_device: invalid argument");
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
-  return c->run_search(d_roots, n, c->A_create, c->d, d_action, d_values, c->A_create, st);
+  if (n == 0) return BCTS_OK;
+  return c->run_graphed({uintptr_t(n), reinterpret_cast<uintptr_t>(d_roots), reinterpret_cast<uintptr_t>(d_action),
+                         reinterpret_cast<uintptr_t>(d_values), reinterpret_cast<uintptr_t>(st)},
+                        st, [&] { return c->run_search(d_roots, n, c->A_create, c->d, d_action, d_values, c->A_create, st); });
 }
 
 extern "C" int64_t bcts_tree_nodes(int n, int A, int d) {
@@ -687,6 +690,63 @@ namespace bcts {
 // Host-pointer search: stage through pinned memory, run, copy back, check the
 // device error word, synchronise.  With depths/actions set, roots are grouped by
 // (A, d) (the batched form); otherwise all use the context's A and d.
+// A plain search that ran eagerly before under the same key, with unchanged
+// buffers, is captured into a CUDA graph and replayed from then on: small
+// searches are bound by their launches.  Profiling runs eagerly (it records
+// events); a stream that cannot be captured (the legacy stream, or one the
+// caller is capturing) runs eagerly too.
+int Ctx::run_graphed(const GraphKey &key, cudaStream_t st, const std::function<int()> &enqueue) {
+  if (profiler_on(prof)) return enqueue();
+  {
+    SearchGraph &g = sgraphs[key];
+    if (g.exec && g.generation == buf_generation) {
+      BCTS_CUDA_TRY(cudaGraphLaunch(g.exec, st), err);
+      profiler_add(prof, g.launches);
+      return BCTS_OK;
+    }
+    if (g.calls >= 1 && g.last_generation == buf_generation) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+      const int64_t before = profiler_total(prof);
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        cudaGraph_t graph = nullptr;
+        const int rc = enqueue();
+        const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        const bool ok = rc == BCTS_OK && ce == cudaSuccess && graph &&
+                        cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (rc != BCTS_OK) return rc;
+        if (ok) {
+          g.generation = buf_generation;
+          g.launches = profiler_total(prof) - before;
+          BCTS_CUDA_TRY(cudaGraphLaunch(g.exec, st), err);
+          return BCTS_OK;
+        }
+        g.exec = nullptr;
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
+  const int rc = enqueue();
+  if (rc != BCTS_OK) return rc;
+  if (sgraphs.size() > 32) {  // keep a few keys only
+    for (auto it = sgraphs.begin(); it != sgraphs.end();) {
+      if (it->first != key) {
+        if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+        it = sgraphs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  SearchGraph &g = sgraphs[key];
+  ++g.calls;
+  g.last_generation = buf_generation;
+  return BCTS_OK;
+}
+
 int Ctx::search_host(const bcts_state *roots, int n, const int32_t *depths, const int32_t *actions,
                      int32_t *out_action, float *out_values) {
   const int As = A_create;
@@ -713,60 +773,14 @@ int Ctx::search_host(const bcts_state *roots, int n, const int32_t *depths, cons
     BCTS_CUDA_TRY(cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream), err);
     return BCTS_OK;
   };
-  // A plain search of a root count seen before, with unchanged buffers, is
-  // captured into a CUDA graph and replayed from then on: small searches are
-  // bound by their launches.  (Profiling runs eagerly: it records events.)
-  bool done = false;
-  if (!depths && prune_keep == 0 && !tree_R && !profiler_on(prof)) {
-    SearchGraph &g = sgraphs[n];
-    if (g.exec && g.generation == buf_generation) {
-      BCTS_CUDA_TRY(cudaGraphLaunch(g.exec, stream), err);
-      profiler_add(prof, g.launches);
-      done = true;
-    } else if (g.calls >= 1 && g.last_generation == buf_generation) {
-      if (g.exec) cudaGraphExecDestroy(g.exec);
-      g.exec = nullptr;
-      const int64_t before = profiler_total(prof);
-      cudaGraph_t graph = nullptr;
-      if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        rc = enqueue();
-        const cudaError_t ce = cudaStreamEndCapture(stream, &graph);
-        if (rc == BCTS_OK && ce == cudaSuccess && graph &&
-            cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess) {
-          g.generation = buf_generation;
-          g.launches = profiler_total(prof) - before;
-          BCTS_CUDA_TRY(cudaGraphLaunch(g.exec, stream), err);
-          done = true;
-        } else {
-          g.exec = nullptr;
-        }
-        if (graph) cudaGraphDestroy(graph);
-        cudaGetLastError();
-        if (rc != BCTS_OK) return rc;
-      }
-    }
-    if (!done && sgraphs.size() > 16) {  // keep a few root counts only
-      for (auto it = sgraphs.begin(); it != sgraphs.end();) {
-        if (it->first != n) {
-          if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
-          it = sgraphs.erase(it);
-        } else {
-          ++it;
-        }
-      }
-    }
-  }
-  if (!done) {
+  if (!depths && prune_keep == 0 && !tree_R) {
+    rc = run_graphed({uintptr_t(n), 0, 0, 0, reinterpret_cast<uintptr_t>(stream)}, stream, enqueue);
+  } else {
     rc = enqueue();
-    if (rc != BCTS_OK) {
-      cudaStreamSynchronize(stream);
-      return rc;
-    }
-    if (!depths && prune_keep == 0 && !tree_R) {
-      SearchGraph &g = sgraphs[n];
-      ++g.calls;
-      g.last_generation = buf_generation;
-    }
+  }
+  if (rc != BCTS_OK) {
+    cudaStreamSynchronize(stream);
+    return rc;
   }
   BCTS_CUDA_TRY(cudaStreamSynchronize(stream), err);
   if (*herr != 0) {

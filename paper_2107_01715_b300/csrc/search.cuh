@@ -1,6 +1,8 @@
 // search.cuh -- the search context shared by search.cu, mixed.cu and serve.cu.
 #pragma once
 
+#include <array>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -48,7 +50,9 @@ struct Ctx {
   DevBuf io_roots, io_action, io_values, mixed_buf, z_buf;
   DevBuf pr_cand, pr_candR, pr_candQ, pr_par, pr_parR, pr_idx;  // pruned search
   int prune_keep = 0;  // > 0: run_search keeps this many nodes per root action and level (d >= 3)
-  // host-API searches replayed from CUDA graphs, keyed by root count
+  // plain searches replayed from CUDA graphs, keyed by (root count, the caller's
+  // device pointers or 0 for the host API, stream)
+  using GraphKey = std::array<uintptr_t, 5>;
   struct SearchGraph {
     cudaGraphExec_t exec = nullptr;
     uint64_t generation = 0;  // buffer generation the graph was captured with
@@ -56,7 +60,8 @@ struct Ctx {
     int calls = 0;
     uint64_t last_generation = 0;  // generation after the previous eager call
   };
-  std::map<int, SearchGraph> sgraphs;
+  std::map<GraphKey, SearchGraph> sgraphs;
+  int run_graphed(const GraphKey &key, cudaStream_t st, const std::function<int()> &enqueue);
   HostBuf host_stage;
 
   ServeState *serve = nullptr;

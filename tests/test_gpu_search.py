@@ -316,3 +316,29 @@ def test_graph_replayed_searches_are_identical(dev, precision):
     np.testing.assert_array_equal(val, val2)
     ctx.close()
     ctx2.close()
+
+
+@pytest.mark.parametrize("precision", [p for p in PRECISIONS if p in ("fp32", "bf16")])
+def test_graph_replayed_device_searches(dev, precision):
+    """The device API replays a captured graph for repeated (root count, pointers,
+    stream): new inputs written into the same buffers give the eager answers, and
+    other buffers or streams are separate graphs."""
+    torch, bcts = dev
+    A, d, n = 6, 3, 4
+    ctx, W = _ctx(bcts, A, d, 0.99, 1.0, precision)
+    ref_ctx, _ = _ctx(bcts, A, d, 0.99, 1.0, precision)
+    d_roots = torch.empty(n * 80, dtype=torch.uint8, device="cuda")
+    d_act = torch.empty(n, dtype=torch.int32, device="cuda")
+    d_val = torch.empty(n * A, dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    for i in range(5):  # eager, capture, replays: new roots each time in the same buffers
+        roots = inputs.root_states(range(100 * i, 100 * i + n))
+        d_roots.copy_(torch.from_numpy(roots.view(np.uint8).copy()))
+        torch.cuda.synchronize()
+        bcts.bcts_search_device(ctx, d_roots, n, d_act, d_val, st)
+        st.synchronize()
+        act_ref, val_ref = bcts.bcts_search(ref_ctx, roots)
+        np.testing.assert_array_equal(d_act.cpu().numpy(), act_ref)
+        np.testing.assert_array_equal(d_val.cpu().numpy().reshape(n, A), val_ref)
+    ctx.close()
+    ref_ctx.close()
