@@ -192,6 +192,31 @@ __device__ __forceinline__ uint4 pixels16_to_e4m3(const uint32_t (&w)[4]) {
   return make_uint4(o[0], o[1], o[2], o[3]);
 }
 
+// Epilogue arithmetic on column pairs: the packed FP32x2 add / multiply-add
+// (IEEE round-to-nearest per lane, the same results as the scalar operations),
+// and conversions that clamp negative values to zero as they round, so the
+// ReLU costs no instruction of its own.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// max(a, 0) and max(b, 0) as bf16, a in the low half
+__device__ __forceinline__ uint32_t relu_bf16x2(float2 a) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+// max(., 0) of a.x, a.y, b.x, b.y as saturated E4M3 codes, bytes 0..3 in that order
+__device__ __forceinline__ uint32_t relu_e4m3x4(float2 a, float2 b) {
+  uint32_t r;
+  asm("{\n\t.reg .b16 l, h;\n\t"
+      "cvt.rn.satfinite.relu.e4m3x2.f32 l, %2, %1;\n\t"
+      "cvt.rn.satfinite.relu.e4m3x2.f32 h, %4, %3;\n\t"
+      "mov.b32 %0, {l, h};\n\t}"
+      : "=r"(r)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
 // Byte offset of 16-byte chunk `ch` of row `r` in a 128-byte-swizzled tile.
 __device__ __forceinline__ uint32_t sw128_off(int r, int ch) {
   return uint32_t(r) * 128u + (uint32_t(ch ^ (r & 7)) << 4);
@@ -838,79 +863,71 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       for (int j = 0; j < BN / 16; ++j) {
         uint32_t r[16];
         tmem_ld16(tbase + uint32_t(j * 16), r);
-        float v[16];
+        float2 v[8];  // columns 2e, 2e + 1 of this 16-column chunk
         if (C::B_CAT) {
           uint32_t r2[16];  // the A_hi * B_lo half
           tmem_ld16(tbase + uint32_t(BN + j * 16), r2);
           tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]) + __uint_as_float(r2[e]);
+          for (int e = 0; e < 8; ++e)
+            v[e] = add2(make_float2(__uint_as_float(r[2 * e]), __uint_as_float(r[2 * e + 1])),
+                        make_float2(__uint_as_float(r2[2 * e]), __uint_as_float(r2[2 * e + 1])));
         } else {
           tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+          for (int e = 0; e < 8; ++e) v[e] = make_float2(__uint_as_float(r[2 * e]), __uint_as_float(r[2 * e + 1]));
         }
-        if constexpr (V == 2) {
+        // per-column scale (E4M3 accumulators carry the weight and input scales)
+        // plus offset: the bias, or for a leaf's conv1 the parent's partial map,
+        // which carries the bias
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {  // the partial carries the bias
-            const float4 z4 = *reinterpret_cast<const float4 *>(stg + lane * kStgRow + j * 64 + e * 16);
-            const int n = n0 + j * 16 + 4 * e;
-            if (FP8) {  // E4M3 accumulators carry the weight and input scales
-              v[4 * e] *= scale_s[n];
-              v[4 * e + 1] *= scale_s[n + 1];
-              v[4 * e + 2] *= scale_s[n + 2];
-              v[4 * e + 3] *= scale_s[n + 3];
-            }
-            v[4 * e] = fmaxf(v[4 * e] + z4.x, 0.f);
-            v[4 * e + 1] = fmaxf(v[4 * e + 1] + z4.y, 0.f);
-            v[4 * e + 2] = fmaxf(v[4 * e + 2] + z4.z, 0.f);
-            v[4 * e + 3] = fmaxf(v[4 * e + 3] + z4.w, 0.f);
-          }
-        } else if constexpr (V == 1) {
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {  // partial sum: no ReLU yet
-            const int n = n0 + j * 16 + e;
-            v[e] = FP8 ? fmaf(v[e], scale_s[n], bias_s[n]) : v[e] + bias_s[n];
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int n = n0 + j * 16 + e;
-            v[e] = fmaxf(FP8 ? fmaf(v[e], scale_s[n], bias_s[n]) : v[e] + bias_s[n], 0.f);
+        for (int e = 0; e < 4; ++e) {
+          const int n = n0 + j * 16 + 4 * e;
+          const float4 c4 = V == 2 ? *reinterpret_cast<const float4 *>(stg + lane * kStgRow + j * 64 + e * 16)
+                                   : *reinterpret_cast<const float4 *>(bias_s + n);
+          const float2 c0 = make_float2(c4.x, c4.y), c1 = make_float2(c4.z, c4.w);
+          if (FP8) {
+            const float4 s4 = *reinterpret_cast<const float4 *>(scale_s + n);
+            v[2 * e] = fma2(v[2 * e], make_float2(s4.x, s4.y), c0);
+            v[2 * e + 1] = fma2(v[2 * e + 1], make_float2(s4.z, s4.w), c1);
+          } else {
+            v[2 * e] = add2(v[2 * e], c0);
+            v[2 * e + 1] = add2(v[2 * e + 1], c1);
           }
         }
-        if constexpr (V == 1) {
+        if constexpr (V == 1) {  // partial sum: no ReLU yet
 #pragma unroll
           for (int e = 0; e < 4; ++e)
             *reinterpret_cast<float4 *>(stg + lane * kStgRow + j * 64 + e * 16) =
-                make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                make_float4(v[2 * e].x, v[2 * e].y, v[2 * e + 1].x, v[2 * e + 1].y);
         } else if constexpr (LAYER == 4) {
 #pragma unroll
           for (int e = 0; e < 4; ++e)
             *reinterpret_cast<float4 *>(stg + lane * kStgRow + e * 16) =
-                make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                make_float4(fmaxf(v[2 * e].x, 0.f), fmaxf(v[2 * e].y, 0.f), fmaxf(v[2 * e + 1].x, 0.f),
+                            fmaxf(v[2 * e + 1].y, 0.f));
           flush(static_cast<uint8_t *>(p.out_hi) + (size_t(n0) + j * 16) * 4, size_t(G::NTOT) * 4, mw0);
         } else if constexpr (FP8) {
+          // ReLU, then the output map's activation scale (positive, so the order is free)
+          const float2 inv = make_float2(p.out_inv_scale, p.out_inv_scale);
+          uint32_t w[4];
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const uint32_t lo = __nv_cvt_float2_to_fp8x2(
-                make_float2(v[4 * h] * p.out_inv_scale, v[4 * h + 1] * p.out_inv_scale), __NV_SATFINITE, __NV_E4M3);
-            const uint32_t hi = __nv_cvt_float2_to_fp8x2(
-                make_float2(v[4 * h + 2] * p.out_inv_scale, v[4 * h + 3] * p.out_inv_scale), __NV_SATFINITE,
-                __NV_E4M3);
-            olo[0] = lo | (hi << 16);  // reuse as a temporary
-            reinterpret_cast<uint32_t *>(stg + lane * kStgRow + j * 16)[h] = olo[0];
-          }
+          for (int h = 0; h < 4; ++h) w[h] = relu_e4m3x4(mul2(v[2 * h], inv), mul2(v[2 * h + 1], inv));
+          *reinterpret_cast<uint4 *>(stg + lane * kStgRow + j * 16) = make_uint4(w[0], w[1], w[2], w[3]);
         } else {
           uint32_t hh[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-            hh[e] = *reinterpret_cast<const uint32_t *>(&h);
             if constexpr (SPLIT) {
-              const float2 hf = __bfloat1622float2(h);
-              const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+              // hi = bf16(relu(v)), lo = bf16(relu(v) - hi)
+              const float2 x = make_float2(fmaxf(v[e].x, 0.f), fmaxf(v[e].y, 0.f));
+              const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+              hh[e] = *reinterpret_cast<const uint32_t *>(&h);
+              const float2 d = fma2(__bfloat1622float2(h), make_float2(-1.f, -1.f), x);  // exact product, one rounding
+              const __nv_bfloat162 l = __floats2bfloat162_rn(d.x, d.y);
               olo[j * 8 + e] = *reinterpret_cast<const uint32_t *>(&l);
+            } else {
+              hh[e] = relu_bf16x2(v[e]);
             }
           }
           *reinterpret_cast<uint4 *>(stg + lane * kStgRow + j * 32) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
