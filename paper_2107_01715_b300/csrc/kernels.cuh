@@ -50,6 +50,12 @@ int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts
                     float *maxq, void *scratch, cudaStream_t stream, int *d_err, const uint8_t *node_A = nullptr,
                     const ZLeaf *zl = nullptr);
 bool tc_has_partial(const TcWeights *w);
+// leaf_conv1.cu: conv1 of n leaves (states) from their parents' partial maps, as
+// ReLU(Z + the newest slot's term).  mode: 0 BF16, 1 FP32-class split (bf16 hi +
+// lo), 2 E4M3 scaled by out_scale.  T [4][2][2][32] and W3 [64][32] as built with
+// the tensor-core weights.
+int launch_leaf_conv1(int mode, const bcts_state *states, int64_t n, const ZLeaf &zl, const float *T,
+                      const float *W3, float out_scale, void *out_hi, void *out_lo, cudaStream_t st);
 int tc_conv1_partial(const TcWeights *w, const bcts_state *states, int64_t n, float *z, cudaStream_t st, int *d_err);
 
 // search.cu backup kernels

@@ -1024,10 +1024,21 @@ struct TcWeights {
   const float *colscale[4] = {};  // FP8: weight scale of each output channel x input activation scale
   float out_inv_scale[4] = {};    // FP8: 1 / activation scale of each layer's output map
   const float *f2w = nullptr, *f2b = nullptr;
+  // leaf conv1 (the newest slot's weights W_3 as this precision multiplies them):
+  const float *leafT = nullptr;   // [4 objects][2 dy][2 dx][32] palette x W_3 summed over the sprite
+  const float *leafW3 = nullptr;  // [64 patch pixels][32]
 };
 
 namespace {
 constexpr int kWRows[4] = {32, 64, 64, 512};
+
+// Value of an E4M3 code (1 sign, 4 exponent bits with bias 7, 3 mantissa bits;
+// exponent 0 is subnormal; the saturated encoder never emits the NaN code).
+float e4m3_value(uint8_t b) {
+  const int e = (b >> 3) & 15, m = b & 7;
+  const float mag = e == 0 ? std::ldexp(float(m), -9) : std::ldexp(float(8 + m), e - 10);
+  return (b & 0x80) ? -mag : mag;
+}
 constexpr int kWK[4] = {256, 512, 576, 3136};
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -1095,6 +1106,10 @@ int tc_weights_create(const float *w, int A, int precision, const float *act_sca
   total += align256(size_t(A) * 512 * 4);
   const size_t off_f2b = total;
   total += align256(size_t(A) * 4);
+  const size_t off_T = total;
+  total += align256(size_t(kObj) * 4 * kC1 * 4);
+  const size_t off_W3 = total;
+  total += align256(size_t(64) * kC1 * 4);
   std::vector<uint8_t> h(total, 0);
   TcWeights *t = new TcWeights();
   for (int l = 0; l < 4; ++l) {
@@ -1125,6 +1140,36 @@ int tc_weights_create(const float *w, int A, int precision, const float *act_sca
     }
     std::memcpy(h.data() + off[8 + l], bsrc[l], R * 4);
   }
+  {
+    // W_3 (conv1 weights of the newest slot, K = 192 + ky * 8 + kx) as this
+    // precision's leaf layer multiplies them, and the per-object sprite sums
+    float *W3 = reinterpret_cast<float *>(h.data() + off_W3);  // [64][32]
+    for (int c = 0; c < kC1; ++c)
+      for (int k = 0; k < 64; ++k) {
+        float w;
+        if (precision == BCTS_PREC_FP32) {
+          w = src[0][c * 256 + 192 + k];
+        } else if (fp8) {
+          const uint8_t code = h[off[0] + size_t(c) * kpad[0] + 192 + k];
+          w = e4m3_value(code) * reinterpret_cast<const float *>(h.data() + off[12])[c];
+        } else {
+          w = tc::bf2f(reinterpret_cast<const uint16_t *>(h.data() + off[0])[c * 256 + 192 + k]);
+        }
+        W3[k * kC1 + c] = w;
+      }
+    float *T = reinterpret_cast<float *>(h.data() + off_T);  // [object][dy][dx][32]
+    for (int o = 0; o < kObj; ++o)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx)
+          for (int c = 0; c < kC1; ++c) {
+            double acc = 0.0;
+            for (int sy = 0; sy < 4; ++sy)
+              for (int sx = 0; sx < 4; ++sx)
+                if ((kSprites >> (16 * o + 4 * sy + sx)) & 1ull)
+                  acc += double(W3[((4 * dy + sy) * 8 + 4 * dx + sx) * kC1 + c]);
+            T[((o * 2 + dy) * 2 + dx) * kC1 + c] = float(acc * double((kPalette >> (8 * o)) & 0xFFu));
+          }
+  }
   std::memcpy(h.data() + off_f2w, f2w, size_t(A) * 512 * 4);
   std::memcpy(h.data() + off_f2b, f2b, size_t(A) * 4);
   t->A = A;
@@ -1146,6 +1191,8 @@ int tc_weights_create(const float *w, int A, int precision, const float *act_sca
   }
   t->f2w = reinterpret_cast<const float *>(b + off_f2w);
   t->f2b = reinterpret_cast<const float *>(b + off_f2b);
+  t->leafT = reinterpret_cast<const float *>(b + off_T);
+  t->leafW3 = reinterpret_cast<const float *>(b + off_W3);
   *out = t;
   return BCTS_OK;
 }
@@ -1190,11 +1237,7 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
   };
   layer(0, states ? static_cast<const void *>(states) : static_cast<const void *>(frames), nullptr, a1, a1l);
   if (zl && states) {
-    p.zmap = zl->zmap;
-    p.z_leaf0 = zl->leaf0;
-    p.z_branch = zl->branch;
-    p.z_parent = zl->parent;
-    rc = tc::launch<1, MODE, true, 2>(p, (long long)n * kP1, K_CONV1_LEAF, st);
+    rc = launch_leaf_conv1(MODE, states, n, *zl, w->leafT, w->leafW3, w->out_inv_scale[0], a1, a1l, st);
   } else {
     rc = states ? tc::launch<1, MODE, true>(p, (long long)n * kP1, K_CONV1, st)
                 : tc::launch<1, MODE, false>(p, (long long)n * kP1, K_CONV1, st);

@@ -74,6 +74,31 @@ def test_search_matches_oracle(oracle_lib, dev, precision, A, d, n, c):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
+def test_search_overlapping_sprites(oracle_lib, dev, precision):
+    """Objects that share a cell in every frame (zero velocity), inside the grid
+    and on its edges and corners: the later object paints over the earlier one's
+    pixels (Sec. 5's renderer), which the leaves' conv1 must reproduce."""
+    torch, bcts = dev
+    A, d, gamma, c = 6, 2, 0.99, 1.0
+    shared = [((3, 4), (2, 3)), ((0, 0), (1, 2)), ((20, 20), (1, 3)), ((10, 0), (1, 2, 3)), ((19, 7), (2, 3)),
+              ((0, 20), (1, 2, 3)), ((11, 11), (1, 3))]
+    roots = inputs.root_states(range(200, 200 + len(shared)))
+    for i, ((x, y), objs) in enumerate(shared):
+        for k in objs:
+            roots["pos"][i, :, k, 0] = x
+            roots["pos"][i, :, k, 1] = y
+            roots["vel"][i, k] = 0
+    ctx, W = _ctx(bcts, A, d, gamma, c, precision)
+    act, val = bcts.bcts_search(ctx, roots)
+    ref = oracle_lib.search(roots, W, A, d, float(np.float32(gamma)), c)
+    tol = TOL[precision]
+    keep = [i for i in range(len(shared)) if precision in ("fp32", "fp32_simt") or pi_o_decided(ref["q0"][i], tol)]
+    assert value_close(val[keep], ref["values"][keep], tol).all(), np.abs(val[keep] - ref["values"][keep]).max()
+    check_actions(act[keep], ref["values"][keep], tol)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_search_ragged_chunks(oracle_lib, dev, precision):
     """Leaf chunk smaller than the leaf count and not dividing it: 3 roots x 6^2
     leaves = 108 leaves in chunks of 40."""
