@@ -60,17 +60,16 @@ WORKLOADS = {
 }
 L2_BYTES = 126 * 2 ** 20
 DTYPES = {"fp32": "f32 (bf16x3 split products, f32 accumulate)", "bf16": "bf16", "fp8": "e4m3", "fp32_simt": "f32"}
-# Multiply-accumulates per node each kernel class executes (Nature-DQN layers; conv1 over a
-# whole 4-frame stack, over three stack slots for a parent's partial map, over the one new
-# slot for a leaf scored from its parent's partial map).
-EXEC_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 400 * 32 * 192, "conv1_leaf": 400 * 32 * 64,
+# Tensor-core multiply-accumulates per node each kernel class executes (Nature-DQN layers;
+# conv1 over a whole 4-frame stack, or over three stack slots for a parent's partial map).
+# A leaf scored from its parent's partial map runs no contraction: its conv1 is a streaming
+# pass, ReLU(partial map + the newest slot's term), bound by its DRAM bytes alone.
+EXEC_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 400 * 32 * 192, "conv1_leaf": 0,
              "conv2": 81 * 64 * 512, "conv3": 49 * 64 * 576, "fc1": 512 * 3136}
 # DRAM bytes per node of each tensor-core kernel class, read + write, from the ncu captures
 # of the current kernels summarised in profiles/tc_gemm_layers_4roots_a18_d3.md (launches
 # over 23,328 leaves; traffic grows in proportion to the nodes a launch processes).
-TRAFFIC_PER_NODE = {"fp32/conv1_leaf": 51959.0, "fp32/conv2": 70891.0,
-                    "bf16/conv1_leaf": 26356.0, "bf16/conv2": 34932.0,
-                    "fp8/conv1_leaf": 13621.0, "fp8/conv2": 16968.0}
+TRAFFIC_PER_NODE = {}
 
 
 def layer_model(cls, precision, A):

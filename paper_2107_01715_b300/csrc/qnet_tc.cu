@@ -15,13 +15,17 @@
 //              epilogue;
 //   warps 8-11 (conv1: 8-15) epilogue: tcgen05.ld the accumulator (one TMEM lane per thread),
 //              add bias, ReLU, round to bf16 (and, in the FP32-class mode, the
-//              bf16 remainder) and store NHWC; up to four accumulators rotate so
-//              the next tiles' MMAs overlap this tile's epilogue.
-// Precision modes: BF16 (one MMA per K step) and FP32-class "split" mode, where
-// every operand x is carried as hi = bf16(x), lo = bf16(x - hi) and the product
-// is hi*hi + hi*lo + lo*hi (three MMAs; two for conv1, whose integer pixels are
-// exact in bf16), accumulated in FP32.  FC2 and the max over actions run in
-// FP32 on CUDA cores (9,216 MACs per node, 0.1 % of the network).
+//              bf16 remainder) or E4M3 and store NHWC; up to eight accumulators
+//              rotate so the next tiles' MMAs overlap this tile's epilogue.
+// Precision modes: BF16 (one MMA per K step), FP8 (E4M3 operands, K = 32 per
+// instruction, per-output-channel weight scales and per-layer activation
+// scales) and FP32-class "split" mode, where every operand x is carried as
+// hi = bf16(x), lo = bf16(x - hi) and the product is hi*hi + hi*lo + lo*hi
+// (three MMAs; two for conv1, whose integer pixels are exact in bf16),
+// accumulated in FP32.  FC2 and the max over actions run in FP32 on CUDA cores
+// (9,216 MACs per node, 0.1 % of the network).  The leaves' conv1 runs here
+// only when their parents' partial maps are not kept; otherwise it is the
+// streaming pass of leaf_conv1.cu.
 //
 // Every wait is bounded: a wait that runs out sets the context's device error
 // word and an abort flag, every role leaves its loop, in-flight copies and MMAs
@@ -278,11 +282,11 @@ constexpr int kBarBytes = 512;  // mbarriers, TMEM address, abort flag
 // with per-output-channel weight scales and per-layer activation scales.
 // A K block is always 128 bytes: 64 bf16 or 128 E4M3 elements (FP8 pads K to a
 // whole block with zero weights).
-// conv1 variants (bf16 and split modes): V = 0 the full 4-channel convolution;
-// V = 1 the parent partial Z = W_0 * slot1 + W_1 * slot2 + W_2 * slot3 + b (FP32
-// out, no ReLU); V = 2 a leaf: W_3 * slot3 + Z(parent), then ReLU.  A child's
-// slots 0..2 are its parent's slots 1..3 (frame stacking), and the convolution is
-// linear, so the leaf level needs one channel instead of four.
+// conv1 variants: V = 0 the full 4-channel convolution; V = 1 a parent's partial
+// map Z = W_0 * slot1 + W_1 * slot2 + W_2 * slot3 + b (FP32 out, no ReLU).  A
+// child's slots 0..2 are its parent's slots 1..3 (frame stacking) and the
+// convolution is linear, so a leaf's conv1 is ReLU(Z + W_3 * slot3), which the
+// streaming leaf kernel (leaf_conv1.cu) forms without a contraction.
 template <int LAYER, int MODE, int V = 0>
 struct Cfg {
   using G = Geo<LAYER>;
@@ -291,14 +295,12 @@ struct Cfg {
   static_assert(V == 0 || LAYER == 1, "partial-map variants are conv1 only");
   // A 128-byte K block holds one history slot (bf16) or two (E4M3: slots 2j, 2j + 1).
   // V1 (a parent's partial map) multiplies weight channels 0-2 with the parent's
-  // slots 1-3; V2 (a leaf) weight channel 3 with the leaf's slot 3.
-  static constexpr int SLOT0 = V == 1 ? 1 : (V == 2 ? (FP8 ? 2 : 3) : 0);  // slot of K block 0 (first half)
-  static constexpr int WC0 = V == 2 ? (FP8 ? 1 : 3) : 0;                   // first weight K block used
+  // slots 1-3.
+  static constexpr int SLOT0 = V == 1 ? 1 : 0;  // slot of K block 0 (first half)
   static constexpr int KB_FULL = FP8 ? (G::K + 127) / 128 : G::K / 64;
-  static constexpr int KB = V == 1 ? (FP8 ? 2 : 3) : (V == 2 ? 1 : KB_FULL);  // K blocks this kernel multiplies
-  // K steps (32 bytes each, four per K block) that carry data: E4M3 V2 uses only
-  // the second half of its K block (slot 3), E4M3 V1 only the first half of its last
-  static constexpr int J0 = (FP8 && V == 2) ? 2 : 0;  // first K step of K block 0
+  static constexpr int KB = V == 1 ? (FP8 ? 2 : 3) : KB_FULL;  // K blocks this kernel multiplies
+  // K steps (32 bytes each, four per K block) that carry data: E4M3 V1 uses only
+  // the first half of its last K block (slot 3 with weight channel 2)
   static constexpr int JL = (FP8 && V == 1) ? 2 : 4;  // K steps of the last K block
   static constexpr int KPAD = KB_FULL * (128 / EB);  // stored weight row length in elements
   static constexpr bool A_LO = SPLIT && LAYER != 1;  // conv1's integer pixels are exact in bf16
@@ -325,10 +327,9 @@ struct Cfg {
   // conv1 (32-column tiles, the lightest epilogue) runs two epilogue warpgroups
   // on alternating tiles so each has two tiles' time to hide its load latency
   static constexpr int EPI_WG = LAYER == 1 ? 2 : 1;
-  // contiguous tile range per CTA (see the tile schedule in the kernel): the
-  // conv1 leaf variant (siblings share a parent's partial map) and conv2/conv3
-  // (neighbouring output rows share input rows) gain from it; fc1 does not
-  static constexpr bool CONTIG = V == 2 || LAYER == 2 || LAYER == 3;
+  // contiguous tile range per CTA (see the tile schedule in the kernel):
+  // conv2/conv3 gain from it (neighbouring output rows share input rows)
+  static constexpr bool CONTIG = LAYER == 2 || LAYER == 3;
   static constexpr int MMA_WARP = 8 + 4 * EPI_WG;
   static constexpr int THREADS = 32 * (MMA_WARP + 1);
   static constexpr int SMEM = RES_BYTES + STAGES * STAGE_BYTES + 1024 + kBarBytes + DIRTY_BYTES + 2 * G::NTOT * 4 +
@@ -351,10 +352,6 @@ struct GemmParams {
   const float *bias;
   const float *colscale;  // FP8: per-output-channel weight scale x input activation scale
   float out_inv_scale;    // FP8: 1 / activation scale of this layer's output map
-  const float *zmap;      // conv1 leaf variant: parent partial maps [parent][400][32] FP32
-  uint32_t z_leaf0;       // global index (within the level) of this launch's first leaf
-  uint32_t z_branch;      // A: parent of leaf i = (z_leaf0 + i) / A
-  const uint32_t *z_parent;  // or, when set, parent of leaf i = z_parent[z_leaf0 + i]
   void *out_hi;  // bf16 NHWC (layers 1-3) or FP32 [M][512] (layer 4)
   void *out_lo;  // bf16 remainders (split mode, layers 1-3)
   uint32_t M;  // rows, < 2^31 (checked by the launcher)
@@ -444,7 +441,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
         const int kb = idx / (C::B_ROWS * 8), rem = idx - kb * (C::B_ROWS * 8), r = rem >> 3, c = rem & 7;
         const uint32_t off = uint32_t(kb) * (C::B_ROWS * 128) + sw128_off(r, c);
         const uint8_t *src = static_cast<const uint8_t *>(r < BN ? p.b_hi : p.b_lo);
-        cp_async16(res + off, src + ((long long)(r % BN) * C::KPAD) * EB + (C::WC0 + kb) * 128 + c * 16);
+        cp_async16(res + off, src + ((long long)(r % BN) * C::KPAD) * EB + kb * 128 + c * 16);
       }
       cp_commit();
       cp_wait<0>();
@@ -473,17 +470,10 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       // The fetch is issued after the tile's proxy fence so the fence never waits
       // for it.
       const uint32_t ring = smem_u32(dirty + 8 * kProd);
-      // The leaf variant (one K block per tile, contiguous tiles) renders three
-      // consecutive tiles per round: 384 rows still touch at most two nodes, so
-      // the same candidates cover all three, and the round's barriers, fence and
-      // arrivals are paid once for three tiles.
-      constexpr int TPR = (V == 2 && C::CONTIG) ? 3 : 1;  // tiles per producer round
-      static_assert(TPR == 1 || C::RING >= 2 * TPR, "a round's tiles need a ring of at least two rounds");
-      auto prefetch_states = [&](int t, int slot) {  // t: the round's first tile
+      auto prefetch_states = [&](int t, int slot) {
         if (pt < 10) {
           const uint32_t m0 = uint32_t(t) * 128u;
-          const uint32_t span = 128u * TPR - 1u;
-          const uint32_t mlast = (m0 + span < p.M - 1u) ? m0 + span : p.M - 1u;
+          const uint32_t mlast = (m0 + 127u < p.M - 1u) ? m0 + 127u : p.M - 1u;
           const uint32_t leaf0 = m0 / uint32_t(kP1), leaf_last = mlast / uint32_t(kP1);
           const uint32_t l = (leaf0 + uint32_t(pt / 5) <= leaf_last) ? leaf0 + uint32_t(pt / 5) : leaf_last;
           cp_async16(ring + uint32_t(slot * 160 + pt * 16),
@@ -493,40 +483,35 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       };
       if (T0 < TE) prefetch_states(T0, 0);
       else cp_commit();
-      if (T0 + TPR * TS < TE) prefetch_states(T0 + TPR * TS, 1);
+      if (T0 + TS < TE) prefetch_states(T0 + TS, 1);
       else cp_commit();
-      int c = 0, rd = 0;  // tiles and rounds so far
-      for (int t = T0; t < TE; t += TPR * TS, c += TPR, ++rd) {
-        const int left = (TE - t + TS - 1) / TS;
-        const int nt = left < TPR ? left : TPR;  // tiles in this round
+      int c = 0;  // tiles so far
+      for (int t = T0; t < TE; t += TS, ++c) {
         {
           // the MMA thread commits once per tile, to the tile's last stage: its
           // completion frees all KB stages (and those of every earlier tile)
-          const int gl = (c + nt - 1) * KB + KB - 1;
+          const int gl = c * KB + KB - 1;
           const int s = gl % S;
           const uint32_t round = uint32_t(gl / S);
           wait_bar(empty_bar(s), (round & 1u) ^ 1u, abort_flag, p.d_err, 1);
         }
         named_bar_sync(1, kProd);  // every producer decides together
         if (*abort_flag) break;
-        cp_wait<1>();  // this round's node states (the next round's may still be in flight)
-        for (int tt = 0; tt < nt; ++tt) {
-          const uint32_t *dj = dirty + ((c + tt) % C::RING) * (KB * kProd);
+        cp_wait<1>();  // this tile's node states (the next tile's may still be in flight)
+        uint32_t *dj = dirty + (c % C::RING) * (KB * kProd);
 #pragma unroll
-          for (int j = 0; j < KB; ++j) {
-            const uint32_t a = dj[j * kProd + pt];
-            if (a) st_shared16(a, make_uint4(0u, 0u, 0u, 0u));
-          }
+        for (int j = 0; j < KB; ++j) {
+          const uint32_t a = dj[j * kProd + pt];
+          if (a) st_shared16(a, make_uint4(0u, 0u, 0u, 0u));
         }
         named_bar_sync(1, kProd);  // states visible, re-zeroing done
         uint4 P[4];
         const uint4 *Ps = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(dirty + 8 * kProd) +
-                                                          (rd % 3) * 160 + li * 80);
+                                                          (c % 3) * 160 + li * 80);
 #pragma unroll
         for (int j = 0; j < 4; ++j) P[j] = Ps[j];
         const uint32_t m0 = uint32_t(t) * 128u;
-        const uint32_t span = 128u * uint32_t(nt) - 1u;
-        const uint32_t mlast = (m0 + span < p.M - 1u) ? m0 + span : p.M - 1u;
+        const uint32_t mlast = (m0 + 127u < p.M - 1u) ? m0 + 127u : p.M - 1u;
         const uint32_t leaf0 = m0 / uint32_t(kP1), leaf_last = mlast / uint32_t(kP1);
         // bf16: K block j = history slot j, chunk cc = kernel row cc (8 pixels);
         // E4M3: K block j = slots 2j, 2j+1, chunk cc = slot 2j + cc/4, kernel rows
@@ -534,18 +519,16 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
 #pragma unroll
         for (int j = 0; j < KB; ++j) {
           uint32_t wrote = 0u;
-          int wt = 0;  // the round's tile the candidate row falls in
           const uint32_t leaf = leaf0 + uint32_t(li);
           const int slot = FP8 ? C::SLOT0 + 2 * j + (cc >> 2) : C::SLOT0 + j;
-          // E4M3 partial-map variants leave the halves their MMAs skip unrendered
-          const bool used = slot <= 3 && !(FP8 && V == 2 && cc < 4);
           // the slot depends on the chunk (E4M3): read it from the state ring, not
           // from a runtime-indexed register array (which would live in local memory)
           const uint4 Pv = FP8 ? Ps[slot & 3] : P[slot & 3];
           const uint32_t wk = (k & 2) ? ((k & 1) ? Pv.w : Pv.z) : ((k & 1) ? Pv.y : Pv.x);
           const int ox = int(int16_t(wk & 0xFFFFu)) - dx, oy = int(int16_t(wk >> 16)) - dy;
           const uint32_t m = leaf * uint32_t(kP1) + uint32_t(oy * 20 + ox);
-          if (used && leaf <= leaf_last && ox >= 0 && ox <= 19 && oy >= 0 && oy <= 19 && m >= m0 && m <= mlast) {
+          if (slot <= 3 && leaf <= leaf_last && ox >= 0 && ox <= 19 && oy >= 0 && oy <= 19 && m >= m0 &&
+              m <= mlast) {
             int oxs[4], oys[4];
             unpack_slot(Pv, oxs, oys);
             uint4 v;
@@ -558,20 +541,15 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
               const int y = 4 * oy + cc;
               v = pixels8_to_bf16(render_word(oxs, oys, ox, y), render_word(oxs, oys, ox + 1, y));
             }
-            const uint32_t off = m - m0;
-            wt = int(off >> 7);
-            wrote = sA_of(((c + wt) * KB + j) % S) + sw128_off(int(off & 127u), cc);
+            wrote = sA_of((c * KB + j) % S) + sw128_off(int(m - m0), cc);
             st_shared16(wrote, v);
           }
-          for (int tt = 0; tt < nt; ++tt)
-            dirty[((c + tt) % C::RING) * (KB * kProd) + j * kProd + pt] = tt == wt ? wrote : 0u;
+          dj[j * kProd + pt] = wrote;
         }
         fence_proxy_async();
-        for (int tt = 0; tt < nt; ++tt)
 #pragma unroll
-          for (int kb = 0; kb < KB; ++kb) mbar_arrive(full_bar(((c + tt) * KB + kb) % S));
-        const int t2 = t + 2 * TPR * TS;
-        if (t2 < TE) prefetch_states(t2, (rd + 2) % 3);
+        for (int kb = 0; kb < KB; ++kb) mbar_arrive(full_bar((c * KB + kb) % S));
+        if (t + 2 * TS < TE) prefetch_states(t + 2 * TS, (c + 2) % 3);
         else cp_commit();
       }
       asm volatile("cp.async.wait_all;" ::: "memory");
@@ -728,8 +706,8 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
           const uint32_t sBlo = sB + C::B_BYTES;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {  // K = 16 bf16 / 32 E4M3 = 32 bytes per instruction
-            if ((kb == 0 && j < C::J0) || (kb == KB - 1 && j >= C::JL)) continue;
-            const uint32_t first = (kb != 0 || j != C::J0) ? 1u : 0u;
+            if (kb == KB - 1 && j >= C::JL) continue;
+            const uint32_t first = (kb != 0 || j != 0) ? 1u : 0u;
             const uint64_t a = sw128_desc(sA) + uint64_t(2 * j);
             const uint64_t b = sw128_desc(sB) + uint64_t(2 * j);
             if (FP8) {
@@ -769,8 +747,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
     // ------------------------------------------------------------ epilogue
     // Each warp owns 32 accumulator rows (its TMEM lane quarter).  Results are
     // staged row by row in shared memory and written out as contiguous 16-byte
-    // segments, so every global store instruction covers whole lines; the
-    // parent partial rows of the conv1 leaf variant are read the same way.
+    // segments, so every global store instruction covers whole lines.
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     float *scale_s = bias_s + G::NTOT;
     const int eg = (warp - kEpiWarp0) >> 2;  // warpgroup: tiles it with it % EPI_WG == eg
@@ -796,45 +773,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       }
       __syncwarp();
     };
-    float4 zc[V == 2 ? 8 : 1];  // conv1 leaf: partial rows, fetched cooperatively (row i*4 + lane/8)
-    auto zload = [&](int t) {
-      if constexpr (V == 2) {
-        // a warp's 32 rows span at most two leaves (400 rows each): one division
-        // by the branching factor per tile gives both parents
-        const uint32_t mw0 = uint32_t(t / NT) * 128u + uint32_t(q * 32);
-        const uint32_t mwc = mw0 < p.M ? mw0 : p.M - 1u;  // a warp past the end reads row M - 1
-        const uint32_t leafA = mwc / uint32_t(kP1), pxA = mwc - leafA * uint32_t(kP1);
-        const uint32_t gA = p.z_leaf0 + leafA;
-        uint32_t parA, parB;
-        if (p.z_parent) {  // groups of different branching (batched form): per-leaf table
-          const uint32_t lastLeaf = (p.M - 1u) / uint32_t(kP1);
-          parA = __ldg(p.z_parent + gA);
-          parB = __ldg(p.z_parent + p.z_leaf0 + (leafA + 1u <= lastLeaf ? leafA + 1u : lastLeaf));
-        } else {
-          parA = gA / p.z_branch;
-          parB = parA + ((gA - parA * p.z_branch + 1u == p.z_branch) ? 1u : 0u);
-        }
-        const float *zA = p.zmap + size_t(parA) * (kP1 * kC1);
-        const float *zB = p.zmap + size_t(parB) * (kP1 * kC1);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const uint32_t r = uint32_t(i * 4 + (lane >> 3));
-          uint32_t px = pxA + r;
-          const float *zrow = zA;
-          if (px >= uint32_t(kP1)) {
-            px -= uint32_t(kP1);
-            zrow = zB;
-          }
-          if (mw0 + r >= p.M) {  // ragged last tile: a valid row (its output is not stored)
-            px = pxA;
-            zrow = zA;
-          }
-          zc[i] = __ldg(reinterpret_cast<const float4 *>(zrow + size_t(px) * kC1) + (lane & 7));
-        }
-      }
-    };
     constexpr int EW = C::EPI_WG;
-    if (V == 2 && T0 + eg * TS < TE) zload(T0 + eg * TS);
     int it = eg;
     for (int t = T0 + eg * TS; t < TE; t += EW * TS, it += EW) {
       const int acc = it % NA;
@@ -843,18 +782,6 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
       const uint32_t mw0 = uint32_t(t / NT) * 128u + uint32_t(q * 32);
       const int n0 = (t % NT) * BN;
       const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * C::ACC_N);
-      if constexpr (V == 2) {
-        // partial rows into this warp's staging rows; chunk j reads bytes [64 j, 64 j + 64)
-        // of its row before it writes output bytes [32 j, 32 j + 32), so nothing is
-        // overwritten before it is read
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          *reinterpret_cast<float4 *>(stg + (i * 4 + (lane >> 3)) * kStgRow + (lane & 7) * 16) = zc[i];
-        __syncwarp();
-        // the registers are free again: fetch the next tile's rows now, so their
-        // latency overlaps this whole tile
-        if (t + EW * TS < TE) zload(t + EW * TS);
-      }
       // this thread's output row: hi part staged as it is produced, lo part kept
       // in registers until the hi rows are written
       constexpr int OW = LAYER == 4 ? 1 : (FP8 ? BN / 4 : BN / 2);
@@ -878,13 +805,11 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
           for (int e = 0; e < 8; ++e) v[e] = make_float2(__uint_as_float(r[2 * e]), __uint_as_float(r[2 * e + 1]));
         }
         // per-column scale (E4M3 accumulators carry the weight and input scales)
-        // plus offset: the bias, or for a leaf's conv1 the parent's partial map,
-        // which carries the bias
+        // plus bias
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int n = n0 + j * 16 + 4 * e;
-          const float4 c4 = V == 2 ? *reinterpret_cast<const float4 *>(stg + lane * kStgRow + j * 64 + e * 16)
-                                   : *reinterpret_cast<const float4 *>(bias_s + n);
+          const float4 c4 = *reinterpret_cast<const float4 *>(bias_s + n);
           const float2 c0 = make_float2(c4.x, c4.y), c1 = make_float2(c4.z, c4.w);
           if (FP8) {
             const float4 s4 = *reinterpret_cast<const float4 *>(scale_s + n);
