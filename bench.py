@@ -66,10 +66,14 @@ DTYPES = {"fp32": "f32 (bf16x3 split products, f32 accumulate)", "bf16": "bf16",
 # pass, ReLU(partial map + the newest slot's term), bound by its DRAM bytes alone.
 EXEC_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 400 * 32 * 192, "conv1_leaf": 0,
              "conv2": 81 * 64 * 512, "conv3": 49 * 64 * 576, "fc1": 512 * 3136}
-# DRAM bytes per node of each tensor-core kernel class, read + write, from the ncu captures
-# of the current kernels summarised in profiles/tc_gemm_layers_4roots_a18_d3.md (launches
-# over 23,328 leaves; traffic grows in proportion to the nodes a launch processes).
-TRAFFIC_PER_NODE = {}
+# DRAM bytes per node of the leaf-level kernel classes, read + write, from the ncu captures
+# of the current kernels summarised in profiles/tc_gemm_layers_4roots_a18_d3.md and
+# profiles/leaf_conv1_4roots_a18_d3.md (launches over 23,328 leaves; traffic grows in
+# proportion to the nodes a launch processes).
+TRAFFIC_PER_NODE = {"fp32/conv2": 70907.0, "bf16/conv2": 34946.0, "fp8/conv2": 16977.0,
+                    "fp32/conv3": 31898.0, "bf16/conv3": 15320.0, "fp8/conv3": 7003.0,
+                    "fp32/fc1": 14581.0, "bf16/fc1": 7442.0, "fp8/fc1": 3568.0,
+                    "fp32/conv1_leaf": 53948.0, "bf16/conv1_leaf": 27207.0, "fp8/conv1_leaf": 13570.0}
 
 
 def layer_model(cls, precision, A):
@@ -129,7 +133,8 @@ def roofline_for(dom, precision, A, nodes, ms, launches, pk, pk_kind):
     tpn = TRAFFIC_PER_NODE.get(f"{precision}/{dom}")
     common = {"kernel": dom, "traffic": tpn * per_launch if tpn else None,
               "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per node of the current "
-                               "kernel (profiles/tc_gemm_layers_4roots_a18_d3.md) x nodes per launch")
+                               "kernel (profiles/tc_gemm_layers_4roots_a18_d3.md, "
+                               "profiles/leaf_conv1_4roots_a18_d3.md) x nodes per launch")
               if tpn else "no ncu capture of this kernel class",
               "algorithmic_bytes_per_launch": (rd + wr) * per_launch,
               "executed_flops_per_launch": flops / max(launches, 1),
@@ -662,26 +667,40 @@ def run_ours(args, wl):
             out = bcts.bcts_search(cx, rts)
             cx.close()
             return out
+        # The corrected values also depend on pi_o = argmax Q_0 (Eq. 3 penalises every action
+        # but pi_o), a discrete choice that flips wherever the root Q top-2 margin is within
+        # the Q-network's error, so a decision is also counted where pi_o is decided: the
+        # root Q top-2 margin exceeds twice the measured root-Q error (d = 0 searches).
         _, v32_0 = run("fp32", 0.0, roots, d)
         _, vlo_0 = run(precision, 0.0, roots, d)
         err0 = np.abs(vlo_0.astype(np.float64) - v32_0)
         tol = float(err0.max())
         extra = inputs.root_states(range(50000, 50256))
-        agree, counted, agree_all, total_roots = 0, 0, 0, 0
-        for rts, dd in ((roots, d), (extra, 2)):
+        q32 = [run("fp32", 0.0, rts, 0)[1] for rts in (roots, extra)]
+        qlo = [run(precision, 0.0, rts, 0)[1] for rts in (roots, extra)]
+        qtol = float(max(np.abs(a.astype(np.float64) - b).max() for a, b in zip(qlo, q32)))
+        agree, counted, agree_all, total_roots, agree_dec, counted_dec = 0, 0, 0, 0, 0, 0
+        for (rts, dd), q in zip(((roots, d), (extra, 2)), q32):
             a32, v32 = run("fp32", wl["c"], rts, dd)
             alo, _ = run(precision, wl["c"], rts, dd)
             srt = np.sort(v32, axis=1)
             sure = (srt[:, -1] - srt[:, -2]) > 2 * tol
+            qs = np.sort(q, axis=1)
+            decided = sure & ((qs[:, -1] - qs[:, -2]) > 2 * qtol)
             agree += int((alo[sure] == a32[sure]).sum())
             counted += int(sure.sum())
+            agree_dec += int((alo[decided] == a32[decided]).sum())
+            counted_dec += int(decided.sum())
             agree_all += int((alo == a32).sum())
             total_roots += len(rts)
         precision_report = {"vs": "fp32-class runs of the same roots",
                             "value_max_abs_err_c0": tol, "value_mean_abs_err_c0": float(err0.mean()),
+                            "root_q_max_abs_err": qtol,
                             "decision_roots": total_roots, "action_agreement_all": agree_all / total_roots,
                             "roots_with_margin_above_2x_err": counted,
-                            "action_agreement_where_margin_exceeds": agree / counted if counted else None}
+                            "action_agreement_where_margin_exceeds": agree / counted if counted else None,
+                            "roots_decided": counted_dec,
+                            "action_agreement_where_decided": agree_dec / counted_dec if counted_dec else None}
 
     lat = sorted(step_ms)
     p50 = lat[len(lat) // 2]

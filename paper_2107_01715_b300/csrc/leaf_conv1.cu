@@ -20,9 +20,9 @@
 // Output formats as the tensor-core layers expect them: bf16 (BF16), bf16 hi + lo
 // (FP32-class split) or E4M3 scaled by the conv1 map's activation scale (FP8).
 #include <cuda_bf16.h>
-#include <cuda_fp8.h>
 
 #include "kernels.cuh"
+#include "pack.cuh"
 #include "render.cuh"
 
 namespace bcts {
@@ -54,27 +54,28 @@ __device__ __forceinline__ uint32_t bf16x2(float a, float b) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// Store ReLU(v) for float4 number f of leaf row-major map (4 channels).
+// Store ReLU(v) for float4 number f of the leaves' row-major maps (4 channels);
+// the ReLU is folded into the rounding conversion where no remainder is kept.
 template <int MODE>
 __device__ __forceinline__ void store_relu(const Args &p, int64_t f, float4 v) {
-  v.x = fmaxf(v.x, 0.f);
-  v.y = fmaxf(v.y, 0.f);
-  v.z = fmaxf(v.z, 0.f);
-  v.w = fmaxf(v.w, 0.f);
-  if constexpr (MODE == 2) {
-    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v.x * p.out_scale, v.y * p.out_scale), __NV_SATFINITE,
-                                                 __NV_E4M3);
-    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v.z * p.out_scale, v.w * p.out_scale), __NV_SATFINITE,
-                                                 __NV_E4M3);
-    reinterpret_cast<uint32_t *>(p.out_hi)[f] = lo | (hi << 16);
+  if constexpr (MODE == 2) {  // activation scale (positive) then E4M3
+    const float2 s = make_float2(p.out_scale, p.out_scale);
+    reinterpret_cast<uint32_t *>(p.out_hi)[f] =
+        relu_e4m3x4(mul2(make_float2(v.x, v.y), s), mul2(make_float2(v.z, v.w), s));
+  } else if constexpr (MODE == 0) {
+    reinterpret_cast<uint2 *>(p.out_hi)[f] =
+        make_uint2(relu_bf16x2(make_float2(v.x, v.y)), relu_bf16x2(make_float2(v.z, v.w)));
   } else {
+    v.x = fmaxf(v.x, 0.f);
+    v.y = fmaxf(v.y, 0.f);
+    v.z = fmaxf(v.z, 0.f);
+    v.w = fmaxf(v.w, 0.f);
     const uint32_t h0 = bf16x2(v.x, v.y), h1 = bf16x2(v.z, v.w);
     reinterpret_cast<uint2 *>(p.out_hi)[f] = make_uint2(h0, h1);
-    if constexpr (MODE == 1) {  // remainder below the bf16 rounding, exact in FP32
-      const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h0));
-      const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h1));
-      reinterpret_cast<uint2 *>(p.out_lo)[f] = make_uint2(bf16x2(v.x - a.x, v.y - a.y), bf16x2(v.z - b.x, v.w - b.y));
-    }
+    // remainder below the bf16 rounding, exact in FP32
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h0));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h1));
+    reinterpret_cast<uint2 *>(p.out_lo)[f] = make_uint2(bf16x2(v.x - a.x, v.y - a.y), bf16x2(v.z - b.x, v.w - b.y));
   }
 }
 
