@@ -129,77 +129,87 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   }
 }
 
-// FC2 + max over actions: q = W2 h + b2, maxq = max_a q[a].  A persistent grid of
-// 256-thread blocks: each block stages W2 (zero rows past A, 36 KB) and b2 in
-// shared memory once, and each warp then takes 32 nodes at a time, one per lane.
-// The warp's 32 rows of h pass through a per-warp shared tile in 32-column
-// chunks (loaded coalesced, read back one row per lane), and every W2 value the
-// lanes multiply is the same for all 32 of them (a broadcast read), so W2 leaves
-// shared memory once per 32 nodes rather than once per node.
-constexpr int kFc2Warps = 8;
-constexpr int kHCols = 32;         // h columns per chunk
-constexpr int kHRow = kHCols + 4;  // tile row stride (floats): 16-byte aligned, conflict-free row reads
-
-size_t fc2_smem_bytes() { return (size_t(kMaxA) * kF1 + 32 + size_t(kFc2Warps) * 32 * kHRow) * sizeof(float); }
-
-__global__ void __launch_bounds__(kFc2Warps * 32) fc2_max_kernel(const float *__restrict__ h,
-                                                                const float *__restrict__ W2,
-                                                                const float *__restrict__ b2, int A, int64_t n,
-                                                                float *__restrict__ q, float *__restrict__ maxq,
-                                                                const uint8_t *__restrict__ node_A) {
-  extern __shared__ __align__(16) float fc2_smem[];
-  float *w = fc2_smem;                  // [kMaxA][512]
-  float *bs = w + kMaxA * kF1;          // [32]
-  float *tile = bs + 32;                // [warps][32][kHRow]
-  for (int i = threadIdx.x; i < kMaxA * kF1; i += blockDim.x) w[i] = i < A * kF1 ? W2[i] : 0.f;
-  if (threadIdx.x < 32) bs[threadIdx.x] = threadIdx.x < A ? b2[threadIdx.x] : 0.f;
+// FC2 + max over actions: q = W2 h + b2, maxq = max_a q[a].  A persistent grid:
+// each block stages W2 (A x 512, at most 36 KB) in shared memory once, with all
+// of a thread's loads in flight together (a loop that waits for each load before
+// its store costs an L2 round trip per element, tens of microseconds per launch),
+// and its warps then take nodes in turn.  Lane l holds h[4 l + 128 j .. + 3]; its 16
+// products per action are summed across the warp by a reduce-scatter butterfly
+// (31 shuffles for all actions at once), after which lane a holds q[a].
+__global__ void __launch_bounds__(256) fc2_max_kernel(const float *__restrict__ h, const float *__restrict__ W2,
+                                                      const float *__restrict__ b2, int A, int64_t n,
+                                                      float *__restrict__ q, float *__restrict__ maxq,
+                                                      const uint8_t *__restrict__ node_A) {
+  __shared__ __align__(16) float w[kMaxA * kF1];
+  if ((reinterpret_cast<uintptr_t>(W2) & 15u) == 0) {
+    constexpr int NV = kMaxA * kF1 / 4, PER = (NV + 255) / 256;
+    float4 v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * 256;
+      v[k] = i < A * (kF1 / 4) ? __ldg(reinterpret_cast<const float4 *>(W2) + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * 256;
+      if (i < NV) reinterpret_cast<float4 *>(w)[i] = v[k];
+    }
+  } else {
+#pragma unroll 12
+    for (int i = threadIdx.x; i < A * kF1; i += blockDim.x) w[i] = __ldg(W2 + i);
+  }
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float *tl = tile + wid * (32 * kHRow);
-  const int64_t groups = (n + 31) / 32;
-  for (int64_t g = int64_t(blockIdx.x) * kFc2Warps + wid; g < groups; g += int64_t(gridDim.x) * kFc2Warps) {
-    const int64_t node0 = g * 32;
-    float acc[kMaxA];
+  const int lane = threadIdx.x & 31;
+  const float bias = lane < A ? __ldg(b2 + lane) : 0.f;
+  const int64_t nwarps = int64_t(gridDim.x) * (blockDim.x / 32);
+  for (int64_t node = int64_t(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5); node < n; node += nwarps) {
+    float x[16];
+    const float4 *hv = reinterpret_cast<const float4 *>(h + node * kF1);
 #pragma unroll
-    for (int a = 0; a < kMaxA; ++a) acc[a] = 0.f;
-    for (int c = 0; c < kF1; c += kHCols) {
-      // rows lane / 8 + 4 i, 16-byte column chunk lane % 8: each load covers four whole 128-byte rows
+    for (int j = 0; j < 4; ++j) {
+      const float4 t = __ldg(hv + lane + 32 * j);
+      x[4 * j] = t.x;
+      x[4 * j + 1] = t.y;
+      x[4 * j + 2] = t.z;
+      x[4 * j + 3] = t.w;
+    }
+    float v[32];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int r = (lane >> 3) + 4 * i;
-        const int64_t nd = node0 + r < n ? node0 + r : n - 1;  // past the end: a valid row, not stored
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(h + nd * kF1 + c) + (lane & 7));
-        *reinterpret_cast<float4 *>(tl + r * kHRow + (lane & 7) * 4) = v;
-      }
-      __syncwarp();
+    for (int a = 0; a < 32; ++a) {
+      float s = 0.f;
+      if (a < kMaxA && a < A) {
+        const float4 *wa = reinterpret_cast<const float4 *>(w + a * kF1);
 #pragma unroll
-      for (int jj = 0; jj < kHCols; jj += 4) {
-        const float4 x = *reinterpret_cast<const float4 *>(tl + lane * kHRow + jj);
-#pragma unroll
-        for (int a = 0; a < kMaxA; ++a) {
-          const float4 wv = *reinterpret_cast<const float4 *>(w + a * kF1 + c + jj);
-          acc[a] = fmaf(x.x, wv.x, acc[a]);
-          acc[a] = fmaf(x.y, wv.y, acc[a]);
-          acc[a] = fmaf(x.z, wv.z, acc[a]);
-          acc[a] = fmaf(x.w, wv.w, acc[a]);
+        for (int j = 0; j < 4; ++j) {
+          const float4 c = wa[lane + 32 * j];
+          s = fmaf(x[4 * j], c.x, s);
+          s = fmaf(x[4 * j + 1], c.y, s);
+          s = fmaf(x[4 * j + 2], c.z, s);
+          s = fmaf(x[4 * j + 3], c.w, s);
         }
       }
-      __syncwarp();
+      v[a] = s;
     }
-    const int64_t node = node0 + lane;
-    if (node < n) {
-      // node_A (batched form): the max runs over this node's own first node_A actions
-      const int An = node_A ? int(node_A[node]) : A;
-      float best = -INFINITY;
+    // reduce-scatter: at offset o a lane keeps the half of its remaining actions
+    // selected by its bit o and receives its partner's partial sums for them
 #pragma unroll
-      for (int a = 0; a < kMaxA; ++a) {
-        if (a >= A) break;
-        const float s = acc[a] + bs[a];
-        if (q) q[node * A + a] = s;
-        if (a < An) best = fmaxf(best, s);
+    for (int o = 16; o >= 1; o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < o; ++i) {
+        const float send = up ? v[i] : v[i + o];
+        const float keep = up ? v[i + o] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
       }
-      if (maxq) maxq[node] = best;
     }
+    const float s = v[0] + bias;  // q[node][lane] for lane < A
+    if (q && lane < A) q[node * A + lane] = s;
+    // node_A (batched form): the max runs over this node's own first node_A actions
+    const int An = node_A ? int(node_A[node]) : A;
+    float best = lane < An ? s : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (maxq && lane == 0) maxq[node] = best;
   }
 }
 
@@ -238,20 +248,19 @@ int simt_qnet_forward(const SimtWeights &w, const uint8_t *frames, int64_t n, fl
 int launch_fc2_max(const float *h, const float *W2, const float *b2, int A, int64_t n, float *q, float *maxq,
                    cudaStream_t st, const uint8_t *node_A) {
   if (n <= 0) return BCTS_OK;
-  if (A < 1 || A > kMaxA) return BCTS_EINVAL;
+  const int warps = 8;
   static int sms = 0;
   static std::once_flag once;
   std::call_once(once, [] {
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
-    cudaFuncSetAttribute(fc2_max_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fc2_smem_bytes()));
   });
-  // persistent: three blocks per SM (74 KB of shared memory each), never more warps than 32-node groups
-  const int64_t blocks = ((n + 31) / 32 + kFc2Warps - 1) / kFc2Warps;
-  const unsigned grid = unsigned(blocks < int64_t(3) * sms ? blocks : int64_t(3) * sms);
+  // persistent: four blocks per SM (36 KB of W2 each), never more blocks than node groups
+  const int64_t groups = (n + warps - 1) / warps;
+  const unsigned grid = unsigned(groups < int64_t(4) * sms ? groups : int64_t(4) * sms);
   ProfScope ps(K_FC2, st);
-  fc2_max_kernel<<<grid, kFc2Warps * 32, fc2_smem_bytes(), st>>>(h, W2, b2, A, n, q, maxq, node_A);
+  fc2_max_kernel<<<grid, warps * 32, 0, st>>>(h, W2, b2, A, n, q, maxq, node_A);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 
