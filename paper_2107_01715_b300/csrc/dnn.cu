@@ -103,10 +103,23 @@ __global__ void __launch_bounds__(kDenseThreads) dense_kernel(const float *__res
   };
   int64_t tile = blockIdx.x;
   if (tile < ntiles) issue(tile, 0);
-  // W, read in its own row order (coalesced), stored transposed
-  for (int i = threadIdx.x; i < kNC * K; i += blockDim.x) {
-    const int n = i / K, k = i - n * K;
-    Wt[k * kNC + n] = n < N ? W[i] : 0.f;
+  // W, read in its own row order (coalesced), stored transposed; ten loads of a
+  // thread in flight at once (one at a time costs an L2 round trip per element)
+  for (int i0 = threadIdx.x; i0 < kNC * K; i0 += 10 * blockDim.x) {
+    float v[10];
+#pragma unroll
+    for (int u = 0; u < 10; ++u) {
+      const int i = i0 + u * blockDim.x;
+      v[u] = (i < kNC * K && i / K < N) ? __ldg(W + i) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 10; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < kNC * K) {
+        const int n = i / K, k = i - n * K;
+        Wt[k * kNC + n] = v[u];
+      }
+    }
   }
   float bias[4];
 #pragma unroll
@@ -172,9 +185,10 @@ __global__ void __launch_bounds__(256) dnn_q_kernel(const float *__restrict__ s,
                                                     const float *__restrict__ bq, int A, float *__restrict__ q,
                                                     float *__restrict__ maxq) {
   __shared__ float w[kMaxDnnA * 128];
-  for (int i = threadIdx.x; i < kMaxDnnA * 128; i += blockDim.x) {
+#pragma unroll
+  for (int i = threadIdx.x; i < kMaxDnnA * 128; i += 256) {  // all of a thread's loads in flight together
     const int a = i >> 7, k = i & 127;
-    w[i] = (a < A && k < kD) ? wq[a * kD + k] : 0.f;
+    w[i] = (a < A && k < kD) ? __ldg(wq + a * kD + k) : 0.f;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
