@@ -293,11 +293,21 @@ struct Cfg {
   static constexpr int B_BYTES = G::BN * 128;            // one of hi / lo
   static constexpr int ACC_N = B_CAT ? 2 * G::BN : G::BN;  // accumulator columns per tile
   static constexpr int RES_BYTES = B_RES ? KB * B_ROWS * 128 : 0;
-  static constexpr int STAGE_BYTES = A_BYTES * (A_LO ? 2 : 1) + (B_RES ? 0 : B_ROWS * 128);
+  // K blocks per pipeline stage, and stages the MMA thread waits for (and
+  // fences) as one group.  A stage's hand-off (barrier wait, arrivals, proxy
+  // fence, commit) costs about as much as its copies for conv2's short 64-column
+  // tiles: two K blocks per stage there (and in E4M3 conv3) halve it.  Split
+  // conv2/conv3 and bf16 conv3 measured faster with single K blocks waited for in
+  // pairs, fc1 with single ones.
+  static constexpr int KPS = ((LAYER == 2 && !SPLIT) || (LAYER == 3 && FP8)) ? 2 : 1;
+  static constexpr int FGROUP = ((LAYER == 2 || LAYER == 3) && KPS == 1) ? 2 : 1;
+  static constexpr int NKS = (KB + KPS - 1) / KPS;  // stages per tile
+  static constexpr int SUB_BYTES = A_BYTES * (A_LO ? 2 : 1) + (B_RES ? 0 : B_ROWS * 128);  // one K block
+  static constexpr int STAGE_BYTES = KPS * SUB_BYTES;
   static constexpr int STAGES_RAW = (192 * 1024 - RES_BYTES) / STAGE_BYTES;
   // fused conv1 fills all KB stages of a tile together: a ring of RING tiles
   static constexpr int RING = LAYER == 1 ? (8 / KB >= 2 ? 8 / KB : 2) : 1;
-  static constexpr int STAGES = LAYER == 1 ? RING * KB : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
+  static constexpr int STAGES = LAYER == 1 ? RING * KB : (STAGES_RAW > 8 / KPS ? 8 / KPS : STAGES_RAW);
   // fused conv1: re-zero lists (8 x 256 entries) + node-state ring (3 tiles x 2 nodes)
   static constexpr int DIRTY_BYTES = LAYER == 1 ? 2 * 4 * 256 * 4 + 3 * 2 * 80 : 0;
   // conv1 (32-column tiles, the lightest epilogue) runs two epilogue warpgroups
@@ -315,7 +325,7 @@ struct Cfg {
   static constexpr int NUM_ACC = (8 * ACC_N <= 512) ? 8 : ((4 * ACC_N <= 512) ? 4 : 2);
   static constexpr uint32_t TMEM_COLS = NUM_ACC * ACC_N < 32 ? 32 : NUM_ACC * ACC_N;
   static_assert(STAGES >= 2, "pipeline depth");
-  static_assert(RES_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0, "1024-byte aligned tiles");
+  static_assert(RES_BYTES % 1024 == 0 && SUB_BYTES % 1024 == 0, "1024-byte aligned tiles");
   static_assert(ACC_N <= 256 && TMEM_COLS <= 512, "accumulator");
   static_assert(SMEM <= 232448, "shared memory");
 };
@@ -385,7 +395,9 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
     TS = 1;
     TE = T0 + per < p.num_tiles ? T0 + per : p.num_tiles;
   }
-  auto sB_of = [&](int s) { return sA_of(s) + C::A_BYTES * (C::A_LO ? 2 : 1); };
+  // K block kk of stage s: A (hi, then lo in split mode), then the weight tile unless resident
+  auto sub_of = [&](int s, int kk) { return sA_of(s) + uint32_t(kk) * C::SUB_BYTES; };
+  auto sB_of = [&](int s, int kk) { return sub_of(s, kk) + C::A_BYTES * (C::A_LO ? 2 : 1); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -558,18 +570,16 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
             rowoff[i] = (long long)m * kKF;
           }
         }
-        for (int kb = 0; kb < KB; ++kb) {
+        for (int ks = 0; ks < C::NKS; ++ks) {
           const int s = g % S;
           const uint32_t round = uint32_t(g / S);
           if (!wait_bar(empty_bar(s), (round & 1u) ^ 1u, abort_flag, p.d_err, 1)) {
             ok = false;
             break;
           }
-          const uint32_t sA = sA_of(s);
-          const uint32_t sAlo = sA + C::A_BYTES;
-          const uint32_t sB = sB_of(s);
-          const uint32_t sBlo = sB + C::B_BYTES;
           if (LAYER == 1) {
+            const int kb = ks;  // one K block per stage
+            const uint32_t sA = sA_of(s);
             // conv1 from uint8 frame stacks: 8 pixels of kernel row ch (bf16), or
             // 16 pixels of kernel rows 2(ch%4), 2(ch%4)+1 of slot 2 kb + ch/4 (E4M3)
 #pragma unroll
@@ -595,6 +605,14 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
             ++g;
             continue;
           }
+#pragma unroll
+          for (int kk = 0; kk < C::KPS; ++kk) {
+          const int kb = ks * C::KPS + kk;
+          if (kb >= KB) break;
+          const uint32_t sA = sub_of(s, kk);
+          const uint32_t sAlo = sA + C::A_BYTES;
+          const uint32_t sB = sB_of(s, kk);
+          const uint32_t sBlo = sB + C::B_BYTES;
           // A tile: im2col rows of the NHWC activation map
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -635,6 +653,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
             cp_async16(sB + off, static_cast<const uint8_t *>(p.b_hi) + eb);
             if (SPLIT) cp_async16(sBlo + off, static_cast<const uint8_t *>(p.b_lo) + eb);
           }
+          }
           cp_async_arrive(full_bar(s));
           ++g;
         }
@@ -655,14 +674,14 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
         tc_fence_after();
         const uint32_t d = tmem + uint32_t(acc * C::ACC_N);
         // cp.async-fed stages were written through the generic proxy and the
-        // hardware arrival carries no proxy fence: one fence per F stages orders
-        // them before the tensor core's async-proxy reads.  conv1's producers
-        // write with st.shared and fence themselves.
+        // hardware arrival carries no proxy fence: one fence per group of F
+        // stages orders them before the tensor core's async-proxy reads.  conv1's
+        // producers write with st.shared and fence themselves.
         constexpr bool kFence = LAYER != 1;
-        constexpr int F = (kFence && S >= 4) ? 2 : 1;
+        constexpr int F = (kFence && S >= 4) ? C::FGROUP : 1;
         constexpr bool kTileCommit = LAYER == 1 && FUSED;  // one commit frees the tile's stages
-        for (int kb0 = 0; kb0 < KB && ok; kb0 += F) {
-          const int nf = (KB - kb0) < F ? (KB - kb0) : F;
+        for (int ks0 = 0; ks0 < C::NKS && ok; ks0 += F) {
+          const int nf = (C::NKS - ks0) < F ? (C::NKS - ks0) : F;
           for (int f = 0; f < nf; ++f) {
             const int sf = (g + f) % S;
             if (!wait_bar(full_bar(sf), uint32_t((g + f) / S) & 1u, abort_flag, p.d_err, 3)) {
@@ -674,11 +693,15 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
           if (kFence) fence_proxy_async();
           tc_fence_after();
           for (int f = 0; f < nf; ++f) {
-          const int kb = kb0 + f;
+          const int ks = ks0 + f;
           const int s = g % S;
-          const uint32_t sA = sA_of(s);
+#pragma unroll
+          for (int kk = 0; kk < C::KPS; ++kk) {
+          const int kb = ks * C::KPS + kk;
+          if (kb >= KB) break;
+          const uint32_t sA = sub_of(s, kk);
           const uint32_t sAlo = sA + C::A_BYTES;
-          const uint32_t sB = C::B_RES ? res + uint32_t(kb) * (C::B_ROWS * 128) : sB_of(s);
+          const uint32_t sB = C::B_RES ? res + uint32_t(kb) * (C::B_ROWS * 128) : sB_of(s, kk);
           const uint32_t sBlo = sB + C::B_BYTES;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {  // K = 16 bf16 / 32 E4M3 = 32 bytes per instruction
@@ -699,7 +722,8 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
               }
             }
           }
-          if (!kTileCommit || kb == KB - 1) mma_commit(empty_bar(s));  // stage(s) free once read
+          }
+          if (!kTileCommit || ks == C::NKS - 1) mma_commit(empty_bar(s));  // stage(s) free once read
           ++g;
           }
         }
