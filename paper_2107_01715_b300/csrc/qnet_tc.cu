@@ -297,10 +297,10 @@ struct Cfg {
   // fences) as one group.  A stage's hand-off (barrier wait, arrivals, proxy
   // fence, commit) costs about as much as its copies for the short 64-column
   // conv2/conv3 tiles: two K blocks per stage there halve it.  Split conv2/conv3
-  // (48 KB K blocks) measured faster with single K blocks waited for in pairs,
-  // fc1 with single ones.
+  // (48 KB K blocks) measured faster with single K blocks waited for in pairs
+  // (and E4M3 with its two-K-block stages in pairs), fc1 with single ones.
   static constexpr int KPS = ((LAYER == 2 || LAYER == 3) && !SPLIT) ? 2 : 1;
-  static constexpr int FGROUP = ((LAYER == 2 || LAYER == 3) && KPS == 1) ? 2 : 1;
+  static constexpr int FGROUP = ((LAYER == 2 || LAYER == 3) && (KPS == 1 || FP8)) ? 2 : 1;
   static constexpr int NKS = (KB + KPS - 1) / KPS;  // stages per tile
   static constexpr int SUB_BYTES = A_BYTES * (A_LO ? 2 : 1) + (B_RES ? 0 : B_ROWS * 128);  // one K block
   static constexpr int STAGE_BYTES = KPS * SUB_BYTES;
