@@ -56,6 +56,10 @@ bool tc_has_partial(const TcWeights *w);
 // the tensor-core weights.
 int launch_leaf_conv1(int mode, const bcts_state *states, int64_t n, const ZLeaf &zl, const float *T,
                       const float *W3, float out_scale, void *out_hi, void *out_lo, cudaStream_t st);
+// The parents' partial maps (FP32, no ReLU) from the sprite tables of weight
+// channels 0-2 (T [3][4][2][2][32] and W [3][64][32] first in the tables).
+int launch_partial_map(const bcts_state *states, int64_t n, const float *T, const float *W, const float *bias,
+                       float *Z, cudaStream_t st);
 int tc_conv1_partial(const TcWeights *w, const bcts_state *states, int64_t n, float *z, cudaStream_t st, int *d_err);
 
 // search.cu backup kernels

@@ -19,6 +19,10 @@
 // leaf, then overwrites the rows next to the leaves' objects with ReLU(Z + term).
 // Output formats as the tensor-core layers expect them: bf16 (BF16), bf16 hi + lo
 // (FP32-class split) or E4M3 scaled by the conv1 map's activation scale (FP8).
+//
+// The parents' partial maps are formed the same way: Z is b on every row and,
+// on the (at most 48) rows next to an object of the parent's slots 1-3, b plus
+// those slots' terms with weight channels 0-2.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -35,6 +39,9 @@ constexpr int kSliceF4 = kSliceRows * kC1 / 4;      // 640 float4 per slice
 constexpr int kF4PerThread = kSliceF4 / kThreads;   // 4
 constexpr int kLeaves = 36;                         // leaves per block
 constexpr int kCands = 16;                          // (object, dy, dx) per leaf
+constexpr int kRowWords = (kSliceRows + 31) / 32;   // per-node bitmap of a slice's listed rows
+constexpr int kSlotF4 = kObj * 2 * 2 * (kC1 / 4);   // one weight channel's table as float4s
+constexpr int kSlotW = 64 * kC1;                    // one weight channel's [64][32] floats
 static_assert(kP1 % kSliceRows == 0 && kSliceF4 % kThreads == 0, "slice geometry");
 
 struct Args {
@@ -191,7 +198,79 @@ __global__ void __launch_bounds__(kThreads) leaf_conv1_kernel(const Args p) {
   }
 }
 
+// A parent's partial map Z = W_0 * slot1 + W_1 * slot2 + W_2 * slot3 + b, FP32,
+// no ReLU; same block layout as the leaves.  T and W hold weight channels 0-2
+// first.
+__global__ void __launch_bounds__(kThreads) partial_map_kernel(const bcts_state *__restrict__ states, int64_t n,
+                                                               const float *__restrict__ T,
+                                                               const float *__restrict__ W,
+                                                               const float *__restrict__ bias, float *__restrict__ Z) {
+  __shared__ float4 Ts[3 * kSlotF4];
+  __shared__ __align__(16) int16_t cells[kLeaves][3][kObj][2];  // the parent's slots 1-3: bytes 16..63 of a state
+  __shared__ uint32_t listed[kLeaves][kRowWords];
+  __shared__ uint32_t hits[kLeaves * 3 * kCands];  // (node << 16) | patch row
+  __shared__ int nhits;
+  const int t = threadIdx.x;
+  const int slice = blockIdx.y;
+  const int64_t l0 = int64_t(blockIdx.x) * kLeaves;
+  const int nl = n - l0 < kLeaves ? int(n - l0) : kLeaves;
+  for (int i = t; i < 3 * kSlotF4; i += kThreads) Ts[i] = __ldg(reinterpret_cast<const float4 *>(T) + i);
+  for (int i = t; i < nl * 3; i += kThreads)
+    reinterpret_cast<uint4 *>(&cells[0][0][0][0])[i] =
+        __ldg(reinterpret_cast<const uint4 *>(states + l0 + i / 3) + 1 + (i % 3));
+  for (int i = t; i < kLeaves * kRowWords; i += kThreads) (&listed[0][0])[i] = 0u;
+  if (t == 0) nhits = 0;
+  __syncthreads();
+  // the rows of this slice next to an object of slots 1-3, each listed once
+  for (int i = t; i < nl * 3 * kCands; i += kThreads) {
+    const int j = i / (3 * kCands), c = i % (3 * kCands), h = c >> 4, k = (c >> 2) & 3;
+    const int ox = cells[j][h][k][0] - (c & 1), oy = cells[j][h][k][1] - ((c >> 1) & 1);
+    if (ox < 0 || ox > 19 || oy < 0 || oy > 19) continue;
+    const int r = oy * 20 + ox - slice * kSliceRows;
+    if (r < 0 || r >= kSliceRows) continue;
+    const uint32_t bit = 1u << (r & 31);
+    if (atomicOr(&listed[j][r >> 5], bit) & bit) continue;
+    hits[atomicAdd(&nhits, 1)] = (uint32_t(j) << 16) | uint32_t(r + slice * kSliceRows);
+  }
+  // every row: b (a thread's four float4s share one channel group)
+  float4 *Z4 = reinterpret_cast<float4 *>(Z);
+  const float4 b4 = __ldg(reinterpret_cast<const float4 *>(bias) + (t & 7));
+  for (int j = 0; j < nl; ++j) {
+    const int64_t fb = (l0 + j) * int64_t(kP1 * kC1 / 4) + slice * kSliceF4;
+#pragma unroll
+    for (int i = 0; i < kF4PerThread; ++i) Z4[fb + i * kThreads + t] = b4;
+  }
+  __syncthreads();  // orders the overwrites below after every thread's first write
+  const int nh = nhits;
+  for (int i = t; i < nh * 8; i += kThreads) {
+    const uint32_t hv = hits[i >> 3];
+    const int c4 = i & 7, j = int(hv >> 16), r = int(hv & 0xFFFFu);
+    float4 v = __ldg(reinterpret_cast<const float4 *>(bias) + c4);
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {
+      int cx[kObj], cy[kObj];
+#pragma unroll
+      for (int k = 0; k < kObj; ++k) {
+        cx[k] = cells[j][h][k][0];
+        cy[k] = cells[j][h][k][1];
+      }
+      add4(v, patch_term(cx, cy, r % 20, r / 20, c4, Ts + h * kSlotF4, W + h * kSlotW));
+    }
+    Z4[(l0 + j) * int64_t(kP1 * kC1 / 4) + r * 8 + c4] = v;
+  }
+}
+
 }  // namespace
+
+int launch_partial_map(const bcts_state *states, int64_t n, const float *T, const float *W, const float *bias,
+                       float *Z, cudaStream_t st) {
+  if (n <= 0) return BCTS_OK;
+  if (n > 0x7FFFFFFFLL * kLeaves) return BCTS_EINVAL;
+  const dim3 grid(unsigned((n + kLeaves - 1) / kLeaves), kSlices);
+  ProfScope ps(K_CONV1_PARTIAL, st);
+  partial_map_kernel<<<grid, kThreads, 0, st>>>(states, n, T, W, bias, Z);
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
 
 int launch_leaf_conv1(int mode, const bcts_state *states, int64_t n, const ZLeaf &zl, const float *T,
                       const float *W3, float out_scale, void *out_hi, void *out_lo, cudaStream_t st) {

@@ -949,9 +949,9 @@ struct TcWeights {
   const float *colscale[4] = {};  // FP8: weight scale of each output channel x input activation scale
   float out_inv_scale[4] = {};    // FP8: 1 / activation scale of each layer's output map
   const float *f2w = nullptr, *f2b = nullptr;
-  // leaf conv1 (the newest slot's weights W_3 as this precision multiplies them):
-  const float *leafT = nullptr;   // [4 objects][2 dy][2 dx][32] palette x W_3 summed over the sprite
-  const float *leafW3 = nullptr;  // [64 patch pixels][32]
+  // conv1 from the sprite tables (the weights as this precision multiplies them):
+  const float *c1T = nullptr;  // [4 channels][4 objects][2 dy][2 dx][32] palette x W_c summed over the sprite
+  const float *c1W = nullptr;  // [4 channels][64 patch pixels][32]
 };
 
 namespace {
@@ -1032,9 +1032,9 @@ int tc_weights_create(const float *w, int A, int precision, const float *act_sca
   const size_t off_f2b = total;
   total += align256(size_t(A) * 4);
   const size_t off_T = total;
-  total += align256(size_t(kObj) * 4 * kC1 * 4);
+  total += align256(size_t(kHist) * kObj * 4 * kC1 * 4);
   const size_t off_W3 = total;
-  total += align256(size_t(64) * kC1 * 4);
+  total += align256(size_t(kHist) * 64 * kC1 * 4);
   std::vector<uint8_t> h(total, 0);
   TcWeights *t = new TcWeights();
   for (int l = 0; l < 4; ++l) {
@@ -1066,34 +1066,38 @@ int tc_weights_create(const float *w, int A, int precision, const float *act_sca
     std::memcpy(h.data() + off[8 + l], bsrc[l], R * 4);
   }
   {
-    // W_3 (conv1 weights of the newest slot, K = 192 + ky * 8 + kx) as this
-    // precision's leaf layer multiplies them, and the per-object sprite sums
-    float *W3 = reinterpret_cast<float *>(h.data() + off_W3);  // [64][32]
-    for (int c = 0; c < kC1; ++c)
-      for (int k = 0; k < 64; ++k) {
-        float w;
-        if (precision == BCTS_PREC_FP32) {
-          w = src[0][c * 256 + 192 + k];
-        } else if (fp8) {
-          const uint8_t code = h[off[0] + size_t(c) * kpad[0] + 192 + k];
-          w = e4m3_value(code) * reinterpret_cast<const float *>(h.data() + off[12])[c];
-        } else {
-          w = tc::bf2f(reinterpret_cast<const uint16_t *>(h.data() + off[0])[c * 256 + 192 + k]);
-        }
-        W3[k * kC1 + c] = w;
-      }
-    float *T = reinterpret_cast<float *>(h.data() + off_T);  // [object][dy][dx][32]
-    for (int o = 0; o < kObj; ++o)
-      for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx)
-          for (int c = 0; c < kC1; ++c) {
-            double acc = 0.0;
-            for (int sy = 0; sy < 4; ++sy)
-              for (int sx = 0; sx < 4; ++sx)
-                if ((kSprites >> (16 * o + 4 * sy + sx)) & 1ull)
-                  acc += double(W3[((4 * dy + sy) * 8 + 4 * dx + sx) * kC1 + c]);
-            T[((o * 2 + dy) * 2 + dx) * kC1 + c] = float(acc * double((kPalette >> (8 * o)) & 0xFFu));
+    // conv1's weights per input channel (K = channel * 64 + ky * 8 + kx) as this
+    // precision multiplies them, and the per-object sprite sums
+    float *Ws = reinterpret_cast<float *>(h.data() + off_W3);  // [channel][64][32]
+    for (int hc = 0; hc < kHist; ++hc)
+      for (int c = 0; c < kC1; ++c)
+        for (int k = 0; k < 64; ++k) {
+          const int kk = hc * 64 + k;
+          float w;
+          if (precision == BCTS_PREC_FP32) {
+            w = src[0][c * 256 + kk];
+          } else if (fp8) {
+            const uint8_t code = h[off[0] + size_t(c) * kpad[0] + kk];
+            w = e4m3_value(code) * reinterpret_cast<const float *>(h.data() + off[12])[c];
+          } else {
+            w = tc::bf2f(reinterpret_cast<const uint16_t *>(h.data() + off[0])[c * 256 + kk]);
           }
+          Ws[(hc * 64 + k) * kC1 + c] = w;
+        }
+    float *T = reinterpret_cast<float *>(h.data() + off_T);  // [channel][object][dy][dx][32]
+    for (int hc = 0; hc < kHist; ++hc)
+      for (int o = 0; o < kObj; ++o)
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dx = 0; dx < 2; ++dx)
+            for (int c = 0; c < kC1; ++c) {
+              double acc = 0.0;
+              for (int sy = 0; sy < 4; ++sy)
+                for (int sx = 0; sx < 4; ++sx)
+                  if ((kSprites >> (16 * o + 4 * sy + sx)) & 1ull)
+                    acc += double(Ws[(hc * 64 + (4 * dy + sy) * 8 + 4 * dx + sx) * kC1 + c]);
+              T[(((hc * kObj + o) * 2 + dy) * 2 + dx) * kC1 + c] =
+                  float(acc * double((kPalette >> (8 * o)) & 0xFFu));
+            }
   }
   std::memcpy(h.data() + off_f2w, f2w, size_t(A) * 512 * 4);
   std::memcpy(h.data() + off_f2b, f2b, size_t(A) * 4);
@@ -1116,8 +1120,8 @@ int tc_weights_create(const float *w, int A, int precision, const float *act_sca
   }
   t->f2w = reinterpret_cast<const float *>(b + off_f2w);
   t->f2b = reinterpret_cast<const float *>(b + off_f2b);
-  t->leafT = reinterpret_cast<const float *>(b + off_T);
-  t->leafW3 = reinterpret_cast<const float *>(b + off_W3);
+  t->c1T = reinterpret_cast<const float *>(b + off_T);
+  t->c1W = reinterpret_cast<const float *>(b + off_W3);
   *out = t;
   return BCTS_OK;
 }
@@ -1162,7 +1166,9 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
   };
   layer(0, states ? static_cast<const void *>(states) : static_cast<const void *>(frames), nullptr, a1, a1l);
   if (zl && states) {
-    rc = launch_leaf_conv1(MODE, states, n, *zl, w->leafT, w->leafW3, w->out_inv_scale[0], a1, a1l, st);
+    // the newest slot: weight channel 3
+    rc = launch_leaf_conv1(MODE, states, n, *zl, w->c1T + 3 * (kObj * 4 * kC1), w->c1W + 3 * (64 * kC1),
+                           w->out_inv_scale[0], a1, a1l, st);
   } else {
     rc = states ? tc::launch<1, MODE, true>(p, (long long)n * kP1, K_CONV1, st)
                 : tc::launch<1, MODE, false>(p, (long long)n * kP1, K_CONV1, st);
@@ -1193,21 +1199,11 @@ bool tc_has_partial(const TcWeights *w) {
   return w->precision == BCTS_PREC_FP32 || w->precision == BCTS_PREC_BF16 || w->precision == BCTS_PREC_FP8;
 }
 
-// Parent partial maps Z = W_0 * slot1 + W_1 * slot2 + W_2 * slot3 + b, FP32 [n][400][32].
+// Parent partial maps Z = W_0 * slot1 + W_1 * slot2 + W_2 * slot3 + b, FP32 [n][400][32],
+// from the sprite tables of weight channels 0-2.
 int tc_conv1_partial(const TcWeights *w, const bcts_state *states, int64_t n, float *z, cudaStream_t st, int *d_err) {
-  if (n <= 0) return BCTS_OK;
-  tc::GemmParams p{};
-  p.d_err = d_err;
-  p.a_hi = states;
-  p.b_hi = w->w_hi[0];
-  p.b_lo = w->w_lo[0];
-  p.bias = w->bias[0];
-  p.colscale = w->colscale[0];
-  p.out_hi = z;
-  if (w->precision == BCTS_PREC_FP32) return tc::launch<1, 1, true, 1>(p, (long long)n * kP1, K_CONV1_PARTIAL, st);
-  if (w->precision == BCTS_PREC_BF16) return tc::launch<1, 0, true, 1>(p, (long long)n * kP1, K_CONV1_PARTIAL, st);
-  if (w->precision == BCTS_PREC_FP8) return tc::launch<1, 2, true, 1>(p, (long long)n * kP1, K_CONV1_PARTIAL, st);
-  return BCTS_ENOKERNEL;
+  (void)d_err;
+  return launch_partial_map(states, n, w->c1T, w->c1W, w->bias[0], z, st);
 }
 
 }  // namespace bcts
