@@ -61,10 +61,10 @@ WORKLOADS = {
 L2_BYTES = 126 * 2 ** 20
 DTYPES = {"fp32": "f32 (bf16x3 split products, f32 accumulate)", "bf16": "bf16", "fp8": "e4m3", "fp32_simt": "f32"}
 # Tensor-core multiply-accumulates per node each kernel class executes (Nature-DQN layers;
-# conv1 over a whole 4-frame stack, or over three stack slots for a parent's partial map).
-# A leaf scored from its parent's partial map runs no contraction: its conv1 is a streaming
-# pass, ReLU(partial map + the newest slot's term), bound by its DRAM bytes alone.
-EXEC_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 400 * 32 * 192, "conv1_leaf": 0,
+# conv1 over a whole 4-frame stack for the roots and depth-1 nodes).  The parents' partial
+# maps and the leaves' conv1 run no contraction: streaming passes over the sprite tables,
+# bound by their DRAM bytes alone.
+EXEC_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 0, "conv1_leaf": 0,
              "conv2": 81 * 64 * 512, "conv3": 49 * 64 * 576, "fc1": 512 * 3136}
 # DRAM bytes per node of the leaf-level kernel classes, read + write, from the ncu captures
 # of the current kernels summarised in profiles/tc_gemm_layers_4roots_a18_d3.md and

@@ -258,26 +258,18 @@ constexpr int kBarBytes = 512;  // mbarriers, TMEM address, abort flag
 // with per-output-channel weight scales and per-layer activation scales.
 // A K block is always 128 bytes: 64 bf16 or 128 E4M3 elements (FP8 pads K to a
 // whole block with zero weights).
-// conv1 variants: V = 0 the full 4-channel convolution; V = 1 a parent's partial
-// map Z = W_0 * slot1 + W_1 * slot2 + W_2 * slot3 + b (FP32 out, no ReLU).  A
-// child's slots 0..2 are its parent's slots 1..3 (frame stacking) and the
-// convolution is linear, so a leaf's conv1 is ReLU(Z + W_3 * slot3), which the
-// streaming leaf kernel (leaf_conv1.cu) forms without a contraction.
-template <int LAYER, int MODE, int V = 0>
+// conv1 here is the full 4-channel convolution, for the roots and depth-1 nodes
+// (rendered from their states) and for materialised frame stacks.  The leaves'
+// conv1 and the parents' partial maps it starts from are streaming passes over
+// sprite tables (leaf_conv1.cu).  A 128-byte K block holds one history slot
+// (bf16) or two (E4M3: slots 2j, 2j + 1).
+template <int LAYER, int MODE>
 struct Cfg {
   using G = Geo<LAYER>;
   static constexpr bool SPLIT = MODE == 1, FP8 = MODE == 2;
   static constexpr int EB = FP8 ? 1 : 2;              // bytes per element
-  static_assert(V == 0 || LAYER == 1, "partial-map variants are conv1 only");
-  // A 128-byte K block holds one history slot (bf16) or two (E4M3: slots 2j, 2j + 1).
-  // V1 (a parent's partial map) multiplies weight channels 0-2 with the parent's
-  // slots 1-3.
-  static constexpr int SLOT0 = V == 1 ? 1 : 0;  // slot of K block 0 (first half)
   static constexpr int KB_FULL = FP8 ? (G::K + 127) / 128 : G::K / 64;
-  static constexpr int KB = V == 1 ? (FP8 ? 2 : 3) : KB_FULL;  // K blocks this kernel multiplies
-  // K steps (32 bytes each, four per K block) that carry data: E4M3 V1 uses only
-  // the first half of its last K block (slot 3 with weight channel 2)
-  static constexpr int JL = (FP8 && V == 1) ? 2 : 4;  // K steps of the last K block
+  static constexpr int KB = KB_FULL;  // K blocks per tile
   static constexpr int KPAD = KB_FULL * (128 / EB);  // stored weight row length in elements
   static constexpr bool A_LO = SPLIT && LAYER != 1;  // conv1's integer pixels are exact in bf16
   // Weights resident in shared memory for the whole kernel: conv1 (8-32 KB) and,
@@ -350,9 +342,9 @@ constexpr int kProdWarps = 8;
 constexpr int kProd = 32 * kProdWarps;  // producer threads
 constexpr int kEpiWarp0 = 8;
 
-template <int LAYER, int MODE, bool FUSED, int V = 0>
-__global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const GemmParams p) {
-  using C = Cfg<LAYER, MODE, V>;
+template <int LAYER, int MODE, bool FUSED>
+__global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const GemmParams p) {
+  using C = Cfg<LAYER, MODE>;
   constexpr int kMmaWarp = C::MMA_WARP;
   using G = Geo<LAYER>;
   constexpr bool SPLIT = C::SPLIT, FP8 = C::FP8;
@@ -508,7 +500,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
         for (int j = 0; j < KB; ++j) {
           uint32_t wrote = 0u;
           const uint32_t leaf = leaf0 + uint32_t(li);
-          const int slot = FP8 ? C::SLOT0 + 2 * j + (cc >> 2) : C::SLOT0 + j;
+          const int slot = FP8 ? 2 * j + (cc >> 2) : j;
           // the slot depends on the chunk (E4M3): read it from the state ring, not
           // from a runtime-indexed register array (which would live in local memory)
           const uint4 Pv = FP8 ? Ps[slot & 3] : P[slot & 3];
@@ -705,7 +697,6 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
           const uint32_t sBlo = sB + C::B_BYTES;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {  // K = 16 bf16 / 32 E4M3 = 32 bytes per instruction
-            if (kb == KB - 1 && j >= C::JL) continue;
             const uint32_t first = (kb != 0 || j != 0) ? 1u : 0u;
             const uint64_t a = sw128_desc(sA) + uint64_t(2 * j);
             const uint64_t b = sw128_desc(sB) + uint64_t(2 * j);
@@ -758,7 +749,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
     named_bar_sync(2, 128 * C::EPI_WG);
     uint8_t *stg = reinterpret_cast<uint8_t *>(bias_s + 2 * G::NTOT) + (warp - kEpiWarp0) * (32 * kStgRow);
     // output row bytes of one array (conv layers: whole rows; fc1: one 16-column chunk)
-    constexpr int ROWB = V == 1 ? kC1 * 4 : (LAYER == 4 ? 64 : (FP8 ? BN : BN * 2));
+    constexpr int ROWB = LAYER == 4 ? 64 : (FP8 ? BN : BN * 2);
     constexpr int SEGS = ROWB / 16;  // 16-byte segments per row
     static_assert(ROWB + 16 <= kStgRow && kC1 * 4 + 16 <= kStgRow, "staging row");
     // write the warp's 32 staged rows (ROWB bytes each) to dst rows of `stride` bytes
@@ -820,12 +811,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
             v[2 * e + 1] = add2(v[2 * e + 1], c1);
           }
         }
-        if constexpr (V == 1) {  // partial sum: no ReLU yet
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            *reinterpret_cast<float4 *>(stg + lane * kStgRow + j * 64 + e * 16) =
-                make_float4(v[2 * e].x, v[2 * e].y, v[2 * e + 1].x, v[2 * e + 1].y);
-        } else if constexpr (LAYER == 4) {
+        if constexpr (LAYER == 4) {
 #pragma unroll
           for (int e = 0; e < 4; ++e)
             *reinterpret_cast<float4 *>(stg + lane * kStgRow + e * 16) =
@@ -859,9 +845,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE, V>::THREADS, 1) tc_gemm(const
           *reinterpret_cast<uint4 *>(stg + lane * kStgRow + j * 32 + 16) = make_uint4(hh[4], hh[5], hh[6], hh[7]);
         }
       }
-      if constexpr (V == 1) {
-        flush(static_cast<uint8_t *>(p.out_hi), size_t(kC1) * 4, mw0);
-      } else if constexpr (LAYER != 4) {
+      if constexpr (LAYER != 4) {
         flush(static_cast<uint8_t *>(p.out_hi), size_t(ROWB), mw0);
         if constexpr (SPLIT) {
 #pragma unroll
@@ -899,14 +883,14 @@ int num_sms() {
   return sms;
 }
 
-template <int LAYER, int MODE, bool FUSED, int V = 0>
+template <int LAYER, int MODE, bool FUSED>
 int launch(const GemmParams &p0, long long M, int kind, cudaStream_t st) {
-  using C = Cfg<LAYER, MODE, V>;
+  using C = Cfg<LAYER, MODE>;
   if (M <= 0) return BCTS_OK;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm<LAYER, MODE, FUSED, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(tc_gemm<LAYER, MODE, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     C::SMEM);
   });
   if (attr_err != cudaSuccess) return BCTS_ECUDA;
@@ -919,7 +903,7 @@ int launch(const GemmParams &p0, long long M, int kind, cudaStream_t st) {
   p.num_tiles = int(tiles);
   const int grid = int(tiles < num_sms() ? tiles : num_sms());
   ProfScope ps(kind, st);
-  tc_gemm<LAYER, MODE, FUSED, V><<<grid, C::THREADS, C::SMEM, st>>>(p);
+  tc_gemm<LAYER, MODE, FUSED><<<grid, C::THREADS, C::SMEM, st>>>(p);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 
