@@ -133,10 +133,11 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 // each block stages W2 (A x 512, at most 36 KB) in shared memory once, with all
 // of a thread's loads in flight together (a loop that waits for each load before
 // its store costs an L2 round trip per element, tens of microseconds per launch),
-// and its warps then take nodes in turn.  Lane l holds h[4 l + 128 j .. + 3]; its 16
+// and its warps then take two nodes at a time, so each W2 value read from shared
+// memory serves both.  Lane l holds h[4 l + 128 j .. + 3] of each node; its 16
 // products per action are summed across the warp by a reduce-scatter butterfly
 // (31 shuffles for all actions at once), after which lane a holds q[a].
-__global__ void __launch_bounds__(256) fc2_max_kernel(const float *__restrict__ h, const float *__restrict__ W2,
+__global__ void __launch_bounds__(256, 2) fc2_max_kernel(const float *__restrict__ h, const float *__restrict__ W2,
                                                       const float *__restrict__ b2, int A, int64_t n,
                                                       float *__restrict__ q, float *__restrict__ maxq,
                                                       const uint8_t *__restrict__ node_A) {
@@ -162,54 +163,70 @@ __global__ void __launch_bounds__(256) fc2_max_kernel(const float *__restrict__ 
   const int lane = threadIdx.x & 31;
   const float bias = lane < A ? __ldg(b2 + lane) : 0.f;
   const int64_t nwarps = int64_t(gridDim.x) * (blockDim.x / 32);
-  for (int64_t node = int64_t(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5); node < n; node += nwarps) {
-    float x[16];
-    const float4 *hv = reinterpret_cast<const float4 *>(h + node * kF1);
+  // two nodes per warp pass: each W2 value read from shared memory serves both
+  for (int64_t g = int64_t(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5); 2 * g < n; g += nwarps) {
+    const int64_t node0 = 2 * g;
+    float x[2][16];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float4 t = __ldg(hv + lane + 32 * j);
-      x[4 * j] = t.x;
-      x[4 * j + 1] = t.y;
-      x[4 * j + 2] = t.z;
-      x[4 * j + 3] = t.w;
+    for (int u = 0; u < 2; ++u) {
+      const int64_t nd = node0 + u < n ? node0 + u : n - 1;
+      const float4 *hv = reinterpret_cast<const float4 *>(h + nd * kF1);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 t = __ldg(hv + lane + 32 * j);
+        x[u][4 * j] = t.x;
+        x[u][4 * j + 1] = t.y;
+        x[u][4 * j + 2] = t.z;
+        x[u][4 * j + 3] = t.w;
+      }
     }
-    float v[32];
+    float v[2][32];
 #pragma unroll
     for (int a = 0; a < 32; ++a) {
-      float s = 0.f;
+      float s0 = 0.f, s1 = 0.f;
       if (a < kMaxA && a < A) {
         const float4 *wa = reinterpret_cast<const float4 *>(w + a * kF1);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float4 c = wa[lane + 32 * j];
-          s = fmaf(x[4 * j], c.x, s);
-          s = fmaf(x[4 * j + 1], c.y, s);
-          s = fmaf(x[4 * j + 2], c.z, s);
-          s = fmaf(x[4 * j + 3], c.w, s);
+          s0 = fmaf(x[0][4 * j], c.x, s0);
+          s0 = fmaf(x[0][4 * j + 1], c.y, s0);
+          s0 = fmaf(x[0][4 * j + 2], c.z, s0);
+          s0 = fmaf(x[0][4 * j + 3], c.w, s0);
+          s1 = fmaf(x[1][4 * j], c.x, s1);
+          s1 = fmaf(x[1][4 * j + 1], c.y, s1);
+          s1 = fmaf(x[1][4 * j + 2], c.z, s1);
+          s1 = fmaf(x[1][4 * j + 3], c.w, s1);
         }
       }
-      v[a] = s;
+      v[0][a] = s0;
+      v[1][a] = s1;
     }
-    // reduce-scatter: at offset o a lane keeps the half of its remaining actions
-    // selected by its bit o and receives its partner's partial sums for them
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      const bool up = (lane & o) != 0;
+    for (int u = 0; u < 2; ++u) {
+      // reduce-scatter: at offset o a lane keeps the half of its remaining actions
+      // selected by its bit o and receives its partner's partial sums for them
 #pragma unroll
-      for (int i = 0; i < o; ++i) {
-        const float send = up ? v[i] : v[i + o];
-        const float keep = up ? v[i + o] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+          const float send = up ? v[u][i] : v[u][i + o];
+          const float keep = up ? v[u][i + o] : v[u][i];
+          v[u][i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
       }
-    }
-    const float s = v[0] + bias;  // q[node][lane] for lane < A
-    if (q && lane < A) q[node * A + lane] = s;
-    // node_A (batched form): the max runs over this node's own first node_A actions
-    const int An = node_A ? int(node_A[node]) : A;
-    float best = lane < An ? s : -INFINITY;
+      const int64_t node = node0 + u;
+      if (node >= n) break;
+      const float s = v[u][0] + bias;  // q[node][lane] for lane < A
+      if (q && lane < A) q[node * A + lane] = s;
+      // node_A (batched form): the max runs over this node's own first node_A actions
+      const int An = node_A ? int(node_A[node]) : A;
+      float best = lane < An ? s : -INFINITY;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (maxq && lane == 0) maxq[node] = best;
+      for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+      if (maxq && lane == 0) maxq[node] = best;
+    }
   }
 }
 
@@ -256,9 +273,9 @@ int launch_fc2_max(const float *h, const float *W2, const float *b2, int A, int6
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
   });
-  // persistent: four blocks per SM (36 KB of W2 each), never more blocks than node groups
-  const int64_t groups = (n + warps - 1) / warps;
-  const unsigned grid = unsigned(groups < int64_t(4) * sms ? groups : int64_t(4) * sms);
+  // persistent: two blocks per SM (36 KB of W2 each), never more warps than node pairs
+  const int64_t groups = ((n + 1) / 2 + warps - 1) / warps;
+  const unsigned grid = unsigned(groups < int64_t(2) * sms ? groups : int64_t(2) * sms);
   ProfScope ps(K_FC2, st);
   fc2_max_kernel<<<grid, warps * 32, 0, st>>>(h, W2, b2, A, n, q, maxq, node_A);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
