@@ -70,10 +70,10 @@ EXEC_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 0, "conv1_leaf": 0,
 # of the current kernels summarised in profiles/tc_gemm_layers_4roots_a18_d3.md and
 # profiles/leaf_conv1_4roots_a18_d3.md (launches over 23,328 leaves; traffic grows in
 # proportion to the nodes a launch processes).
-TRAFFIC_PER_NODE = {"fp32/conv2": 70907.0, "bf16/conv2": 34950.0, "fp8/conv2": 16989.0,
-                    "fp32/conv3": 31925.0, "bf16/conv3": 15336.0, "fp8/conv3": 7025.0,
-                    "fp32/fc1": 14600.0, "bf16/fc1": 7450.0, "fp8/fc1": 3545.0,
-                    "fp32/conv1_leaf": 53946.0, "bf16/conv1_leaf": 27188.0, "fp8/conv1_leaf": 13747.0}
+TRAFFIC_PER_NODE = {"fp32/conv2": 70875.0, "bf16/conv2": 34950.0, "fp8/conv2": 16997.0,
+                    "fp32/conv3": 31911.0, "bf16/conv3": 15315.0, "fp8/conv3": 7010.0,
+                    "fp32/fc1": 14609.0, "bf16/fc1": 7429.0, "fp8/fc1": 3539.0,
+                    "fp32/conv1_leaf": 53939.0, "bf16/conv1_leaf": 27170.0, "fp8/conv1_leaf": 13745.0}
 
 
 def layer_model(cls, precision, A):
