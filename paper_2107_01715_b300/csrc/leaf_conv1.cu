@@ -3,8 +3,8 @@
 // Frame stacking (Sec. 5) makes a child's history slots 0-2 its parent's slots
 // 1-3, and conv1 is linear in its input channels, so a leaf's pre-activation is
 // its parent's partial map Z = W_0 * slot1 + W_1 * slot2 + W_2 * slot3 + b
-// (computed once per parent on the tensor cores) plus the term W_3 * slot3 of
-// its own newest frame.  That frame holds nothing but the four 4 x 4 sprites, so
+// (computed once per parent, by the second pass below) plus the term W_3 * slot3
+// of its own newest frame.  That frame holds nothing but the four 4 x 4 sprites, so
 // the term is zero outside the (at most 16) 8 x 8 stride-4 patches that cover an
 // object's cell, and inside one it is the sum, over the objects in the patch, of
 // T[k][dy][dx] = palette_k x (W_3 summed over sprite k's set pixels placed at cell

@@ -375,10 +375,8 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto sA_of = [&](int s) { return stage0 + uint32_t(s) * C::STAGE_BYTES; };
   // Tile schedule, the same for every role: CTA b takes tiles T0, T0 + TS, ...
-  // below TE.  Grid-stride, or one contiguous range per CTA (CONTIG): then the
-  // tiles of a parent's children (which all read that parent's partial map) run
-  // on one SM and the map is read from L1 rather than once per child from L2,
-  // and consecutive conv2/conv3 tiles re-read each other's input rows while they
+  // below TE.  Grid-stride, or one contiguous range per CTA (CONTIG): then
+  // consecutive conv2/conv3 tiles re-read each other's input rows while they
   // are still in L2.
   int T0 = blockIdx.x, TS = gridDim.x, TE = p.num_tiles;
   if (C::CONTIG) {
