@@ -53,6 +53,9 @@ WORKLOADS = {
                    name="pruned search: 32 roots, |A|=18, d=4, 32 nodes kept per root action and level, FP32"),
     "dnn": dict(n=16, A=10, d=5, gamma=0.99, c=1.0, precision="fp32",
                 name="DNN forward model (Sec. 4): 16 roots, |A|=10, d=5, 100-wide state, 3 hidden layers of 100, FP32"),
+    "stream": dict(n=1 << 20, A=18, frames=100_000, gamma=0.99, c=1.0, precision="fp32",
+                   name="streaming kernels alone: Alg. 1's expansion of 1,048,576 parents x |A|=18 "
+                        "(bcts_expand) and the renderer on 100,000 states (bcts_render)"),
     "serving": dict(n=1024, A=18, d=4, gamma=0.99, c=1.0, precision="bf16", rate=500.0, seconds=4.0,
                     budget=120 << 30,
                     name="serving form: Poisson requests from 1024 episodes, d in {2,3,4}, |A|=18, BF16, "
@@ -448,6 +451,70 @@ def run_pruned(args, wl):
             "cpu_baseline": None, "clocks": _clock_line(clk, pk)}
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def run_stream(args, wl):
+    """The HBM-bound kernels on their own, at sizes where bandwidth rather than launch
+    latency decides: the expansion (one thread per child: read the parent's 80-byte
+    state and R, write the child's state and R) through bcts_expand, and the renderer
+    (read a state, write its 28,224-byte frame stack) through bcts_render.  Inside a
+    search both run on the levels' node counts (0.5 % of the default step); here each
+    is timed alone with CUDA events, inputs and outputs larger than L2."""
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2107_01715_b300 import bcts
+    P, A = wl["n"], wl["A"]
+    F = min(wl["frames"], P // 10)  # rendered from the first children (a reduced --roots case shrinks both)
+    base = inputs.root_states(range(rank * 4096, rank * 4096 + 4096))
+    parents = np.resize(base, P)  # 4,096 seeded states repeated: the kernels' work does not depend on repeats
+    d_par = torch.from_numpy(parents.view(np.uint8).copy()).to(dev)
+    d_parR = torch.zeros(P, dtype=torch.float32, device=dev)
+    d_child = torch.empty(P * A * 80, dtype=torch.uint8, device=dev)
+    d_childR = torch.empty(P * A, dtype=torch.float32, device=dev)
+    d_frames = torch.empty(F * inputs.FRAME_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    reps = max(1, min(args.steps, 20))
+    ops = {"expand": (lambda: bcts.bcts_expand(d_par, d_parR, P, A, 0.99, d_child, d_childR, None, stream),
+                      P * (80 + 4) + P * A * (80 + 4), P * A, "children"),
+           "render": (lambda: bcts.bcts_render(d_child, F, d_frames, stream),
+                      F * (80 + inputs.FRAME_BYTES), F, "frame stacks")}
+    pk, pk_kind = peaks()
+    out = {}
+    with torch.cuda.stream(stream):
+        with ClockSampler(local) as clk:
+            for name, (fn, nbytes, units, unit_name) in ops.items():
+                for _ in range(args.warmup):
+                    fn()
+                stream.synchronize()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+                barrier(world)
+                for i in range(reps):
+                    ev[i][0].record(stream)
+                    fn()
+                    ev[i][1].record(stream)
+                stream.synchronize()
+                ms = max_over_ranks(world, sum(a.elapsed_time(b) for a, b in ev) / reps, dev)
+                ach = nbytes / (ms / 1e3) / 1e9
+                out[name] = {"avg_launch_ms": ms, "algorithmic_bytes_per_launch": nbytes, "units_per_launch": units,
+                             "unit": unit_name, "rate_per_s": world * units / (ms / 1e3),
+                             "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                          "frac": ach / pk["hbm_gbs"],
+                                          "peak_note": f"STREAM-style copy bandwidth (of {pk_kind})"}}
+    if rank != 0:
+        return
+    e = out["expand"]
+    line = {"metric": "expansion children/s and render frame stacks/s (the search's HBM-bound kernels alone)",
+            "value": e["rate_per_s"], "unit": "children/s", "n_gpus": world, "steps": reps, "warmup": args.warmup,
+            "ms_per_step": e["avg_launch_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int16 states, uint8 frames", "data": "synthetic",
+            "config": {"workload": wl["name"], "parents": P, "A": A, "render_states": F,
+                       "l2": "no flush: every launch reads and writes more than the 126 MB L2"},
+            "roofline": dict(e["roofline"], kernel="expand_kernel"), "kernels": out,
+            "gpu_launches": 2 * (reps + args.warmup), "clocks": clk.summary(pk.get("sm_max_mhz", 2032.0)),
+            "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
 
 
 def run_sweep(args, wl):
@@ -907,6 +974,8 @@ def main():
         run_pruned(args, wl)
     elif args.workload == "sweep":
         run_sweep(args, wl)
+    elif args.workload == "stream":
+        run_stream(args, wl)
     else:
         run_ours(args, wl)
 

@@ -107,26 +107,37 @@ __host__ __device__ __forceinline__ int sprite_step(const bcts_state &s, int a, 
   return clampi(reward, -1, 1);
 }
 
-__global__ void __launch_bounds__(256) expand_kernel(const uint4 *__restrict__ parents,
-                                                     const float *__restrict__ parent_R, uint32_t n_child,
-                                                     int A, float gamma_pow, uint4 *__restrict__ children,
-                                                     float *__restrict__ child_R,
-                                                     int8_t *__restrict__ child_reward) {
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_child) return;
-  const uint32_t p = c / uint32_t(A);
-  const int a = int(c - p * uint32_t(A));
-  StateRegs in, out;
+constexpr int kExpandThreads = 256;
+
+__global__ void __launch_bounds__(kExpandThreads) expand_kernel(const uint4 *__restrict__ parents,
+                                                                const float *__restrict__ parent_R, uint32_t n_child,
+                                                                int A, float gamma_pow, uint4 *__restrict__ children,
+                                                                float *__restrict__ child_R,
+                                                                int8_t *__restrict__ child_reward) {
+  // the block's children pass through shared memory, so that their 80-byte
+  // states leave as whole consecutive 16-byte chunks (a thread's own five
+  // stores would each touch 32 scattered half sectors)
+  __shared__ uint4 stage[kExpandThreads * 5];
+  const uint32_t c0 = blockIdx.x * kExpandThreads;
+  const uint32_t c = c0 + threadIdx.x;
+  if (c < n_child) {
+    const uint32_t p = c / uint32_t(A);
+    const int a = int(c - p * uint32_t(A));
+    StateRegs in, out;
 #pragma unroll
-  for (int i = 0; i < 5; ++i) in.v[i] = __ldg(parents + size_t(p) * 5 + i);
-  const int r = sprite_step(in.s, a, out.s);
+    for (int i = 0; i < 5; ++i) in.v[i] = __ldg(parents + size_t(p) * 5 + i);
+    const int r = sprite_step(in.s, a, out.s);
 #pragma unroll
-  for (int i = 0; i < 5; ++i) children[size_t(c) * 5 + i] = out.v[i];
-  if (child_R) {
-    const float base = parent_R ? __ldg(parent_R + p) : 0.0f;
-    child_R[c] = base + gamma_pow * float(r);
+    for (int i = 0; i < 5; ++i) stage[threadIdx.x * 5 + i] = out.v[i];
+    if (child_R) {
+      const float base = parent_R ? __ldg(parent_R + p) : 0.0f;
+      child_R[c] = base + gamma_pow * float(r);
+    }
+    if (child_reward) child_reward[c] = (int8_t)r;
   }
-  if (child_reward) child_reward[c] = (int8_t)r;
+  __syncthreads();
+  const uint32_t nb = n_child - c0 < uint32_t(kExpandThreads) ? n_child - c0 : uint32_t(kExpandThreads);
+  for (uint32_t i = threadIdx.x; i < nb * 5; i += kExpandThreads) children[size_t(c0) * 5 + i] = stage[i];
 }
 
 // Frame layout per state: [4 slots][84 rows][21 words]; word (h, y, cx) holds the
@@ -144,6 +155,16 @@ __global__ void __launch_bounds__(256) render_kernel(const uint4 *__restrict__ s
     const uint4 P = __ldg(states + st * 5 + h);        // pos[h][0..3][x,y], 16 bytes
     int ox[4], oy[4];
     unpack_slot(P, ox, oy);
+    // the chunk's words lie in pixel rows y0 .. y0 + 1 (21 words per row): most
+    // chunks' cell rows hold no object, and are background
+    const int y0 = int(w0 / kGrid), cy0 = y0 >> 2, cy1 = (y0 + 1) >> 2;
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < kObj; ++k) any |= oy[k] == cy0 || oy[k] == cy1;
+    if (!any) {
+      frames[q] = make_uint4(0u, 0u, 0u, 0u);
+      continue;
+    }
     uint32_t word[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
