@@ -5,7 +5,8 @@
 //                   and reward A times, advance the simulator with action a,
 //                   R += gamma^i r).  One thread per child; integer arithmetic only.
 //   render_kernel : the 4 x 84 x 84 uint8 frame stack of a state (Sec. 5 frame
-//                   stacking), one thread per 16 output bytes, 16-byte stores.
+//                   stacking), one block per history slot, one thread per 16
+//                   output bytes, 16-byte stores.
 //
 // The sprite environment (agent + reward + two hazards on a 21 x 21 grid) is the
 // stand-in for the Atari emulator the paper runs on the GPU (Sec. 4).
@@ -141,38 +142,40 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(const uint4 *__r
 }
 
 // Frame layout per state: [4 slots][84 rows][21 words]; word (h, y, cx) holds the
-// 4 pixels of cell cx in pixel row y.  A 16-byte chunk is 4 consecutive words.
-__global__ void __launch_bounds__(256) render_kernel(const uint4 *__restrict__ states, uint64_t n_chunks,
-                                                     uint4 *__restrict__ frames) {
-  constexpr uint32_t kChunksPerSlot = kPix * kPix / 16;  // 441
-  constexpr uint32_t kChunksPerState = kHist * kChunksPerSlot;
-  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n_chunks;
-       q += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t st = q / kChunksPerState;
-    const uint32_t j = uint32_t(q - st * kChunksPerState);
-    const uint32_t h = j / kChunksPerSlot;
-    const uint32_t w0 = (j - h * kChunksPerSlot) * 4;  // first word in the slot
-    const uint4 P = __ldg(states + st * 5 + h);        // pos[h][0..3][x,y], 16 bytes
+// 4 pixels of cell cx in pixel row y.  A 16-byte chunk is 4 consecutive words,
+// 441 chunks per slot.  One block per (state, slot): a thread's chunk position is
+// the same in every slot it renders, and the slot's four object cells are one
+// 16-byte load that all threads share.
+constexpr uint32_t kChunksPerSlot = kPix * kPix / 16;  // 441
+constexpr int kRenderThreads = 448;                    // >= 441, whole warps
+
+__global__ void __launch_bounds__(kRenderThreads) render_kernel(const uint4 *__restrict__ states, uint64_t n_slots,
+                                                                uint4 *__restrict__ frames) {
+  const uint32_t jc = threadIdx.x;  // chunk within the slot
+  if (jc >= kChunksPerSlot) return;
+  const uint32_t w0 = jc * 4;  // first word of the chunk
+  // the chunk's words lie in pixel rows y0 .. y0 + 1 (21 words per row)
+  const int y0 = int(w0 / kGrid), cy0 = y0 >> 2, cy1 = (y0 + 1) >> 2;
+  for (uint64_t b = blockIdx.x; b < n_slots; b += gridDim.x) {  // b = state * 4 + slot
+    const uint4 P = __ldg(states + (b >> 2) * 5 + (b & 3));  // pos[slot][0..3][x, y]
     int ox[4], oy[4];
     unpack_slot(P, ox, oy);
-    // the chunk's words lie in pixel rows y0 .. y0 + 1 (21 words per row): most
-    // chunks' cell rows hold no object, and are background
-    const int y0 = int(w0 / kGrid), cy0 = y0 >> 2, cy1 = (y0 + 1) >> 2;
+    // most chunks' cell rows hold no object, and are background
     bool any = false;
 #pragma unroll
     for (int k = 0; k < kObj; ++k) any |= oy[k] == cy0 || oy[k] == cy1;
-    if (!any) {
-      frames[q] = make_uint4(0u, 0u, 0u, 0u);
-      continue;
-    }
-    uint32_t word[4];
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (any) {
+      uint32_t word[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint32_t w = w0 + i;
-      const int y = int(w / kGrid), cx = int(w - uint32_t(y) * kGrid);
-      word[i] = render_word(ox, oy, cx, y);
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t w = w0 + i;
+        const int y = int(w / kGrid), cx = int(w - uint32_t(y) * kGrid);
+        word[i] = render_word(ox, oy, cx, y);
+      }
+      v = make_uint4(word[0], word[1], word[2], word[3]);
     }
-    frames[q] = make_uint4(word[0], word[1], word[2], word[3]);
+    frames[b * kChunksPerSlot + jc] = v;
   }
 }
 
@@ -194,17 +197,15 @@ int launch_expand(const bcts_state *parents, const float *parent_R, int64_t n_pa
 
 int launch_render(const bcts_state *states, int64_t n, uint8_t *frames, cudaStream_t stream) {
   if (n <= 0) return BCTS_OK;
-  const uint64_t n_chunks = uint64_t(n) * (kFrameBytes / 16);
-  const int threads = 256;
+  const uint64_t n_slots = uint64_t(n) * kHist;
   int sms = 148;
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t want = (n_chunks + threads - 1) / threads;
-  const uint64_t cap = uint64_t(sms) * 8 * 16;  // grid-stride beyond 16 waves
-  const unsigned blocks = unsigned(want < cap ? want : cap);
+  const uint64_t cap = uint64_t(sms) * 4 * 16;  // four blocks per SM, grid-stride beyond 16 waves
+  const unsigned blocks = unsigned(n_slots < cap ? n_slots : cap);
   ProfScope ps(K_RENDER, stream);
-  render_kernel<<<blocks, threads, 0, stream>>>(reinterpret_cast<const uint4 *>(states), n_chunks,
-                                                reinterpret_cast<uint4 *>(frames));
+  render_kernel<<<blocks, kRenderThreads, 0, stream>>>(reinterpret_cast<const uint4 *>(states), n_slots,
+                                                       reinterpret_cast<uint4 *>(frames));
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 
