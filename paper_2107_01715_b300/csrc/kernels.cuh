@@ -52,14 +52,16 @@ int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts
 bool tc_has_partial(const TcWeights *w);
 // leaf_conv1.cu: conv1 of n leaves (states) from their parents' partial maps, as
 // ReLU(Z + the newest slot's term).  mode: 0 BF16, 1 FP32-class split (bf16 hi +
-// lo), 2 E4M3 scaled by out_scale.  T [4][2][2][32] and W3 [64][32] as built with
-// the tensor-core weights.
+// lo), 2 E4M3 scaled by out_scale.  T [4 objects][2][2][32] and W3 [64][32]: the
+// newest slot's (weight channel 3's) part of the sprite tables built with the
+// tensor-core weights.
 int launch_leaf_conv1(int mode, const bcts_state *states, int64_t n, const ZLeaf &zl, const float *T,
                       const float *W3, float out_scale, void *out_hi, void *out_lo, cudaStream_t st);
 // The parents' partial maps (FP32, no ReLU) from the sprite tables of weight
 // channels 0-2 (T [3][4][2][2][32] and W [3][64][32] first in the tables).
 int launch_partial_map(const bcts_state *states, int64_t n, const float *T, const float *W, const float *bias,
                        float *Z, cudaStream_t st);
+// The parents' partial maps Z [n][400][32] FP32 with this context's tables.
 int tc_conv1_partial(const TcWeights *w, const bcts_state *states, int64_t n, float *z, cudaStream_t st, int *d_err);
 
 // search.cu backup kernels
