@@ -241,7 +241,6 @@ int sm_count() {
   return sms;
 }
 
-unsigned elem_blocks(int64_t n) { return unsigned((n + 255) / 256); }
 
 }  // namespace
 
