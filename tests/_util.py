@@ -47,3 +47,39 @@ def pi_o_decided(q0_row, tol):
     if q.size < 2:
         return True
     return q[-1] - q[-2] > 2 * tol * max(abs(q[-1]), 1.0)
+
+
+def golden_transitions():
+    """Rows of tests/golden/env_transitions.txt as integer lists (hand-derived
+    transitions: 16 inputs, 4 outputs, then the respawn cell of each hit object)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "env_transitions.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append([int(t) for t in line.split()])
+    return rows
+
+
+def golden_state(row):
+    """The state and action of a golden transition row."""
+    from paper_2107_01715_b300 import inputs
+    (ax, ay, x1, y1, vx1, vy1, x2, y2, vx2, vy2, x3, y3, vx3, vy3, a, tick) = row[:16]
+    s = inputs.make_state((ax, ay), [(x1, y1), (x2, y2), (x3, y3)],
+                          vels=[(vx1, vy1), (vx2, vy2), (vx3, vy3)], tick=tick)
+    return s, a
+
+
+def golden_expected_cells(row):
+    """{object k: (x, y)} after the step: the respawn cell of each hit object, the
+    moved cell of the others (objects 1-3; every golden row keeps them off walls)."""
+    (ax, ay, x1, y1, vx1, vy1, x2, y2, vx2, vy2, x3, y3, vx3, vy3, a, tick, eax, eay, er, hits) = row[:20]
+    resp = row[20:]
+    hit = [k for k in range(1, 4) if (hits >> k) & 1]
+    cells = {k: (x + vx, y + vy) for k, (x, y, vx, vy) in
+             zip(range(1, 4), ((x1, y1, vx1, vy1), (x2, y2, vx2, vy2), (x3, y3, vx3, vy3)))}
+    for k, x, y in zip(hit, resp[0::2], resp[1::2]):
+        cells[k] = (x, y)
+    return (eax, eay), er, cells

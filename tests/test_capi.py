@@ -95,3 +95,17 @@ def test_host_env_step_matches_oracle(binding, oracle_lib):
     assert hits > 0
     with pytest.raises(binding.BctsError):
         binding.bcts_env_step(states[0], 18)
+
+
+def test_host_env_step_matches_hand_derived_transitions(binding):
+    """bcts_env_step (the library's host copy of the simulator) against the hand-derived
+    transitions, respawn cells included."""
+    from tests._util import golden_expected_cells, golden_state, golden_transitions
+    for row in golden_transitions():
+        s, a = golden_state(row)
+        n, r = binding.bcts_env_step(s, a)
+        agent, er, cells = golden_expected_cells(row)
+        assert tuple(int(v) for v in n["pos"][3, 0]) == agent
+        assert r == er
+        for k, cell in cells.items():
+            assert tuple(int(v) for v in n["pos"][3, k]) == cell, (row, k)

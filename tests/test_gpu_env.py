@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2107_01715_b300 import inputs
-from tests._util import as_state_bytes
+from tests._util import as_state_bytes, golden_expected_cells, golden_state, golden_transitions
 
 pytestmark = pytest.mark.gpu
 
@@ -114,3 +114,27 @@ def test_render_large_batch_sampled(oracle_lib, dev):
         s, _ = oracle_lib.replay(roots[0], A, 3, int(idx), 0.99)
         got = fr[idx * 28224:(idx + 1) * 28224].cpu().numpy().reshape(4, 84, 84)
         assert np.array_equal(got, oracle_lib.render(s)), idx
+
+
+def test_expand_matches_hand_derived_transitions(dev):
+    """bcts_expand on the hand-derived transitions (tests/golden/env_transitions.txt):
+    the child of each golden state under its action carries the listed agent cell,
+    reward and respawn cells."""
+    torch, bcts = dev
+    A = 18
+    rows = golden_transitions()
+    parents = np.stack([golden_state(r)[0] for r in rows])
+    ch = torch.empty(len(rows) * A * 80, dtype=torch.uint8, device="cuda")
+    rew = torch.empty(len(rows) * A, dtype=torch.int8, device="cuda")
+    bcts.bcts_expand(_to_dev(torch, parents), None, len(rows), A, 1.0, ch, None, rew)
+    torch.cuda.synchronize()
+    st = as_state_bytes(ch, len(rows) * A)
+    rw = rew.cpu().numpy()
+    for i, row in enumerate(rows):
+        _, a = golden_state(row)
+        agent, er, cells = golden_expected_cells(row)
+        c = st[i * A + a]
+        assert tuple(int(v) for v in c["pos"][3, 0]) == agent
+        assert int(rw[i * A + a]) == er
+        for k, cell in cells.items():
+            assert tuple(int(v) for v in c["pos"][3, k]) == cell, (i, k)

@@ -79,18 +79,25 @@ def _parse_golden():
 
 @pytest.mark.parametrize("case", _parse_golden())
 def test_hand_derived_transitions(oracle_lib, case):
-    # ax ay  o1x o1y o1vx o1vy  o2x o2y o2vx o2vy  o3x o3y o3vx o3vy  action | ax' ay' reward hit-mask
-    (ax, ay, x1, y1, vx1, vy1, x2, y2, vx2, vy2, x3, y3, vx3, vy3, a, eax, eay, er, hits) = case
+    # ax ay  o1x o1y o1vx o1vy  o2x o2y o2vx o2vy  o3x o3y o3vx o3vy  action tick | ax' ay' reward hit-mask
+    # | respawn cell (x y) of each hit object, in object order
+    (ax, ay, x1, y1, vx1, vy1, x2, y2, vx2, vy2, x3, y3, vx3, vy3, a, tick, eax, eay, er, hits) = case[:20]
+    respawn = case[20:]
+    hit_objs = [k for k in range(1, 4) if (hits >> k) & 1]
+    assert len(respawn) == 2 * len(hit_objs), "one respawn cell per hit object"
     s = inputs.make_state((ax, ay), [(x1, y1), (x2, y2), (x3, y3)],
-                          vels=[(vx1, vy1), (vx2, vy2), (vx3, vy3)], tick=11)
+                          vels=[(vx1, vy1), (vx2, vy2), (vx3, vy3)], tick=tick)
     n, r = oracle_lib.env_step(s, a)
     assert _agent(n) == (eax, eay)
     assert r == er
+    assert int(n["tick"]) == tick + 1
     moved = [(x1 + vx1, y1 + vy1), (x2 + vx2, y2 + vy2), (x3 + vx3, y3 + vy3)]
+    cells = dict(zip(hit_objs, zip(respawn[0::2], respawn[1::2])))
     for k in range(1, 4):
         p = tuple(int(v) for v in n["pos"][3, k])
-        assert 0 <= p[0] <= 20 and 0 <= p[1] <= 20
-        if not (hits >> k) & 1:
+        if k in cells:
+            assert p == cells[k], (k, p, cells[k])  # the hand-evaluated respawn hash
+        else:
             assert p == moved[k - 1]  # an object that was not hit just moved
 
 
