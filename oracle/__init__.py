@@ -73,6 +73,9 @@ def _load():
                                       ctypes.c_double, ctypes.c_int, P, P, P]
         lib.or_dnn_search.restype = ctypes.c_int
         lib.or_replay.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_double, P, P]
+        lib.or_backup.argtypes = [P, P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_int, P, P]
+        lib.or_backup.restype = ctypes.c_int
         lib.or_level.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                  ctypes.c_double, P, P]
         _lib = lib
@@ -179,6 +182,22 @@ def search_pruned(roots, weights: np.ndarray, A: int, d: int, gamma: float, corr
         "delta": diag[:, 2 * A:3 * A], "pi_o": diag[:, 4 * A].astype(np.int64), "B": diag[:, 4 * A + 3],
         "gap": diag[:, 4 * A + 4],
     }
+
+
+def backup(leaf_R, leaf_maxq, q0, r1, maxq1, n: int, A: int, d: int, gamma: float, correction: float,
+           exact_gev: bool = False):
+    """Alg. 1's backup + the BCTS correction on given leaf data (FP64).  leaf_R and
+    leaf_maxq hold n * A^d leaves in Alg. 1's order; q0, r1, maxq1 are [n][A].
+    Returns (actions [n], values [n][A])."""
+    lib = _load()
+    f = [np.ascontiguousarray(x, dtype=np.float64).reshape(-1) for x in (leaf_R, leaf_maxq, q0, r1, maxq1)]
+    act = np.zeros(n, dtype=np.int32)
+    val = np.zeros((n, A), dtype=np.float64)
+    rc = lib.or_backup(*[_ptr(x) for x in f], int(n), int(A), int(d), float(gamma), float(correction),
+                       int(bool(exact_gev)), _ptr(act), _ptr(val))
+    if rc != 0:
+        raise ValueError("oracle backup rejected its arguments")
+    return act, val
 
 
 def tree_node(root, weights: np.ndarray, A: int, d: int, gamma: float, level: int, idx: int):

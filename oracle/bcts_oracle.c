@@ -357,6 +357,57 @@ int or_search(const or_state *roots, int n, const float *W, int A, int d, double
     return or_search_ex(roots, n, W, A, d, gamma, corr, 0, actions, values, diag);
 }
 
+/*
+ * Alg. 1's backup and the BCTS correction on given leaf data, n roots:
+ *   leaf_R, leaf_maxq : n * A^d leaves in Alg. 1's order (child = parent * A + a),
+ *                       accumulated discounted reward R and max_a Q of each leaf
+ *   q0, r1, maxq1     : n * A, root Q-values, r(s_0, a) and max_a' Q(s_1^a, a')
+ * V(a_0) = max over the A^(d-1) leaves below root action a_0 of R + gamma^d maxq
+ * (Eq. 1 in its flat form; Alg. 1's argmax over the leaves), delta(a) = r1 +
+ * gamma maxq1 - q0 (Prop. 1), the penalty (Eq. 7, or Lemma 2's gap when
+ * exact_gev), values (Eq. 3) and the action (Eq. 4).  d = 0 returns q0 and pi_o.
+ */
+int or_backup(const double *leaf_R, const double *leaf_maxq, const double *q0, const double *r1,
+              const double *maxq1, int n, int A, int d, double gamma, double corr, int exact_gev, int *actions,
+              double *values) {
+    if (A < 1 || A > 64 || d < 0 || n < 0) return -1;
+    long long seg = 1;
+    for (int i = 1; i < d; ++i) seg *= A;
+    double gd = pow(gamma, (double)d);
+    for (int i = 0; i < n; ++i) {
+        const double *q = q0 + (size_t)i * A;
+        double *val = values + (size_t)i * A;
+        int pi_o = or_argmax_lowest(q, A);
+        if (d == 0) {
+            for (int a = 0; a < A; ++a) val[a] = q[a];
+            actions[i] = pi_o;
+            continue;
+        }
+        double V[64], delta[64];
+        for (int a = 0; a < A; ++a) {
+            long long first = ((long long)i * A + a) * seg;
+            double best = -INFINITY;
+            for (long long j = 0; j < seg; ++j) {
+                double v = leaf_R[first + j] + gd * leaf_maxq[first + j];
+                if (v > best) best = v;
+            }
+            V[a] = best;
+            delta[a] = r1[(size_t)i * A + a] + gamma * maxq1[(size_t)i * A + a] - q[a];
+        }
+        double delta_o = fabs(delta[pi_o]), delta_e = 0.0;
+        if (A > 1) {
+            for (int a = 0; a < A; ++a)
+                if (a != pi_o) delta_e += fabs(delta[a]);
+            delta_e /= (double)(A - 1);
+        }
+        double B = exact_gev ? or_bellman_penalty_exact(delta_e, delta_o, A, d)
+                             : or_bellman_penalty(delta_e, delta_o, A, d);
+        for (int a = 0; a < A; ++a) val[a] = (a == pi_o) ? V[a] : V[a] - gd * corr * B;
+        actions[i] = or_argmax_lowest(val, A);
+    }
+    return 0;
+}
+
 /* ---- tree enumeration in Alg. 1 order ------------------------------------ */
 /* Replay node `idx` of level `depth` (0 <= idx < A^depth): its actions are the
  * base-A digits of idx, most significant first (child = parent * A + a).
