@@ -244,6 +244,32 @@ BCTS_API int bcts_poll(bcts_ctx *ctx, uint64_t ticket, int32_t *out_action, floa
 BCTS_API int bcts_expand(const bcts_state *d_parents, const float *d_parent_R, int64_t n_parents, int A, float gamma_pow,
                 bcts_state *d_children, float *d_child_R, int8_t *d_child_reward, void *stream);
 
+/*
+ * Alg. 1's backup and the BCTS correction as a step of their own (device
+ * pointers, asynchronous on `stream`, no context, no allocation):
+ *   d_leaf_R     : n * A^d floats, Alg. 1's accumulated discounted reward R of every
+ *                  leaf, level order (leaf k of root i is i * A^d + k; child = parent * A + a)
+ *   d_leaf_maxq  : n * A^d floats, max_a Q(leaf, a)
+ *   d_q0         : n * A floats, root Q-values Q_0(s_0, .)
+ *   d_r1         : n * A floats, the rewards r(s_0, a) of the depth-1 nodes
+ *   d_maxq1      : n * A floats, max_a' Q(s_1^a, a') of the depth-1 nodes
+ *   A in [1, 32], d in [0, 16], gamma in (0, 1], correction = c (Sec. 5.1),
+ *   flags = 0 or BCTS_FLAG_EXACT_GEV (Lemma 2's gap instead of Eq. 7)
+ *   d_out_action : n int32, Eq. 4;  d_out_values : n * A floats, Eq. 3
+ * V(a_0) = max over the A^(d-1) leaves below root action a_0 of R + gamma^d maxq
+ * (Alg. 1's leaf term and argmax; Eq. 1), delta(a) = r1 + gamma maxq1 - Q_0
+ * (Prop. 1), delta_o = |delta(pi_o)|, delta_e = mean |delta(a)| over a != pi_o,
+ * B by Eq. 7, values V(a) - [a != pi_o] gamma^d c B, action = lowest-index argmax.
+ * d = 0: values = Q_0, action = pi_o (the leaf and depth-1 pointers may be NULL).
+ * At d = 1 the leaves are the depth-1 nodes (pass d_r1 and d_maxq1 as the leaf
+ * arrays).  d_out_values also holds the intermediate segment maxima, so it must
+ * not overlap the inputs.  Errors: BCTS_EINVAL (bad sizes, NULL pointers, more
+ * than 2^40 leaves per root action), BCTS_ECUDA.
+ */
+BCTS_API int bcts_backup(const float *d_leaf_R, const float *d_leaf_maxq, const float *d_q0, const float *d_r1,
+                         const float *d_maxq1, int n, int A, int d, float gamma, float correction, int flags,
+                         int32_t *d_out_action, float *d_out_values, void *stream);
+
 /* One environment tick on the host: *out = G(*s, a), *reward (may be NULL) in
  * {-1, 0, 1}; a in [0, 18).  The same rules as bcts_expand (Alg. 1's simulator),
  * for callers that advance an episode by the chosen action.  No context, no GPU. */
@@ -331,17 +357,25 @@ BCTS_API const char *bcts_dnn_last_error(const bcts_dnn_ctx *ctx);
  * FP32 Q-network (the same kernels as a context created with
  * BCTS_PREC_FP32_SIMT) and calls no cudaMalloc, cudaFree or other allocating
  * routine.  Its scratch -- the weights in the kernels' layout and the activation
- * maps -- is one static device array of about 18 MB that every GPU loading the
- * library holds until the process exits.
+ * maps -- is one static device array of about 18 MB, part of this entry point's
+ * device code, which a GPU holds from the time that code is loaded on it until
+ * the process exits.
+ * Set-up: the CUDA runtime loads device code lazily (on first use) unless
+ * CUDA_MODULE_LOADING=EAGER.  The first call on each device, made with that
+ * device current, loads the kernels this entry point runs, places the array and
+ * looks up its address (cudaGetSymbolAddress); n = 0 is enough.  Make that call
+ * at start-up, before any allocation limit applies and before any stream
+ * capture: later calls on the device then neither allocate nor load anything.
+ * Cost: every call first rewrites the caller's weights into the kernels' layout
+ * inside the array (about 1.69 M floats, 13.5 MB of extra reads and writes),
+ * which for small batches can take longer than the network itself.
  *   d_qnet_weights : device, bcts_qnet_numel(A) floats, PyTorch order (as in bcts_create)
  *   A              : 1..18
  *   d_frames       : device, uint8 [n][4][84][84]
  *   n              : 0..BCTS_STATIC_MAX_NODES; larger n returns BCTS_EINVAL
  *   d_q            : device, n * A floats
  *   stream         : cudaStream_t as void*, NULL = legacy default stream
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call on a device shares the one array and leaves
+ * Every call on a device shares the one array and leaves
  * its contents behind; each call overwrites all of it that it reads, so nothing
  * needs clearing, but calls whose execution overlaps on the GPU (different
  * streams, or different host threads) race on the array and must be serialised

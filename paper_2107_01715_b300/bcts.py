@@ -34,7 +34,7 @@ EXPORTED = ["bcts_qnet_numel", "bcts_create", "bcts_destroy", "bcts_last_error",
             "bcts_render", "bcts_qnet", "bcts_profile", "bcts_qnet_static", "bcts_env_step", "bcts_selftest_wait", "bcts_tree_nodes",
             "bcts_search_tree", "bcts_dnn_numel", "bcts_dnn_create", "bcts_dnn_destroy", "bcts_dnn_search",
             "bcts_dnn_search_device", "bcts_dnn_profile", "bcts_dnn_last_error", "bcts_search_pruned",
-            "bcts_search_pruned_device"]
+            "bcts_search_pruned_device", "bcts_backup"]
 BCTS_STATIC_MAX_NODES = 128
 BCTS_FLAG_FRAMES = 1
 BCTS_FLAG_EXACT_GEV = 2
@@ -74,6 +74,8 @@ lib.bcts_profile.argtypes = [_P, _I, _P, _P, _P]
 lib.bcts_qnet_static.argtypes = [_P, _I, _P, _I64, _P, _P]
 lib.bcts_env_step.argtypes = [_P, _I, _P, ctypes.POINTER(_I)]
 lib.bcts_selftest_wait.argtypes = [_I]
+lib.bcts_backup.argtypes = [_P, _P, _P, _P, _P, _I, _I, _I, ctypes.c_float, ctypes.c_float, _I, _P, _P, _P]
+lib.bcts_backup.restype = _I
 lib.bcts_tree_nodes.argtypes = [_I, _I, _I]
 lib.bcts_tree_nodes.restype = ctypes.c_int64
 lib.bcts_search_tree.argtypes = [_P, _P, _I, _P, _P, _P, _P, _P]
@@ -239,6 +241,14 @@ def bcts_expand(d_parents, d_parent_R, n_parents: int, A: int, gamma_pow: float,
                 d_child_reward=None, stream=None) -> int:
     return _check(lib.bcts_expand(_addr(d_parents), _addr(d_parent_R), n_parents, A, gamma_pow,
                                   _addr(d_children), _addr(d_child_R), _addr(d_child_reward), _stream(stream)))
+
+
+def bcts_backup(d_leaf_R, d_leaf_maxq, d_q0, d_r1, d_maxq1, n: int, A: int, d: int, gamma: float,
+                correction: float, d_action, d_values, flags: int = 0, stream=None) -> int:
+    """Alg. 1's backup + the BCTS correction on device leaf data (no context)."""
+    return _check(lib.bcts_backup(_addr(d_leaf_R), _addr(d_leaf_maxq), _addr(d_q0), _addr(d_r1), _addr(d_maxq1),
+                                  int(n), int(A), int(d), float(gamma), float(correction), int(flags),
+                                  _addr(d_action), _addr(d_values), _stream(stream)))
 
 
 def bcts_render(d_states, n: int, d_frames, stream=None) -> int:

@@ -162,7 +162,7 @@ static int mixed_enqueue(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_
   float *q0 = static_cast<float *>(m->q0.p);
   c->A = As;
   // root evaluation over all roots (all As columns; each root reads its first A)
-  if ((rc = c->eval_nodes(roots, pl.n, q0, nullptr, st)) != BCTS_OK) return rc;
+  if ((rc = c->eval_nodes_ref(roots, pl.n, q0, nullptr, st)) != BCTS_OK) return rc;
   bcts_state *L1 = static_cast<bcts_state *>(m->L1.p);
   float *r1 = static_cast<float *>(m->r1.p);
   uint8_t *nA1 = static_cast<uint8_t *>(m->nodeA1.p);
@@ -174,7 +174,7 @@ static int mixed_enqueue(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_
     BCTS_CUDA_TRY(cudaMemsetAsync(nA1 + g.l1_off, g.A, size_t(g.n) * g.A, st), c->err);
   }
   float *maxq1 = static_cast<float *>(m->maxq1.p);
-  if (pl.n1 > 0 && (rc = c->eval_nodes(L1, pl.n1, nullptr, maxq1, st, nA1)) != BCTS_OK) return rc;
+  if (pl.n1 > 0 && (rc = c->eval_nodes_ref(L1, pl.n1, nullptr, maxq1, st, nA1)) != BCTS_OK) return rc;
   bcts_state *leaves = static_cast<bcts_state *>(m->leaves.p);
   float *Rleaf = static_cast<float *>(m->Rleaf.p);
   uint8_t *nAl = static_cast<uint8_t *>(m->nodeA_leaf.p);

@@ -90,10 +90,10 @@ int Ctx::run_search_pruned(const bcts_state *d_roots, int n, int keep, int32_t *
   float *parR = static_cast<float *>(pr_parR.p);
   int32_t *kept = static_cast<int32_t *>(pr_idx.p);
   // root Q and pi_o; depth 1 (one node per group) and its Q for the Bellman errors
-  if ((rc = eval_nodes(d_roots, n, q0, nullptr, st)) != BCTS_OK) return rc;
+  if ((rc = eval_nodes_ref(d_roots, n, q0, nullptr, st)) != BCTS_OK) return rc;
   if ((rc = launch_expand(d_roots, nullptr, n, A_, 1.f, par, r1, nullptr, st)) != BCTS_OK)
     return fail(rc, "expand launch failed");
-  if ((rc = eval_nodes(par, G, nullptr, maxq1, st)) != BCTS_OK) return rc;
+  if ((rc = eval_nodes_ref(par, G, nullptr, maxq1, st)) != BCTS_OK) return rc;
   const float *curR = r1;
   int64_t S = 1;  // survivors per group
   double gprev = double(gamma);

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -27,102 +28,212 @@ const char *thread_error() { return g_thread_err.c_str(); }
 // ---------------------------------------------------------------------------
 namespace {
 
+// Segment maxima are kept as order-preserving 32-bit keys: for finite floats
+// key(a) < key(b) exactly when a < b, and key 0 lies below every float, so a
+// zero-filled array means "no value yet" and atomicMax on keys is a float max
+// whose result does not depend on the order of the updates.
+__device__ __forceinline__ uint32_t order_key(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_value(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
 // V[s] = max over the seg_len consecutive leaves of segment s of R + gamma^d maxq
 // (Alg. 1's leaf term; Eq. 1's max over a_1..a_d for root action s mod A).
-__global__ void __launch_bounds__(128) segment_max_kernel(const float *__restrict__ R,
-                                                          const float *__restrict__ maxq, int64_t seg_len,
-                                                          float gamma_pow, float *__restrict__ V) {
-  const int64_t s = blockIdx.x;
-  const int64_t base = s * seg_len;
+// Short segments: one warp per segment, four coalesced loads of each array in
+// flight per lane.
+__global__ void __launch_bounds__(256) segment_max_warp_kernel(const float *__restrict__ R,
+                                                               const float *__restrict__ maxq, int64_t n_seg,
+                                                               int64_t seg_len, float gamma_pow,
+                                                               uint32_t *__restrict__ V) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t s = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n_seg; s += nwarps) {
+    const float *r = R + s * seg_len, *q = maxq + s * seg_len;
+    float best = -INFINITY;
+    int64_t i = lane;
+    for (; i + 96 < seg_len; i += 128) {
+      const float r0 = __ldg(r + i), r1 = __ldg(r + i + 32), r2 = __ldg(r + i + 64), r3 = __ldg(r + i + 96);
+      const float q0 = __ldg(q + i), q1 = __ldg(q + i + 32), q2 = __ldg(q + i + 64), q3 = __ldg(q + i + 96);
+      best = fmaxf(fmaxf(best, fmaxf(r0 + gamma_pow * q0, r1 + gamma_pow * q1)),
+                   fmaxf(r2 + gamma_pow * q2, r3 + gamma_pow * q3));
+    }
+    for (; i < seg_len; i += 32) best = fmaxf(best, __ldg(r + i) + gamma_pow * __ldg(q + i));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) V[s] = order_key(best);
+  }
+}
+
+// Long segments: each block reduces kSegPart consecutive leaves of one segment
+// (eight loads of each array in flight per thread) and folds its maximum into the
+// segment's key with atomicMax; V is zero-filled first.
+constexpr int kSegThreads = 256, kSegPerThread = 16, kSegPart = kSegThreads * kSegPerThread;
+__global__ void __launch_bounds__(kSegThreads) segment_max_split_kernel(const float *__restrict__ R,
+                                                                       const float *__restrict__ maxq,
+                                                                       int64_t seg_len, int64_t parts,
+                                                                       float gamma_pow,
+                                                                       uint32_t *__restrict__ V) {
+  const int64_t s = blockIdx.x / parts, part = blockIdx.x - s * parts;
+  const int64_t lo = part * kSegPart, hi = lo + kSegPart < seg_len ? lo + kSegPart : seg_len;
+  const float *r = R + s * seg_len, *q = maxq + s * seg_len;
   float best = -INFINITY;
-  for (int64_t i = threadIdx.x; i < seg_len; i += blockDim.x) {
-    const float v = __ldg(R + base + i) + gamma_pow * __ldg(maxq + base + i);
-    best = fmaxf(best, v);
+  if (hi - lo == kSegPart) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v[kSegPerThread / 2];
+#pragma unroll
+      for (int k = 0; k < kSegPerThread / 2; ++k) {
+        const int64_t i = lo + threadIdx.x + int64_t(h * (kSegPerThread / 2) + k) * kSegThreads;
+        v[k] = __ldg(r + i) + gamma_pow * __ldg(q + i);
+      }
+#pragma unroll
+      for (int k = 0; k < kSegPerThread / 2; ++k) best = fmaxf(best, v[k]);
+    }
+  } else {
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kSegThreads)
+      best = fmaxf(best, __ldg(r + i) + gamma_pow * __ldg(q + i));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-  __shared__ float part[4];
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = best;
+  __shared__ float part_max[kSegThreads / 32];
+  if ((threadIdx.x & 31) == 0) part_max[threadIdx.x >> 5] = best;
   __syncthreads();
   if (threadIdx.x == 0) {
-    float b = part[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, part[w]);
-    V[s] = b;
+    float b = part_max[0];
+#pragma unroll
+    for (int w = 1; w < kSegThreads / 32; ++w) b = fmaxf(b, part_max[w]);
+    atomicMax(V + s, order_key(b));
   }
 }
 
-// One thread per root: pi_o = argmax Q_0 (Sec. 3.3), delta(a) from depths 0
-// and 1 (Prop. 1), delta_o = |delta(pi_o)|, delta_e = mean |delta(a)| over
-// a != pi_o, B by Eq. 7, corrected values (Eq. 3, scaled by c), action (Eq. 4).
-// Lemma 2: expected shift of the maximum of m iid standard normals, the mean of
-// its GEV limit, Phi^-1(1 - 1/m) + gamma_EM (Phi^-1(1 - 1/(e m)) - Phi^-1(1 - 1/m));
-// 0 for one element.  Upper quantiles via Phi^-1(1 - q) = -Phi^-1(q).
-__device__ double gev_shift(double m) {
-  if (m <= 1.0) return 0.0;
-  const double x1 = -normcdfinv(1.0 / m);
-  const double xe = -normcdfinv(1.0 / (2.718281828459045 * m));
-  return x1 + 0.5772156649015329 * (xe - x1);
+// Lowest-index argmax across the warp (lanes carry (value, index) pairs).
+__device__ __forceinline__ void warp_argmax_lowest(float &v, int &idx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
 }
 
-__global__ void finalize_kernel(const float *__restrict__ q0, const float *__restrict__ maxq1,
-                                const float *__restrict__ r1, const float *__restrict__ V, int n, int A,
-                                int depth, int A_stride, float gamma, float gamma_d, float corr,
-                                int32_t *__restrict__ action, float *__restrict__ values, int q_stride,
-                                int exact_gev) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float *q = q0 + size_t(i) * q_stride;
-  int pi_o = 0;
-  for (int a = 1; a < A; ++a)
-    if (q[a] > q[pi_o]) pi_o = a;
+// One warp per root, lane a holding action a (A <= 32): pi_o = argmax Q_0
+// (Sec. 3.3, lowest index on ties), delta(a) from depths 0 and 1 (Prop. 1),
+// delta_o = |delta(pi_o)|, delta_e = mean |delta(a)| over a != pi_o, the penalty
+// B (Eq. 7, or with exact_gev Lemma 2's gap from the GEV shifts gev_e, gev_o the
+// host computed for A^d - A^(d-1) and A^(d-1) leaves), corrected values (Eq. 3,
+// scaled by c) and the action (Eq. 4).  V holds the segment maxima as order
+// keys; `values` may alias V (each lane reads its own key before it writes).
+__global__ void __launch_bounds__(256) finalize_kernel(const float *__restrict__ q0, const float *__restrict__ maxq1,
+                                                       const float *__restrict__ r1, const uint32_t *V, int n,
+                                                       int A, int depth, int A_stride, float gamma, float gamma_d,
+                                                       float corr, int32_t *__restrict__ action, float *values,
+                                                       int q_stride, int exact_gev, float gev_e, float gev_o) {
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;  // whole warps leave together
+  const bool on = lane < A;
+  const float q = on ? q0[size_t(i) * q_stride + lane] : -INFINITY;
+  float bq = q;
+  int pi_o = on ? lane : 64;
+  warp_argmax_lowest(bq, pi_o);
   float *out = values + size_t(i) * A_stride;
   if (depth == 0) {
-    for (int a = 0; a < A; ++a) out[a] = q[a];
-    for (int a = A; a < A_stride; ++a) out[a] = 0.f;
-    action[i] = pi_o;
+    if (on) out[lane] = q;
+    else if (lane < A_stride) out[lane] = 0.f;
+    if (lane == 0) action[i] = pi_o;
     return;
   }
-  float d_o = 0.f, d_e = 0.f;
-  for (int a = 0; a < A; ++a) {
-    const float delta = r1[size_t(i) * A + a] + gamma * maxq1[size_t(i) * A + a] - q[a];
-    if (a == pi_o)
-      d_o = fabsf(delta);
-    else
-      d_e += fabsf(delta);
-  }
+  const float Vv = on ? key_value(V[size_t(i) * A + lane]) : -INFINITY;
+  const float delta = on ? r1[size_t(i) * A + lane] + gamma * maxq1[size_t(i) * A + lane] - q : 0.f;
+  const float d_o = __shfl_sync(0xffffffffu, fabsf(delta), pi_o);
+  float d_e = (on && lane != pi_o) ? fabsf(delta) : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d_e += __shfl_xor_sync(0xffffffffu, d_e, o);
   if (A > 1) d_e /= float(A - 1);
   float B;
   if (exact_gev) {
-    // Eq. 3's gap B_e - B_o itself (Lemma 2): A^d - A^(d-1) leaves under a != pi_o
-    // against A^(d-1) under pi_o, sigma = delta / sqrt(2) (Prop. 1)
-    const double n_o = pow(double(A), double(depth - 1)), n_e = pow(double(A), double(depth)) - n_o;
-    B = float(0.7071067811865476 * (double(d_e) * gev_shift(n_e) - double(d_o) * gev_shift(n_o)));
+    B = 0.70710678118654752f * (d_e * gev_e - d_o * gev_o);  // sigma = delta / sqrt(2) (Prop. 1)
   } else {
     B = sqrtf(logf(float(A))) * (d_e * sqrtf(float(depth)) - d_o * sqrtf(float(depth - 1))) -
         (d_e - d_o) * 0.35355339059327373f;  // Eq. 7; 1 / sqrt(8)
   }
   const float pen = gamma_d * corr * B;
-  int best = 0;
-  float bestv = -INFINITY;
-  for (int a = 0; a < A; ++a) {
-    const float v = V[size_t(i) * A + a] - (a == pi_o ? 0.f : pen);
-    out[a] = v;
-    if (a == 0 || v > bestv) {
-      bestv = v;
-      best = a;
-    }
-  }
-  for (int a = A; a < A_stride; ++a) out[a] = 0.f;
-  action[i] = best;
+  float v = on ? Vv - (lane == pi_o ? 0.f : pen) : -INFINITY;
+  __syncwarp();
+  if (on) out[lane] = v;
+  else if (lane < A_stride) out[lane] = 0.f;
+  int best = on ? lane : 64;
+  warp_argmax_lowest(v, best);
+  if (lane == 0) action[i] = best;
 }
 
 }  // namespace
 
+// Lemma 2: expected shift of the maximum of m iid standard normals, the mean of
+// its GEV limit, Phi^-1(1 - 1/m) + gamma_EM (Phi^-1(1 - 1/(e m)) - Phi^-1(1 - 1/m));
+// 0 for one element.  Computed on the host in double: it depends only on (A, d).
+// The upper quantile x(p), Q(x) = erfc(x / sqrt 2) / 2 = p, is found by Newton's
+// method on log Q(x) = log p, kept inside a bisection bracket.
+static double upper_normal_quantile(double p) {
+  if (!(p > 0.0 && p < 1.0)) return p >= 1.0 ? -INFINITY : INFINITY;
+  const double kRt2 = 1.4142135623730951, kRt2Pi = 2.5066282746310002;
+  double lo = -40.0, hi = 40.0;
+  double x = p < 0.5 ? std::sqrt(-2.0 * std::log(p)) : 0.0;
+  for (int it = 0; it < 200; ++it) {
+    const double Q = 0.5 * std::erfc(x / kRt2);
+    if (Q > p) lo = x; else hi = x;
+    const double phi = std::exp(-0.5 * x * x) / kRt2Pi;
+    // d/dx log Q = -phi / Q, so the Newton step is (log Q - log p) Q / phi
+    double nx = (Q > 0.0 && phi > 0.0) ? x + (std::log(Q) - std::log(p)) * Q / phi : 0.5 * (lo + hi);
+    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+    if (std::fabs(nx - x) <= 1e-15 * std::max(1.0, std::fabs(x))) return nx;
+    x = nx;
+  }
+  return x;
+}
+
+static double gev_shift_host(double m) {
+  if (m <= 1.0) return 0.0;
+  const double x1 = upper_normal_quantile(1.0 / m);
+  const double xe = upper_normal_quantile(1.0 / (2.718281828459045 * m));
+  return x1 + 0.5772156649015329 * (xe - x1);
+}
+
+static int num_sms_backup() {
+  static int sms = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+  });
+  return sms;
+}
+
+// V (n_seg floats of storage) receives the segment maxima as order keys.
 int launch_segment_max(const float *R, const float *maxq, int64_t n_seg, int64_t seg_len, float gamma_pow,
                        float *V, cudaStream_t st) {
   if (n_seg <= 0) return BCTS_OK;
   ProfScope ps(K_BACKUP, st);
-  segment_max_kernel<<<unsigned(n_seg), 128, 0, st>>>(R, maxq, seg_len, gamma_pow, V);
+  uint32_t *key = reinterpret_cast<uint32_t *>(V);
+  if (seg_len >= 2 * kSegPart) {
+    const int64_t parts = (seg_len + kSegPart - 1) / kSegPart;
+    if (n_seg * parts > 0x7FFFFFFFLL) return BCTS_EINVAL;
+    if (cudaMemsetAsync(key, 0, size_t(n_seg) * sizeof(uint32_t), st) != cudaSuccess) return BCTS_ECUDA;
+    segment_max_split_kernel<<<unsigned(n_seg * parts), kSegThreads, 0, st>>>(R, maxq, seg_len, parts, gamma_pow,
+                                                                              key);
+  } else {
+    const int64_t blocks = (n_seg + 7) / 8;
+    const int64_t cap = int64_t(num_sms_backup()) * 8;  // 8 resident 256-thread blocks per SM
+    segment_max_warp_kernel<<<unsigned(blocks < cap ? blocks : cap), 256, 0, st>>>(R, maxq, n_seg, seg_len,
+                                                                                   gamma_pow, key);
+  }
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 
@@ -152,10 +263,19 @@ int launch_finalize(const float *q0, const float *maxq1, const float *r1, const 
                     int A_stride, float gamma, float gamma_d, float corr, int32_t *action, float *values,
                     cudaStream_t st, int q_stride, int exact_gev) {
   if (n <= 0) return BCTS_OK;
+  if (A > 32 || A_stride > 32) return BCTS_EINVAL;  // one warp per root
   ProfScope ps(K_BACKUP, st);
-  finalize_kernel<<<unsigned((n + 127) / 128), 128, 0, st>>>(q0, maxq1, r1, V, n, A, depth, A_stride, gamma,
-                                                              gamma_d, corr, action, values,
-                                                              q_stride > 0 ? q_stride : A, exact_gev);
+  float gev_e = 0.f, gev_o = 0.f;
+  if (exact_gev && depth >= 1) {
+    // Eq. 3's gap B_e - B_o itself (Lemma 2): A^d - A^(d-1) leaves under a != pi_o
+    // against A^(d-1) under pi_o
+    const double n_o = std::pow(double(A), double(depth - 1)), n_e = std::pow(double(A), double(depth)) - n_o;
+    gev_e = float(gev_shift_host(n_e));
+    gev_o = float(gev_shift_host(n_o));
+  }
+  finalize_kernel<<<unsigned((int64_t(n) * 32 + 255) / 256), 256, 0, st>>>(
+      q0, maxq1, r1, reinterpret_cast<const uint32_t *>(V), n, A, depth, A_stride, gamma, gamma_d, corr, action,
+      values, q_stride > 0 ? q_stride : A, exact_gev, gev_e, gev_o);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 
@@ -236,6 +356,14 @@ int Ctx::eval_nodes(const bcts_state *states, int64_t count, float *q, float *ma
   return BCTS_OK;
 }
 
+int Ctx::eval_nodes_ref(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st,
+                        const uint8_t *node_A) {
+  ref_eval = true;
+  const int rc = eval_nodes(states, count, q, maxq, st, node_A);
+  ref_eval = false;
+  return rc;
+}
+
 // Q-network on at most one chunk of nodes, given either states (rendered here)
 // or frames.
 int Ctx::qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
@@ -262,8 +390,9 @@ int Ctx::qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt
     frames = static_cast<const uint8_t *>(frames_buf.p);
     states = nullptr;
   }
-  if ((rc = ensure(scratch_buf, tc_scratch_bytes(cnt, precision))) != BCTS_OK) return rc;
-  rc = tc_qnet_forward(tc, A, frames, states, cnt, q, maxq, scratch_buf.p, st, d_err, node_A,
+  const bool ref = ref_eval && tc_ref;
+  if ((rc = ensure(scratch_buf, tc_scratch_bytes(cnt, ref ? int(BCTS_PREC_FP32) : precision))) != BCTS_OK) return rc;
+  rc = tc_qnet_forward(ref ? tc_ref : tc, A, frames, states, cnt, q, maxq, scratch_buf.p, st, d_err, node_A,
                        states ? zl : nullptr);
   if (rc != BCTS_OK) return fail(rc, "tensor-core Q-network launch failed");
   return BCTS_OK;
@@ -317,8 +446,8 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
     float *q0 = static_cast<float *>(q0_buf.p);
     float *maxq1 = static_cast<float *>(maxq1_buf.p);
     float *V = static_cast<float *>(V_buf.p);
-    // a1: root evaluation, pi_o
-    if ((rc = eval_nodes(d_roots, n, q0, nullptr, st)) != BCTS_OK) break;
+    // a1: root evaluation, pi_o (FP32-class in every precision)
+    if ((rc = eval_nodes_ref(d_roots, n, q0, nullptr, st)) != BCTS_OK) break;
     if (d_ == 0) {
       rc = launch_finalize(q0, nullptr, nullptr, nullptr, n, A_, 0, A_stride, gamma, 1.f, corr, d_action,
                            d_values, st);
@@ -339,8 +468,9 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
     }
     if (tree_R)
       BCTS_CUDA_TRY(cudaMemcpyAsync(tree_R, r1, size_t(N[1]) * sizeof(float), cudaMemcpyDeviceToDevice, st), err);
-    // a3: depth-1 evaluation (for d = 1 these are the leaves)
-    if ((rc = eval_nodes(L1, N[1], nullptr, maxq1, st)) != BCTS_OK) break;
+    // a3: depth-1 evaluation (for d = 1 these are the leaves), FP32-class in every
+    // precision: these Q-values enter the Bellman errors of Prop. 1
+    if ((rc = eval_nodes_ref(L1, N[1], nullptr, maxq1, st)) != BCTS_OK) break;
     const float *leafR = r1;
     const float *leafMax = maxq1;
     if (d_ >= 2) {
@@ -431,6 +561,7 @@ Ctx::~Ctx() {
   if (d_err) cudaFree(d_err);
   if (mixed) mixed_destroy(mixed);
   if (tc && owns_weights) tc_weights_destroy(tc);
+  if (tc_ref && owns_weights) tc_weights_destroy(tc_ref);
   if (prof) profiler_destroy(prof);
   if (stream) cudaStreamDestroy(stream);
 }
@@ -617,6 +748,8 @@ extern "C" int bcts_create(const bcts_env_desc *env, const float *w, int A, int 
     if (rc == BCTS_OK)
       rc = tc_weights_create(hw.data(), A, c->precision, c->precision == BCTS_PREC_FP8 ? act_scale : nullptr,
                              &c->tc, e);
+    if (rc == BCTS_OK && c->precision != BCTS_PREC_FP32)
+      rc = tc_weights_create(hw.data(), A, BCTS_PREC_FP32, nullptr, &c->tc_ref, e);
     if (rc != BCTS_OK) {
       delete c;
       set_thread_error("bcts_create: " + e);
@@ -649,6 +782,48 @@ extern "C" int bcts_search_device(bcts_ctx *ctx, const bcts_state *d_roots, int 
   return c->run_graphed({uintptr_t(n), reinterpret_cast<uintptr_t>(d_roots), reinterpret_cast<uintptr_t>(d_action),
                          reinterpret_cast<uintptr_t>(d_values), reinterpret_cast<uintptr_t>(st)},
                         st, [&] { return c->run_search(d_roots, n, c->A_create, c->d, d_action, d_values, c->A_create, st); });
+}
+
+extern "C" int bcts_backup(const float *d_leaf_R, const float *d_leaf_maxq, const float *d_q0, const float *d_r1,
+                           const float *d_maxq1, int n, int A, int d, float gamma, float correction, int flags,
+                           int32_t *d_action, float *d_values, void *stream) {
+  using namespace bcts;
+  if (n < 0 || A < 1 || A > 32 || d < 0 || d > 16 || !(gamma > 0.f && gamma <= 1.f) || !std::isfinite(correction) ||
+      (flags & ~BCTS_FLAG_EXACT_GEV) != 0) {
+    set_thread_error("bcts_backup: invalid argument");
+    return BCTS_EINVAL;
+  }
+  if (n == 0) return BCTS_OK;
+  if (!d_q0 || !d_action || !d_values || (d >= 1 && (!d_leaf_R || !d_leaf_maxq || !d_r1 || !d_maxq1))) {
+    set_thread_error("bcts_backup: missing pointer");
+    return BCTS_EINVAL;
+  }
+  int64_t seg = 1;
+  for (int i = 1; i < d; ++i) {
+    if (seg > (int64_t(1) << 40) / A) {
+      set_thread_error("bcts_backup: more than 2^40 leaves per root action");
+      return BCTS_EINVAL;
+    }
+    seg *= A;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double gd = 1.0;
+  for (int i = 0; i < d; ++i) gd *= double(gamma);
+  int rc;
+  if (d >= 1) {
+    // the segment maxima go to d_values (n * A floats of storage), which finalize
+    // then overwrites in place with the corrected values
+    if ((rc = launch_segment_max(d_leaf_R, d_leaf_maxq, int64_t(n) * A, seg, float(gd), d_values, st)) != BCTS_OK) {
+      set_thread_error("bcts_backup: segment max launch failed");
+      return rc;
+    }
+  }
+  if ((rc = launch_finalize(d_q0, d_maxq1, d_r1, d_values, n, A, d, A, gamma, float(gd), correction, d_action,
+                            d_values, st, 0, (flags & BCTS_FLAG_EXACT_GEV) ? 1 : 0)) != BCTS_OK) {
+    set_thread_error("bcts_backup: finalize launch failed");
+    return rc;
+  }
+  return BCTS_OK;
 }
 
 extern "C" int64_t bcts_tree_nodes(int n, int A, int d) {

@@ -38,6 +38,11 @@ struct Ctx {
 
   SimtWeights simt{};
   TcWeights *tc = nullptr;
+  // FP32-class (bf16 split) weights of a BF16 / FP8 context: the roots and the
+  // depth-1 nodes are scored with them, so pi_o and the Bellman errors of
+  // Prop. 1 carry no reduced-precision error; only the leaves use `tc`.
+  TcWeights *tc_ref = nullptr;
+  bool ref_eval = false;  // set while eval_nodes_ref runs
   bool tc_fused_render = false;
   bool exact_gev = false;  // Lemma 2's exact bias gap instead of Eq. 7
   // per-node export of the current search (bcts_search_tree), level-major; null otherwise
@@ -78,6 +83,9 @@ struct Ctx {
   int eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st,
                  const uint8_t *node_A = nullptr, const float *zmap = nullptr, uint32_t zbranch = 0,
                  const uint32_t *zparent = nullptr);
+  // eval_nodes with the FP32-class weights (tc_ref) when the context has them
+  int eval_nodes_ref(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st,
+                     const uint8_t *node_A = nullptr);
   int qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
                  cudaStream_t st, const uint8_t *node_A = nullptr, const ZLeaf *zl = nullptr);
   int export_tree(const std::vector<int64_t> &N, int A_, int d_, const float *leafMax, cudaStream_t st);

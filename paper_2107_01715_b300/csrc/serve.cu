@@ -75,6 +75,7 @@ Ctx *clone_ctx(const Ctx *o) {
   if (c->opt.leaf_chunk <= 0) c->opt.leaf_chunk = 32768;
   c->simt = o->simt;
   c->tc = o->tc;
+  c->tc_ref = o->tc_ref;
   c->tc_fused_render = o->tc_fused_render;
   c->exact_gev = o->exact_gev;
   c->owns_weights = false;
