@@ -29,6 +29,9 @@ size_t simt_scratch_bytes(int64_t chunk);
 int simt_qnet_forward(const SimtWeights &w, const uint8_t *frames, int64_t n, float *q, float *maxq,
                       void *scratch, cudaStream_t stream, const uint8_t *node_A = nullptr);
 
+// Load the kernels of simt_qnet_forward on the current device now (see qnet_simt.cu).
+int simt_preload();
+
 // FC2 + max over actions on FP32 fc1 activations h [n][512] (one warp per node).
 int launch_fc2_max(const float *h, const float *W2, const float *b2, int A, int64_t n, float *q, float *maxq,
                    cudaStream_t st, const uint8_t *node_A = nullptr);

@@ -243,6 +243,24 @@ int run_gemm(int kind, const typename Geo::In *in, const float *W, const float *
 
 }  // namespace
 
+// Load every kernel simt_qnet_forward launches on the current device.  The CUDA
+// runtime loads device code lazily, on a kernel's first launch, unless
+// CUDA_MODULE_LOADING=EAGER; querying a kernel's attributes loads it now.
+int simt_preload() {
+  cudaFuncAttributes fa;
+  const void *fns[] = {reinterpret_cast<const void *>(simt_gemm<GeoConv1, 128, 32, 16, 8, 2>),
+                       reinterpret_cast<const void *>(simt_gemm<GeoConv2, 128, 64, 16, 8, 4>),
+                       reinterpret_cast<const void *>(simt_gemm<GeoConv3, 128, 64, 16, 8, 4>),
+                       reinterpret_cast<const void *>(simt_gemm<GeoFc1, 128, 64, 16, 8, 4>),
+                       reinterpret_cast<const void *>(fc2_max_kernel)};
+  for (const void *f : fns)
+    if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) {
+      cudaGetLastError();
+      return BCTS_ECUDA;
+    }
+  return BCTS_OK;
+}
+
 size_t simt_scratch_bytes(int64_t chunk) {
   return size_t(chunk) * sizeof(float) * (kP1 * kC1 + kP2 * kC2 + kP3 * kC3 + kF1) + 4096;
 }

@@ -7,9 +7,13 @@
 // serves them: it runs the same plain FP32 Q-network kernels as a context with
 // BCTS_PREC_FP32_SIMT, but takes its scratch (the weights in the kernels'
 // layout and the activation maps of up to BCTS_STATIC_MAX_NODES stacks) from
-// one file-scope __device__ array instead of cudaMalloc.  That array is part of
-// the library image: every GPU that loads the library holds it (about 18 MB)
-// until the process exits.
+// one file-scope __device__ array instead of cudaMalloc.  The array belongs to
+// this file's device code: a GPU holds it (about 18 MB) from the moment that code
+// is loaded on it until the process exits.  The CUDA runtime loads device code
+// lazily (on first use) unless CUDA_MODULE_LOADING=EAGER, so the first call on
+// each device -- n = 0 is enough -- loads the code this entry point runs and looks
+// up the array's address; that call is the one that may allocate, and it must come
+// before any allocation limit applies and before any stream capture.
 #include <mutex>
 
 #include "common.cuh"
@@ -69,7 +73,9 @@ __global__ void static_permute_weights(const float *__restrict__ src, int A, flo
 std::mutex g_setup_mu;
 float *g_scratch_ptr[64] = {};
 
-// Device address of the scratch on the current device, looked up once per device.
+// Set-up, once per device with that device current: load the kernels this entry
+// point launches (the permute kernel here, the plain FP32 network's kernels in
+// qnet_simt.cu) and look up the scratch's device address.
 int static_scratch(float **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
@@ -79,7 +85,9 @@ int static_scratch(float **out) {
   std::lock_guard<std::mutex> lk(g_setup_mu);
   if (!g_scratch_ptr[dev]) {
     void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+    cudaFuncAttributes fa;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p ||
+        cudaFuncGetAttributes(&fa, static_permute_weights) != cudaSuccess || simt_preload() != BCTS_OK) {
       cudaGetLastError();
       return BCTS_ECUDA;
     }
@@ -106,7 +114,7 @@ extern "C" int bcts_qnet_static(const float *d_qnet_weights, int A, const uint8_
   }
   float *scratch = nullptr;
   if (static_scratch(&scratch) != BCTS_OK) {
-    set_thread_error("bcts_qnet_static: cudaGetSymbolAddress of the static scratch failed");
+    set_thread_error("bcts_qnet_static: set-up (loading the kernels, cudaGetSymbolAddress of the static scratch) failed");
     return BCTS_ECUDA;
   }
   if (n == 0) return BCTS_OK;
