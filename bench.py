@@ -53,9 +53,11 @@ WORKLOADS = {
                    name="pruned search: 32 roots, |A|=18, d=4, 32 nodes kept per root action and level, FP32"),
     "dnn": dict(n=16, A=10, d=5, gamma=0.99, c=1.0, precision="fp32",
                 name="DNN forward model (Sec. 4): 16 roots, |A|=10, d=5, 100-wide state, 3 hidden layers of 100, FP32"),
-    "stream": dict(n=1 << 20, A=18, frames=100_000, gamma=0.99, c=1.0, precision="fp32",
+    "stream": dict(n=1 << 20, A=18, frames=100_000, backup_roots=1024, backup_d=4, gamma=0.99, c=1.0,
+                   precision="fp32",
                    name="streaming kernels alone: Alg. 1's expansion of 1,048,576 parents x |A|=18 "
-                        "(bcts_expand) and the renderer on 100,000 states (bcts_render)"),
+                        "(bcts_expand), the renderer on 100,000 states (bcts_render) and the backup with the "
+                        "BCTS correction over 1,024 roots x 18^4 leaves (bcts_backup)"),
     "serving": dict(n=1024, A=18, d=4, gamma=0.99, c=1.0, precision="bf16", rate=500.0, seconds=4.0,
                     budget=120 << 30,
                     name="serving form: Poisson requests from 1024 episodes, d in {2,3,4}, |A|=18, BF16, "
@@ -63,34 +65,33 @@ WORKLOADS = {
 }
 L2_BYTES = 126 * 2 ** 20
 DTYPES = {"fp32": "f32 (bf16x3 split products, f32 accumulate)", "bf16": "bf16", "fp8": "e4m3", "fp32_simt": "f32"}
-# Tensor-core multiply-accumulates per node each kernel class executes (Nature-DQN layers;
-# conv1 over a whole 4-frame stack for the roots and depth-1 nodes).  The parents' partial
-# maps and the leaves' conv1 run no contraction: streaming passes over the sprite tables,
-# bound by their DRAM bytes alone.
-EXEC_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 0, "conv1_leaf": 0,
-             "conv2": 81 * 64 * 512, "conv3": 49 * 64 * 576, "fc1": 512 * 3136}
-# DRAM bytes per node of the leaf-level kernel classes, read + write, from the ncu captures
-# of the current kernels summarised in profiles/tc_gemm_layers_4roots_a18_d3.md and
-# profiles/leaf_conv1_4roots_a18_d3.md (launches over 23,328 leaves; traffic grows in
-# proportion to the nodes a launch processes).
-TRAFFIC_PER_NODE = {"fp32/conv2": 70875.0, "bf16/conv2": 34950.0, "fp8/conv2": 16997.0,
-                    "fp32/conv3": 31911.0, "bf16/conv3": 15315.0, "fp8/conv3": 7010.0,
-                    "fp32/fc1": 14609.0, "bf16/fc1": 7429.0, "fp8/fc1": 3539.0,
-                    "fp32/conv1_leaf": 53939.0, "bf16/conv1_leaf": 27170.0, "fp8/conv1_leaf": 13745.0}
+# Multiply-accumulates per node of each kernel class in the method's own network
+# (Nature-DQN; conv1 over a whole 4-frame stack for the roots and depth-1 nodes).  The
+# parents' partial maps and the leaves' conv1 run no contraction: streaming passes over
+# the sprite tables, bound by their DRAM bytes alone.
+ALG_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 0, "conv1_leaf": 0,
+            "conv2": 81 * 64 * 512, "conv3": 49 * 64 * 576, "fc1": 512 * 3136}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per node of the leaf-level
+# kernel classes from one ncu capture of the current kernel version at 4 roots, A = 18,
+# d = 3 (launches over 23,328 leaves; traffic grows in proportion to the nodes a launch
+# processes).  A class whose kernel changed after its capture has no entry here.
+TRAFFIC_PER_NODE = {"fp32/conv1_leaf": 53939.0, "bf16/conv1_leaf": 27170.0, "fp8/conv1_leaf": 13745.0}
 
 
 def layer_model(cls, precision, A):
-    """Roofline terms of one node of a kernel class: (executed MACs, tensor MMAs per MAC,
-    algorithmic DRAM bytes read, written).  Activation maps are bf16 (2 bytes), bf16 hi + lo
-    in the FP32-class split mode (4 bytes), E4M3 in FP8 (1 byte); the partial conv1 map of a
-    parent is FP32 and each of its A children reads it, so a leaf's share is 1/A of it; the
-    fc1 output is FP32.  Weights stay resident in shared memory (read once per CTA)."""
+    """Roofline terms of one node of a kernel class: (algorithmic MACs, tensor MMAs
+    executed per MAC, algorithmic DRAM bytes read, written).  Activation maps are bf16
+    (2 bytes), bf16 hi + lo in the FP32-class split mode (4 bytes), E4M3 in FP8 (1 byte);
+    the partial conv1 map of a parent is FP32 and each of its A children reads it, so a
+    leaf's share is 1/A of it; the fc1 output is FP32.  Weights stay resident in shared
+    memory (read once per CTA).  The split mode executes 2 bf16 MMAs per conv1 MAC
+    (pixels are exact in bf16) and 3 per MAC elsewhere."""
     e = {"fp32": 4, "bf16": 2, "fp8": 1}.get(precision, 4)
     c1, c2, c3, f1 = 400 * 32, 81 * 64, 49 * 64, 512
     rw = {"conv1": (80, c1 * e), "conv1_partial": (80, c1 * 4), "conv1_leaf": (80 + c1 * 4 / A, c1 * e),
           "conv2": (c1 * e, c2 * e), "conv3": (c2 * e, c3 * e), "fc1": (c3 * e, f1 * 4),
           "fc2": (f1 * 4, 4)}.get(cls, (0, 0))
-    macs = EXEC_MACS.get(cls, A * 512 if cls == "fc2" else 0)
+    macs = ALG_MACS.get(cls, A * 512 if cls == "fc2" else 0)
     mma = (2 if cls.startswith("conv1") else 3) if precision == "fp32" else 1
     return macs, mma, rw[0], rw[1]
 
@@ -112,44 +113,50 @@ def class_nodes(cls, n, A, d, prof_cnt):
 
 
 def roofline_for(dom, precision, A, nodes, ms, launches, pk, pk_kind):
-    """Roofline of the dominant kernel class.  The binding resource is the one whose
-    minimum time (executed tensor FLOPs at the tensor peak for the operand type, or
-    algorithmic DRAM bytes at the measured copy bandwidth) is longer; achieved is that
-    quantity per second over the class's CUDA-event time."""
+    """Roofline of the dominant kernel class.  `achieved` counts the method's own work:
+    algorithmic FLOPs (2 x the layer's MACs per node) for a contraction, algorithmic DRAM
+    bytes otherwise, over the class's CUDA-event time.  The binding resource is the one
+    whose minimum time is longer: the FLOPs the kernel executes (split mode: 2-3 bf16 MMAs
+    per MAC) at the tensor peak of the operand type, or the algorithmic bytes at the
+    measured copy bandwidth.  `executed_frac` is the executed MMA rate against the same
+    peak."""
     macs, mma, rd, wr = layer_model(dom, precision, A)
     secs = ms / 1e3
     bytes_ = (rd + wr) * nodes
     hbm = pk["hbm_gbs"]
+    alg_flops = 2.0 * macs * nodes
     if precision == "fp32_simt":
         peak_t = pk.get("sm_max_mhz", 2032.0) * 1e6 * 148 * 128 * 2 / 1e12
-        t_unit, t_note, t_bound = "TFLOP/s", "FP32 FMA: 148 SMs x 128 lanes x 2 FLOP x max SM clock", "alu"
-        flops = 2.0 * macs * nodes
+        t_note, t_bound = "FP32 FMA: 148 SMs x 128 lanes x 2 FLOP x max SM clock", "alu"
+        exec_flops = alg_flops
     else:
         ratio = 2.0 if precision == "fp8" else 1.0  # nominal dense fp8 / bf16 = 4.5 / 2.25
         peak_t = pk["bf16_tflops_sustained"] * ratio
-        flops = 2.0 * macs * nodes * mma  # executed tensor FLOPs (3 or 2 bf16 MMAs per MAC when split)
-        t_unit, t_bound = "TFLOP/s", "tensor"
+        exec_flops = alg_flops * mma
+        t_bound = "tensor"
         t_note = "bf16 dense sustained" + (" x 2 (nominal fp8/bf16 ratio)" if ratio > 1 else "")
-    t_tensor = flops / (peak_t * 1e12)
+    t_tensor = exec_flops / (peak_t * 1e12)
     t_hbm = bytes_ / (hbm * 1e9)
     per_launch = nodes / max(launches, 1)
     tpn = TRAFFIC_PER_NODE.get(f"{precision}/{dom}")
     common = {"kernel": dom, "traffic": tpn * per_launch if tpn else None,
-              "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per node of the current "
-                               "kernel (profiles/tc_gemm_layers_4roots_a18_d3.md, "
-                               "profiles/leaf_conv1_4roots_a18_d3.md) x nodes per launch")
-              if tpn else "no ncu capture of this kernel class",
+              "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per node from one capture of "
+                                 "this kernel version (4 roots, A=18, d=3), x nodes per launch; not measured in "
+                                 "this run") if tpn else "no ncu capture of the current version of this kernel",
               "algorithmic_bytes_per_launch": (rd + wr) * per_launch,
-              "executed_flops_per_launch": flops / max(launches, 1),
+              "algorithmic_flops_per_launch": alg_flops / max(launches, 1),
+              "executed_flops_per_launch": exec_flops / max(launches, 1),
               "avg_launch_ms": ms / max(launches, 1), "launches": launches,
-              "min_time_ms": {"tensor_or_alu": 1e3 * t_tensor, "hbm": 1e3 * t_hbm}}
+              "min_time_ms": {"tensor_or_alu_executed": 1e3 * t_tensor, "hbm": 1e3 * t_hbm},
+              "hbm_achieved_gbs": bytes_ / secs / 1e9}
     if t_hbm >= t_tensor:
         ach = bytes_ / secs / 1e9
         return dict(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
                     peak_note=f"STREAM-style copy bandwidth (of {pk_kind})", **common)
-    ach = flops / secs / 1e12
-    return dict(bound=t_bound, achieved=ach, peak=peak_t, unit=t_unit, frac=ach / peak_t,
-                peak_note=f"{t_note} (of {pk_kind})", **common)
+    ach = alg_flops / secs / 1e12
+    return dict(bound=t_bound, achieved=ach, peak=peak_t, unit="TFLOP/s", frac=ach / peak_t,
+                executed_frac=exec_flops / secs / 1e12 / peak_t,
+                peak_note=f"{t_note} (of {pk_kind}); achieved counts the method's FLOPs (2 x MACs)", **common)
 
 
 def parse():
@@ -436,7 +443,7 @@ def run_pruned(args, wl):
     pk, pk_kind = peaks()
     dom = max(prof_ms, key=lambda k: prof_ms[k])
     roofline = None
-    if dom in EXEC_MACS and prof_ms[dom] > 0:
+    if prof_ms[dom] > 0:
         roofline = roofline_for(dom, precision, A, scored * args.steps, prof_ms[dom], prof_cnt[dom], pk, pk_kind)
     line = {"metric": METRIC, "value": value, "unit": "leaf nodes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -480,6 +487,20 @@ def run_stream(args, wl):
                       P * (80 + 4) + P * A * (80 + 4), P * A, "children"),
            "render": (lambda: bcts.bcts_render(d_child, F, d_frames, stream),
                       F * (80 + inputs.FRAME_BYTES), F, "frame stacks")}
+    # backup: seeded leaf rewards and max-Q values of nb roots x A^db leaves (Alg. 1 order)
+    nb, db = wl["backup_roots"], wl["backup_d"]
+    if args.roots:
+        nb = max(1, nb * args.roots // WORKLOADS["stream"]["n"])
+    LB = nb * A ** db
+    gen = torch.Generator(device=dev).manual_seed(5)
+    b_R = torch.randint(-1, 2, (LB,), device=dev, generator=gen).float() * 0.99
+    b_q = torch.rand(LB, device=dev, generator=gen)
+    b_q0, b_r1, b_m1 = (torch.rand(nb * A, device=dev, generator=gen) for _ in range(3))
+    b_act = torch.empty(nb, dtype=torch.int32, device=dev)
+    b_val = torch.empty(nb * A, dtype=torch.float32, device=dev)
+    ops["backup"] = (lambda: bcts.bcts_backup(b_R, b_q, b_q0, b_r1, b_m1, nb, A, db, 0.99, 1.0, b_act, b_val,
+                                              stream=stream),
+                     LB * 8 + nb * A * (3 * 4 + 4) + nb * 4, nb, "decisions")
     pk, pk_kind = peaks()
     out = {}
     with torch.cuda.stream(stream):
@@ -510,9 +531,10 @@ def run_stream(args, wl):
             "ms_per_step": e["avg_launch_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int16 states, uint8 frames", "data": "synthetic",
             "config": {"workload": wl["name"], "parents": P, "A": A, "render_states": F,
+                       "backup_leaves": LB,
                        "l2": "no flush: every launch reads and writes more than the 126 MB L2"},
             "roofline": dict(e["roofline"], kernel="expand_kernel"), "kernels": out,
-            "gpu_launches": 2 * (reps + args.warmup), "clocks": clk.summary(pk.get("sm_max_mhz", 2032.0)),
+            "gpu_launches": 4 * (reps + args.warmup), "clocks": clk.summary(pk.get("sm_max_mhz", 2032.0)),
             "e2e": None, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
 
@@ -623,6 +645,73 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+# Root-value tolerances per precision, |v - v_oracle| <= tol * max(|v_oracle|, 1): the
+# FP32-class bound of the FP32 path; BF16 / FP8 leaf Q-networks carry their operand
+# rounding (8 / 4 significant bits) through four layers.  The same figures as the tests'.
+PRECISION_TOL = {"fp32": 1e-4, "bf16": 2e-2, "fp8": 8e-2}
+
+
+def working_set_gb(n, A, d, precision):
+    """DRAM bytes one search streams through besides the weights: the two deepest node
+    levels (80-byte states + R), the parents' FP32 partial conv1 maps and one leaf
+    chunk's activation maps (32,768 leaves)."""
+    e = {"fp32": 4, "bf16": 2, "fp8": 1}.get(precision, 4)
+    leaves = n * A ** d
+    parents = n * A ** max(d - 1, 0)
+    chunk = min(leaves, 32768)
+    return (84 * (leaves + parents) + parents * 400 * 32 * 4 +
+            chunk * ((400 * 32 + 81 * 64 + 49 * 64) * e + 512 * 4)) / 1e9
+
+
+def report_vs_oracle(bcts, W, wl):
+    """Root values and actions of the FP32-class, BF16 and FP8 leaf Q-networks against
+    the stored FP64 oracle values (written by tests/golden/make_oracle_values.py, which
+    calls only the oracle): the precision workload's 8 roots at d = 4, and a separate
+    line for 256 more roots at d = 2.  Errors are relative, |v - v_oracle| /
+    max(|v_oracle|, 1), with the correction on (c = 1, Eq. 3) and off (c = 0, Eq. 2).
+    A root's action counts towards the agreement wherever the oracle's top-2 value
+    margin exceeds the precision's tolerance (PRECISION_TOL)."""
+    gamma = float(np.float32(wl["gamma"]))
+    out = {"tolerance": PRECISION_TOL, "vs": "stored FP64 oracle values"}
+    for fname, label in (("oracle_precision8_a18_d4.json", "8 roots, A=18, d=4 (the precision form)"),
+                         ("oracle_precision256_a18_d2.json", "256 roots, A=18, d=2 (additional roots)")):
+        path = os.path.join(ROOT, "tests", "golden", fname)
+        if not os.path.exists(path):
+            out[label] = "stored oracle values missing"
+            continue
+        with open(path) as f:
+            g = json.load(f)
+        A, d, c = g["A"], g["d"], g["correction"]
+        Wg = inputs.qnet_weights(A, seed=g["weights_seed"])
+        roots = inputs.root_states(g["seeds"])
+        ref_v = np.array([r["values"] for r in g["roots"]])
+        ref_u = np.array([r["v_uncorrected"] for r in g["roots"]])
+        ref_a = np.array([r["action"] for r in g["roots"]])
+        srt = np.sort(ref_v, axis=1)
+        margin = (srt[:, -1] - srt[:, -2]) / np.maximum(np.abs(srt[:, -1]), 1.0)
+        res = {"roots": len(roots), "oracle_margin_quantiles": np.quantile(margin, [0.1, 0.5, 0.9]).tolist()}
+        for prec, tol in PRECISION_TOL.items():
+            vals = {}
+            for cc in (c, 0.0):
+                cx = bcts.bcts_create(Wg, A, d, gamma, cc, precision=prec)
+                vals[cc] = bcts.bcts_search(cx, roots)
+                cx.close()
+            act, v1 = vals[c]
+            _, v0 = vals[0.0]
+            e1 = np.abs(v1 - ref_v) / np.maximum(np.abs(ref_v), 1.0)
+            e0 = np.abs(v0 - ref_u) / np.maximum(np.abs(ref_u), 1.0)
+            counted = margin > tol
+            res[prec] = {"max_rel_err_c1": float(e1.max()), "p99_rel_err_c1": float(np.quantile(e1, 0.99)),
+                         "mean_rel_err_c1": float(e1.mean()), "max_rel_err_c0": float(e0.max()),
+                         "within_tolerance": bool((e1 <= tol).all() and (e0 <= tol).all()),
+                         "roots_with_margin_above_tol": int(counted.sum()),
+                         "action_agreement_where_margin_above_tol":
+                             float((act[counted] == ref_a[counted]).mean()) if counted.any() else None,
+                         "action_agreement_all_roots": float((act == ref_a).mean())}
+        out[label] = res
+    return out
+
+
 def run_ours(args, wl):
     import torch
     world, rank, local = dist_setup(args.gpus)
@@ -723,51 +812,8 @@ def run_ours(args, wl):
         cb = cpu_baseline(W, wl)
 
     precision_report = None
-    if args.workload == "precision" and precision != "fp32":
-        # reduced-precision leaf Q-network against the FP32-class path (held to 1e-4 of the
-        # FP64 oracle by the tests).  Values with correction 0 are a continuous function of
-        # the Q-values (their error is the Q-network's); with the correction on, pi_o is a
-        # discrete argmax, so decisions are compared where the FP32-class top-2 margin
-        # exceeds twice that error.  Decisions: the 8 d=4 roots plus 256 d=2 roots.
-        def run(prec, c, rts, dd):
-            cx = bcts.bcts_create(W, A, dd, wl["gamma"], c, precision=prec)
-            out = bcts.bcts_search(cx, rts)
-            cx.close()
-            return out
-        # The corrected values also depend on pi_o = argmax Q_0 (Eq. 3 penalises every action
-        # but pi_o), a discrete choice that flips wherever the root Q top-2 margin is within
-        # the Q-network's error, so a decision is also counted where pi_o is decided: the
-        # root Q top-2 margin exceeds twice the measured root-Q error (d = 0 searches).
-        _, v32_0 = run("fp32", 0.0, roots, d)
-        _, vlo_0 = run(precision, 0.0, roots, d)
-        err0 = np.abs(vlo_0.astype(np.float64) - v32_0)
-        tol = float(err0.max())
-        extra = inputs.root_states(range(50000, 50256))
-        q32 = [run("fp32", 0.0, rts, 0)[1] for rts in (roots, extra)]
-        qlo = [run(precision, 0.0, rts, 0)[1] for rts in (roots, extra)]
-        qtol = float(max(np.abs(a.astype(np.float64) - b).max() for a, b in zip(qlo, q32)))
-        agree, counted, agree_all, total_roots, agree_dec, counted_dec = 0, 0, 0, 0, 0, 0
-        for (rts, dd), q in zip(((roots, d), (extra, 2)), q32):
-            a32, v32 = run("fp32", wl["c"], rts, dd)
-            alo, _ = run(precision, wl["c"], rts, dd)
-            srt = np.sort(v32, axis=1)
-            sure = (srt[:, -1] - srt[:, -2]) > 2 * tol
-            qs = np.sort(q, axis=1)
-            decided = sure & ((qs[:, -1] - qs[:, -2]) > 2 * qtol)
-            agree += int((alo[sure] == a32[sure]).sum())
-            counted += int(sure.sum())
-            agree_dec += int((alo[decided] == a32[decided]).sum())
-            counted_dec += int(decided.sum())
-            agree_all += int((alo == a32).sum())
-            total_roots += len(rts)
-        precision_report = {"vs": "fp32-class runs of the same roots",
-                            "value_max_abs_err_c0": tol, "value_mean_abs_err_c0": float(err0.mean()),
-                            "root_q_max_abs_err": qtol,
-                            "decision_roots": total_roots, "action_agreement_all": agree_all / total_roots,
-                            "roots_with_margin_above_2x_err": counted,
-                            "action_agreement_where_margin_exceeds": agree / counted if counted else None,
-                            "roots_decided": counted_dec,
-                            "action_agreement_where_decided": agree_dec / counted_dec if counted_dec else None}
+    if args.workload == "precision":
+        precision_report = report_vs_oracle(bcts, W, wl)
 
     lat = sorted(step_ms)
     p50 = lat[len(lat) // 2]
@@ -781,10 +827,11 @@ def run_ours(args, wl):
         "data": "synthetic",
         "config": {"workload": wl["name"], "roots_per_step": n, "A": A, "d": d, "gamma": wl["gamma"],
                    "correction": wl["c"], "leaves_per_step": leaves, "precision": precision,
-                   "l2": "flushed between steps (256 MB write); frames per step "
-                         f"{leaves * 28224 / 1e9:.2f} GB > 126 MB L2"},
+                   "l2": "flushed between steps (256 MB write); per-step DRAM working set "
+                         f"{working_set_gb(n, A, d, precision):.2f} GB (node levels, partial conv1 maps, "
+                         "one leaf chunk's activation maps) > 126 MB L2"},
         "decisions_per_s": decisions,
-        "latency_ms": {"p50": p50, "p99": p99, "what": "one search of the 32-root batch, device time"},
+        "latency_ms": {"p50": p50, "p99": p99, "what": f"one search of the {n}-root batch, device time"},
         "e2e": {"value": e2e_value, "unit": "leaf nodes/s", "h2d_bytes_per_step": int(n * 80),
                 "d2h_bytes_per_step": int(n * 4 + n * A * 4),
                 "ms_per_step": 1e3 * e2e_total / args.steps},
