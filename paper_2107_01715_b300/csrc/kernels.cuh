@@ -49,10 +49,26 @@ struct ZLeaf {
   uint32_t leaf0, branch;
   const uint32_t *parent = nullptr;  // if set: parent of leaf i = parent[leaf0 + i] (mixed branching)
 };
+// conv_tma_mask: conv2 (bit 0) / conv3 (bit 1) through the TMA-fed kernel of
+// conv_tma.cu instead of the cp.async-gathered tc_gemm; -1 = this precision's default.
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
                     float *maxq, void *scratch, cudaStream_t stream, int *d_err, const uint8_t *node_A = nullptr,
-                    const ZLeaf *zl = nullptr);
+                    const ZLeaf *zl = nullptr, int conv_tma_mask = -1);
+int tc_default_conv_mask(int precision);
 bool tc_has_partial(const TcWeights *w);
+// conv_tma.cu: conv2 (layer 2) or conv3 (layer 3) of n nodes on tcgen05 fed by TMA
+// im2col loads.  mode: 0 BF16, 1 FP32-class split (hi + lo arrays), 2 E4M3.
+struct ConvTmaArgs {
+  const void *in_hi, *in_lo;    // NHWC input maps (lo: split mode)
+  const void *w_hi, *w_lo;      // weights [64][kpad], K = (ky, kx, c)
+  int kpad;                     // weight row length in elements
+  const float *bias, *colscale; // colscale: FP8 per-channel weight x input activation scale
+  float out_inv_scale;          // FP8: 1 / activation scale of the output map
+  void *out_hi, *out_lo;        // NHWC output maps
+  int64_t n;                    // nodes
+  int *d_err;
+};
+int launch_conv_tma(int layer, int mode, const ConvTmaArgs &a, cudaStream_t st);
 // leaf_conv1.cu: conv1 of n leaves (states) from their parents' partial maps, as
 // ReLU(Z + the newest slot's term).  mode: 0 BF16, 1 FP32-class split (bf16 hi +
 // lo), 2 E4M3 scaled by out_scale.  T [4 objects][2][2][32] and W3 [64][32]: the

@@ -43,185 +43,10 @@
 #include "kernels.cuh"
 #include "pack.cuh"
 #include "render.cuh"
+#include "tc_ptx.cuh"
 
 namespace bcts {
 namespace tc {
-
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-// Arrive on `bar` (counted in its expected arrivals) once every cp.async this
-// thread issued before has landed in shared memory.
-__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void st_shared16(uint32_t addr, uint4 v) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
-               : "memory");
-}
-
-__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// 8 uint8 pixels (two little-endian words) -> 8 bf16.  A pixel b becomes the
-// float 2^23 + b by byte permutation, minus 2^23 gives b exactly (integers
-// below 256 have at most 8 significant bits, so the bf16 is the top half).
-__device__ __forceinline__ uint4 pixels8_to_bf16(uint32_t w0, uint32_t w1) {
-  uint32_t o[4];
-#pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    const uint32_t w = h < 2 ? w0 : w1;
-    const uint32_t j = 2 * (h & 1);
-    const float f0 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + j)) - 8388608.0f;
-    const float f1 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + j + 1)) - 8388608.0f;
-    o[h] = (__float_as_uint(f0) >> 16) | (__float_as_uint(f1) & 0xFFFF0000u);
-  }
-  return make_uint4(o[0], o[1], o[2], o[3]);
-}
-
-// Shared-memory matrix descriptor: K-major tile, 128-byte rows, 128-byte
-// swizzle, 8-row groups 1024 bytes apart (the tile base is 1024-byte aligned).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= uint64_t((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= uint64_t(1) << 16;                  // leading-dimension offset (unused for this layout)
-  d |= uint64_t(1024 >> 4) << 32;          // stride between 8-row groups
-  d |= uint64_t(1) << 46;                  // descriptor version
-  d |= uint64_t(2) << 61;                  // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor, kind::f16: bf16 A and B, FP32 accumulator, both
-// K-major, M = 128, N = n.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
-}
-
-// Instruction descriptor, kind::f8f6f4: E4M3 A and B, FP32 accumulator, K-major,
-// M = 128, N = n (K = 32 elements = 32 bytes per instruction).
-__host__ __device__ constexpr uint32_t idesc_e4m3(int n) {
-  return (1u << 4) | (0u << 7) | (0u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
-}
-
-// 16 uint8 pixels (four little-endian words) -> 16 E4M3 codes (saturating,
-// round to nearest; the renderer's palette values are exact).
-__device__ __forceinline__ uint4 pixels16_to_e4m3(const uint32_t (&w)[4]) {
-  uint32_t o[4];
-#pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    float f[4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) f[b] = __uint_as_float(__byte_perm(w[h], 0x4B000000u, 0x7440u + b)) - 8388608.0f;
-    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(f[0], f[1]), __NV_SATFINITE, __NV_E4M3);
-    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(f[2], f[3]), __NV_SATFINITE, __NV_E4M3);
-    o[h] = lo | (hi << 16);
-  }
-  return make_uint4(o[0], o[1], o[2], o[3]);
-}
-
-// Byte offset of 16-byte chunk `ch` of row `r` in a 128-byte-swizzled tile.
-__device__ __forceinline__ uint32_t sw128_off(int r, int ch) {
-  return uint32_t(r) * 128u + (uint32_t(ch ^ (r & 7)) << 4);
-}
-
-constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
-
-// Bounded mbarrier wait.  On time-out: error code into the device error word,
-// abort flag for the whole CTA, returns false.
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *d_err,
-                                         int code, long long limit = kWaitCycles) {
-  if (mbar_try(bar, parity)) return true;
-  const long long t0 = clock64();
-  int spins = 0;
-  while (!mbar_try(bar, parity)) {
-    if (*abort_flag) return false;
-    if (++spins > 4096) __nanosleep(32);
-    if (clock64() - t0 > limit) {
-      *abort_flag = 1;
-      if (d_err) atomicCAS(d_err, 0, code);
-      return false;
-    }
-  }
-  return true;
-}
 
 // ---------------------------------------------------------------------------
 // Layer geometry
@@ -930,6 +755,7 @@ struct TcWeights {
   const float *bias[4] = {};
   const float *colscale[4] = {};  // FP8: weight scale of each output channel x input activation scale
   float out_inv_scale[4] = {};    // FP8: 1 / activation scale of each layer's output map
+  int kpad[4] = {};               // stored weight row length per layer (elements)
   const float *f2w = nullptr, *f2b = nullptr;
   // conv1 from the sprite tables (the weights as this precision multiplies them):
   const float *c1T = nullptr;  // [4 channels][4 objects][2 dy][2 dx][32] palette x W_c summed over the sprite
@@ -1085,6 +911,7 @@ int tc_weights_create(const float *w, int A, int precision, const float *act_sca
   std::memcpy(h.data() + off_f2b, f2b, size_t(A) * 4);
   t->A = A;
   t->precision = precision;
+  for (int l = 0; l < 4; ++l) t->kpad[l] = kpad[l];
   if (cudaMalloc(&t->blob, total) != cudaSuccess ||
       cudaMemcpy(t->blob, h.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
@@ -1118,7 +945,7 @@ namespace {
 template <int MODE>
 int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n,
                     float *q, float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A,
-                    const ZLeaf *zl) {
+                    const ZLeaf *zl, int conv_tma_mask) {
   constexpr bool SPLIT = MODE == 1;
   const size_t eb = MODE == 2 ? 1 : 2;
   uint8_t *s = static_cast<uint8_t *>(scratch);
@@ -1156,25 +983,62 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
                 : tc::launch<1, MODE, false>(p, (long long)n * kP1, K_CONV1, st);
   }
   if (rc != BCTS_OK) return rc;
-  layer(1, a1, a1l, a2, a2l);
-  if ((rc = tc::launch<2, MODE, false>(p, (long long)n * kP2, K_CONV2, st)) != BCTS_OK) return rc;
-  layer(2, a2, a2l, a3, a3l);
-  if ((rc = tc::launch<3, MODE, false>(p, (long long)n * kP3, K_CONV3, st)) != BCTS_OK) return rc;
+  // conv2 and conv3: TMA-fed implicit GEMMs (conv_tma.cu)
+  auto conv = [&](int l, const void *in, const void *in_lo, void *o, void *o_lo) {
+    ConvTmaArgs a{};
+    a.in_hi = in;
+    a.in_lo = in_lo;
+    a.w_hi = w->w_hi[l];
+    a.w_lo = w->w_lo[l];
+    a.kpad = w->kpad[l];
+    a.bias = w->bias[l];
+    a.colscale = w->colscale[l];
+    a.out_inv_scale = w->out_inv_scale[l];
+    a.out_hi = o;
+    a.out_lo = o_lo;
+    a.n = n;
+    a.d_err = d_err;
+    return launch_conv_tma(l + 1, MODE, a, st);
+  };
+  // conv2 / conv3: TMA im2col-fed (conv_tma.cu) or cp.async-gathered (tc_gemm),
+  // chosen per layer by conv_tma_mask (bit 0 conv2, bit 1 conv3)
+  if (conv_tma_mask & 1) {
+    rc = conv(1, a1, a1l, a2, a2l);
+  } else {
+    layer(1, a1, a1l, a2, a2l);
+    rc = tc::launch<2, MODE, false>(p, (long long)n * kP2, K_CONV2, st);
+  }
+  if (rc != BCTS_OK) return rc;
+  if (conv_tma_mask & 2) {
+    rc = conv(2, a2, a2l, a3, a3l);
+  } else {
+    layer(2, a2, a2l, a3, a3l);
+    rc = tc::launch<3, MODE, false>(p, (long long)n * kP3, K_CONV3, st);
+  }
+  if (rc != BCTS_OK) return rc;
   layer(3, a3, a3l, h, nullptr);  // FP32 output for FC2
   if ((rc = tc::launch<4, MODE, false>(p, (long long)n, K_FC1, st)) != BCTS_OK) return rc;
   return launch_fc2_max(h, w->f2w, w->f2b, A, n, q, maxq, st, node_A);
 }
 }  // namespace
 
+int tc_default_conv_mask(int precision) {
+  // measured per layer on B300 at the Atari-scale workload (CUDA events, same
+  // call): TMA im2col wins for conv3 in the FP32-class split and E4M3 modes,
+  // the cp.async gather everywhere else
+  return precision == BCTS_PREC_BF16 ? 0 : 2;
+}
+
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
                     float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A,
-                    const ZLeaf *zl) {
+                    const ZLeaf *zl, int conv_tma_mask) {
   if (n <= 0) return BCTS_OK;
+  if (conv_tma_mask < 0) conv_tma_mask = tc_default_conv_mask(w->precision);
   if (w->precision == BCTS_PREC_FP32)
-    return tc_forward_impl<1>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl);
+    return tc_forward_impl<1>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl, conv_tma_mask);
   if (w->precision == BCTS_PREC_FP8)
-    return tc_forward_impl<2>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl);
-  return tc_forward_impl<0>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl);
+    return tc_forward_impl<2>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl, conv_tma_mask);
+  return tc_forward_impl<0>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl, conv_tma_mask);
 }
 
 bool tc_has_partial(const TcWeights *w) {

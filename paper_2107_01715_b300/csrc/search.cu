@@ -393,7 +393,7 @@ int Ctx::qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt
   const bool ref = ref_eval && tc_ref;
   if ((rc = ensure(scratch_buf, tc_scratch_bytes(cnt, ref ? int(BCTS_PREC_FP32) : precision))) != BCTS_OK) return rc;
   rc = tc_qnet_forward(ref ? tc_ref : tc, A, frames, states, cnt, q, maxq, scratch_buf.p, st, d_err, node_A,
-                       states ? zl : nullptr);
+                       states ? zl : nullptr, ref ? -1 : conv_mask);
   if (rc != BCTS_OK) return fail(rc, "tensor-core Q-network launch failed");
   return BCTS_OK;
 }

@@ -73,6 +73,7 @@ struct Ctx {
   MixedState *mixed = nullptr;
   Profiler *prof = nullptr;
   int64_t chunk_override = 0;    // leaf chunk chosen by the batched form's autotuner
+  int conv_mask = -1;            // conv2/conv3 kernel variants of the leaf Q-network (-1: per-precision default)
   uint64_t buf_generation = 1;   // bumped whenever a device buffer moves
 
   ~Ctx();

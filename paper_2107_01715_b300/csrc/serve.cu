@@ -76,6 +76,7 @@ Ctx *clone_ctx(const Ctx *o) {
   c->simt = o->simt;
   c->tc = o->tc;
   c->tc_ref = o->tc_ref;
+  c->conv_mask = o->conv_mask;
   c->tc_fused_render = o->tc_fused_render;
   c->exact_gev = o->exact_gev;
   c->owns_weights = false;
