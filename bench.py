@@ -169,6 +169,8 @@ def parse():
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--frames", action="store_true",
+                    help="the frame path: every node's frame rendered to device memory, conv1 on the tensor cores")
     ap.add_argument("--roots", type=int, default=None, help="override the root count (smaller profiling cases)")
     ap.add_argument("--rate", type=float, default=None, help="serving: mean request rate (req/s)")
     ap.add_argument("--seconds", type=float, default=None, help="serving: length of the arrival stream (s)")
@@ -721,7 +723,8 @@ def run_ours(args, wl):
     precision = args.precision or wl["precision"]
     n, A, d = wl["n"], wl["A"], wl["d"]
     W = inputs.qnet_weights(A, seed=1234)
-    ctx = bcts.bcts_create(W, A, d, wl["gamma"], wl["c"], precision=precision)
+    ctx = bcts.bcts_create(W, A, d, wl["gamma"], wl["c"], precision=precision,
+                           flags=bcts.BCTS_FLAG_FRAMES if args.frames else 0)
     roots = inputs.root_states(range(rank * n, rank * n + n))  # each rank its own roots
     d_roots = torch.from_numpy(roots.view(np.uint8).copy()).to(dev)
     d_act = torch.empty(n, dtype=torch.int32, device=dev)

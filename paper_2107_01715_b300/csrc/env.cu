@@ -149,37 +149,73 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(const uint4 *__r
 constexpr uint32_t kChunksPerSlot = kPix * kPix / 16;  // 441
 constexpr int kRenderThreads = 448;                    // >= 441, whole warps
 
-__global__ void __launch_bounds__(kRenderThreads) render_kernel(const uint4 *__restrict__ states, uint64_t n_slots,
-                                                                uint4 *__restrict__ frames) {
-  const uint32_t jc = threadIdx.x;  // chunk within the slot
-  if (jc >= kChunksPerSlot) return;
-  const uint32_t w0 = jc * 4;  // first word of the chunk
-  // the chunk's words lie in pixel rows y0 .. y0 + 1 (21 words per row)
-  const int y0 = int(w0 / kGrid), cy0 = y0 >> 2, cy1 = (y0 + 1) >> 2;
-  for (uint64_t b = blockIdx.x; b < n_slots; b += gridDim.x) {  // b = state * 4 + slot
-    const uint4 P = __ldg(states + (b >> 2) * 5 + (b & 3));  // pos[slot][0..3][x, y]
-    int ox[4], oy[4];
-    unpack_slot(P, ox, oy);
-    // most chunks' cell rows hold no object, and are background
-    bool any = false;
+// Frames are background except the sprite rows: each object is 4 rows of one
+// 4-pixel word (word index = pixel row * 21 + cell column).  A block renders a
+// group of kRenderGroup slots: every thread writes its 16-byte background chunk
+// of each slot, then, after a barrier, one thread per (slot, object, sprite row)
+// writes that word as the renderer paints it (render_word: all objects in the
+// cell, in index order, so objects sharing a cell give every writer the same
+// value).  The barrier orders the word stores after the block's chunk stores;
+// the next group writes other slots.
+constexpr int kRenderGroup = 8;
+
+__device__ __forceinline__ void render_group(const uint4 *__restrict__ states, uint64_t b0, uint64_t step,
+                                             uint64_t n, bool newest, uint4 *__restrict__ frames) {
+  const uint32_t jc = threadIdx.x;
+  if (jc < kChunksPerSlot) {
 #pragma unroll
-    for (int k = 0; k < kObj; ++k) any |= oy[k] == cy0 || oy[k] == cy1;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (any) {
-      uint32_t word[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const uint32_t w = w0 + i;
-        const int y = int(w / kGrid), cx = int(w - uint32_t(y) * kGrid);
-        word[i] = render_word(ox, oy, cx, y);
-      }
-      v = make_uint4(word[0], word[1], word[2], word[3]);
+    for (int k = 0; k < kRenderGroup; ++k) {
+      const uint64_t b = b0 + k * step;
+      if (b < n) frames[b * kChunksPerSlot + jc] = make_uint4(0u, 0u, 0u, 0u);
     }
-    frames[b * kChunksPerSlot + jc] = v;
+  }
+  __syncthreads();
+  if (jc < kRenderGroup * 16) {  // (slot, object, sprite row)
+    const int k = int(jc >> 4), obj = int(jc >> 2) & 3, r = int(jc & 3);
+    const uint64_t b = b0 + k * step;
+    if (b < n) {
+      const uint4 P = __ldg(newest ? states + b * 5 + 3 : states + (b >> 2) * 5 + (b & 3));
+      int ox[4], oy[4];
+      unpack_slot(P, ox, oy);
+      const int y = 4 * oy[obj] + r, cx = ox[obj];
+      reinterpret_cast<uint32_t *>(frames + b * kChunksPerSlot)[y * kGrid + cx] = render_word(ox, oy, cx, y);
+    }
   }
 }
 
+// All four history slots: block-strided over (state, slot) pairs b = state * 4 + slot.
+__global__ void __launch_bounds__(kRenderThreads) render_kernel(const uint4 *__restrict__ states, uint64_t n_slots,
+                                                                uint4 *__restrict__ frames) {
+  const uint64_t step = gridDim.x;
+  for (uint64_t b0 = blockIdx.x; b0 < n_slots; b0 += kRenderGroup * step)
+    render_group(states, b0, step, n_slots, false, frames);
+}
+
+// The newest history slot of each state only: frames [n][84][84], one per
+// state.  In a search every expanded node's stack is its own newest frame plus
+// its ancestors' (frame stacking, Sec. 5; Alg. 1's parent of x is x / A), so
+// each node's frame is rendered once, when its level is expanded.
+__global__ void __launch_bounds__(kRenderThreads) render_newest_kernel(const uint4 *__restrict__ states, uint64_t n,
+                                                                       uint4 *__restrict__ frames) {
+  const uint64_t step = gridDim.x;
+  for (uint64_t b0 = blockIdx.x; b0 < n; b0 += kRenderGroup * step)
+    render_group(states, b0, step, n, true, frames);
+}
+
 }  // namespace
+
+int launch_render_newest(const bcts_state *states, int64_t n, uint8_t *frames, cudaStream_t stream) {
+  if (n <= 0) return BCTS_OK;
+  int sms = 148;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t cap = uint64_t(sms) * 4 * 2;  // two waves of four blocks per SM, each striding over states
+  const unsigned blocks = unsigned(uint64_t(n) < cap ? uint64_t(n) : cap);
+  ProfScope ps(K_RENDER, stream);
+  render_newest_kernel<<<blocks, kRenderThreads, 0, stream>>>(reinterpret_cast<const uint4 *>(states), uint64_t(n),
+                                                              reinterpret_cast<uint4 *>(frames));
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
 
 int launch_expand(const bcts_state *parents, const float *parent_R, int64_t n_parents, int A, float gamma_pow,
                   bcts_state *children, float *child_R, int8_t *child_reward, cudaStream_t stream) {

@@ -9,6 +9,9 @@ namespace bcts {
 int launch_expand(const bcts_state *parents, const float *parent_R, int64_t n_parents, int A, float gamma_pow,
                   bcts_state *children, float *child_R, int8_t *child_reward, cudaStream_t stream);
 int launch_render(const bcts_state *states, int64_t n, uint8_t *frames, cudaStream_t stream);
+// The newest history slot only: frames [n][84][84] (7,056 bytes per state).
+int launch_render_newest(const bcts_state *states, int64_t n, uint8_t *frames, cudaStream_t stream);
+constexpr int kSlotBytes = kPix * kPix;  // 7,056
 
 // Weights of the plain FP32 CUDA-core Q-network, in the layouts its kernels read:
 //   c1w [32][256]  k = c*64 + ky*8 + kx, pre-scaled by 1/255
@@ -49,11 +52,32 @@ struct ZLeaf {
   uint32_t leaf0, branch;
   const uint32_t *parent = nullptr;  // if set: parent of leaf i = parent[leaf0 + i] (mixed branching)
 };
+// Rendered frames as conv1's input (any frame source): history slot s of node i
+// of a launch is the 84 x 84 uint8 frame at
+//   src[s] + ((node0 + i) / div[s] - sub[s]) * stride[s].
+// A search renders each node's newest frame when its level is expanded, so a
+// node's stack is its own frame and its ancestors' (Alg. 1: the parent of x is
+// x / A), and the roots' four slots.  With zmap set, conv1 runs the newest slot
+// only (src[0]) and adds the parent's partial map (zparent[zleaf0 + i] if set,
+// else (zleaf0 + i) / zbranch) before the ReLU.
+struct FrameSrc {
+  const uint8_t *src[4] = {};
+  uint32_t div[4] = {1, 1, 1, 1}, sub[4] = {}, stride[4] = {};
+  uint32_t node0 = 0;
+  const float *zmap = nullptr;
+  const uint32_t *zparent = nullptr;
+  uint32_t zleaf0 = 0, zbranch = 1;
+};
+// The parents' partial maps Z [n][400][32] FP32 from rendered frames: conv1's
+// weight channels 0-2 (plus its bias) over the parents' history slots 1-3, which
+// fs.src[0..2] describe.
+int tc_conv1_zmap_frames(const TcWeights *w, const FrameSrc &fs, int64_t n, float *z, cudaStream_t st, int *d_err);
 // conv_tma_mask: conv2 (bit 0) / conv3 (bit 1) through the TMA-fed kernel of
 // conv_tma.cu instead of the cp.async-gathered tc_gemm; -1 = this precision's default.
+// fs (frames and states NULL): conv1 from rendered frames (see FrameSrc).
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
                     float *maxq, void *scratch, cudaStream_t stream, int *d_err, const uint8_t *node_A = nullptr,
-                    const ZLeaf *zl = nullptr, int conv_tma_mask = -1);
+                    const ZLeaf *zl = nullptr, int conv_tma_mask = -1, const FrameSrc *fs = nullptr);
 int tc_default_conv_mask(int precision);
 bool tc_has_partial(const TcWeights *w);
 // conv_tma.cu: conv2 (layer 2) or conv3 (layer 3) of n nodes on tcgen05 fed by TMA

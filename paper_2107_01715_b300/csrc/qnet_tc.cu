@@ -74,6 +74,18 @@ template <>
 struct Geo<4> {
   static constexpr int BN = 256, KB = 49, P = 1, NTOT = 512, K = 3136;
 };
+// LAYER 5: the parents' partial conv1 maps from rendered frames: weight channels
+//          0-2 over the parent's history slots 1-3, FP32 out, no ReLU.
+// LAYER 6: the leaves' conv1 from rendered frames: weight channel 3 over the
+//          leaf's newest frame, plus its parent's partial map, then the ReLU.
+template <>
+struct Geo<5> {
+  static constexpr int BN = 32, KB = 3, P = 400, NTOT = 32, K = 192;
+};
+template <>
+struct Geo<6> {
+  static constexpr int BN = 32, KB = 1, P = 400, NTOT = 32, K = 64;
+};
 
 // Epilogue staging: 32 rows of up to 128 bytes (+16 to spread the banks) per warp.
 constexpr int kStgRow = 144;
@@ -96,11 +108,19 @@ struct Cfg {
   static constexpr int KB_FULL = FP8 ? (G::K + 127) / 128 : G::K / 64;
   static constexpr int KB = KB_FULL;  // K blocks per tile
   static constexpr int KPAD = KB_FULL * (128 / EB);  // stored weight row length in elements
-  static constexpr bool A_LO = SPLIT && LAYER != 1;  // conv1's integer pixels are exact in bf16
+  // conv1 family (A from uint8 frame pixels): layers 1, 5, 6
+  static constexpr bool C1 = LAYER == 1 || LAYER == 5 || LAYER == 6;
+  static constexpr int WROW = C1 ? 256 : KPAD;  // row length of the stored weights
+  // first weight K block and first weight channel (history slot) the tile uses,
+  // and the number of channels: layer 5 channels 0-2, layer 6 channel 3
+  static constexpr int KB0 = LAYER == 6 ? (FP8 ? 1 : 3) : 0;
+  static constexpr int CH0 = LAYER == 6 ? 3 : 0;
+  static constexpr int NCH = LAYER == 5 ? 3 : (LAYER == 6 ? 1 : 4);
+  static constexpr bool A_LO = SPLIT && !C1;  // conv1's integer pixels are exact in bf16
   // Weights resident in shared memory for the whole kernel: conv1 (8-32 KB) and,
   // outside split mode, conv2/conv3 (32-72 KB), instead of one weight tile per
   // K block of every output tile fetched again from L2.
-  static constexpr bool B_RES = LAYER == 1 || (!SPLIT && (LAYER == 2 || LAYER == 3));
+  static constexpr bool B_RES = C1 || (!SPLIT && (LAYER == 2 || LAYER == 3));
   // Split mode stores the weight tile as [hi rows; lo rows] so that one MMA of
   // twice the width gives A_hi*B_hi and A_hi*B_lo side by side in TMEM (the
   // epilogue adds the halves); fc1's 256-wide tiles keep separate MMAs.
@@ -129,7 +149,7 @@ struct Cfg {
   static constexpr int DIRTY_BYTES = LAYER == 1 ? 2 * 4 * 256 * 4 + 3 * 2 * 80 : 0;
   // conv1 (32-column tiles, the lightest epilogue) runs two epilogue warpgroups
   // on alternating tiles so each has two tiles' time to hide its load latency
-  static constexpr int EPI_WG = LAYER == 1 ? 2 : 1;
+  static constexpr int EPI_WG = C1 ? 2 : 1;
   // contiguous tile range per CTA (see the tile schedule in the kernel):
   // conv2/conv3 gain from it (neighbouring output rows share input rows)
   static constexpr bool CONTIG = LAYER == 2 || LAYER == 3;
@@ -158,6 +178,17 @@ struct GemmParams {
   void *out_hi;  // bf16 NHWC (layers 1-3) or FP32 [M][512] (layer 4)
   void *out_lo;  // bf16 remainders (split mode, layers 1-3)
   uint32_t M;  // rows, < 2^31 (checked by the launcher)
+  // conv1 family over frames: the A operand's history slot s (weight channel
+  // CH0 + s) of node i of this launch is the 84 x 84 frame at
+  // fsrc[s] + ((node0 + i) / fdiv[s] - fsub[s]) * fstride[s]
+  const uint8_t *fsrc[4];
+  uint32_t fdiv[4], fsub[4], fstride[4];
+  uint32_t node0;
+  // layer 6: partial map of the parent (FP32 [parent][400][32]) of node i: parent
+  // = zparent[zleaf0 + i] if zparent is set, else (zleaf0 + i) / zbranch
+  const float *zmap;
+  const uint32_t *zparent;
+  uint32_t zleaf0, zbranch;
   int num_tiles;
   int *d_err;
 };
@@ -244,14 +275,14 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
         const int kb = idx / (C::B_ROWS * 8), rem = idx - kb * (C::B_ROWS * 8), r = rem >> 3, c = rem & 7;
         const uint32_t off = uint32_t(kb) * (C::B_ROWS * 128) + sw128_off(r, c);
         const uint8_t *src = static_cast<const uint8_t *>(r < BN ? p.b_hi : p.b_lo);
-        cp_async16(res + off, src + ((long long)(r % BN) * C::KPAD) * EB + kb * 128 + c * 16);
+        cp_async16(res + off, src + ((long long)(r % BN) * C::WROW) * EB + (kb + C::KB0) * 128 + c * 16);
       }
       cp_commit();
       cp_wait<0>();
       fence_proxy_async();
       mbar_arrive(wready_bar);
     }
-    if (LAYER == 1 && FUSED) {
+    if constexpr (LAYER == 1 && FUSED) {
       // conv1 operand rendered from node states (channel kb = history slot kb),
       // all KB stages of a tile at once.  An im2col row is zero unless one of
       // the 2 x 2 cells its 8 x 8 patch covers holds an object, so the tiles
@@ -356,6 +387,106 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
         else cp_commit();
       }
       asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if constexpr (C::C1) {
+      // conv1 from rendered frames, one K block of one tile per stage.  Thread pt
+      // fills row pt / 2 of the tile, chunks 4 (pt % 2) .. + 3: bf16, chunk ch =
+      // 8 pixels of kernel row ch of weight channel CH0 + kb; E4M3, chunk ch = 16
+      // pixels of kernel rows 2(ch%4), 2(ch%4)+1 of weight channel
+      // 2 (KB0 + kb) + ch/4 (channels outside the tile's range stay zero).  The
+      // row's frame address is computed once per stage, and neighbouring lanes
+      // read neighbouring pixels.  The next stages' pixel words are loaded into
+      // registers before this stage is converted and stored.
+      constexpr int NW = FP8 ? 4 : 2;  // 32-bit pixel words per 16-byte chunk
+      const int row = pt >> 1, half = pt & 1;
+      auto live_of = [&](int kb) {
+        const int sl = FP8 ? 2 * (C::KB0 + kb) + half - C::CH0 : kb;
+        return sl >= 0 && sl < C::NCH;
+      };
+      auto load_stage = [&](int t, int kb, uint32_t(&w)[4][NW]) {
+        const uint32_t m0 = uint32_t(t / NT) * 128u;
+        const int sl = FP8 ? 2 * (C::KB0 + kb) + half - C::CH0 : kb;  // A slot
+        const bool live = sl >= 0 && sl < C::NCH;
+        const int sc = live ? sl : 0;
+        uint32_t m = m0 + uint32_t(row);
+        if (m > p.M - 1u) m = p.M - 1u;
+        const uint32_t node = m / uint32_t(kP1);
+        const int px = int(m - node * uint32_t(kP1)), oy = px / 20, ox = px - oy * 20;
+        const uint32_t nd = p.node0 + node, fd = p.fdiv[sc];
+        const uint8_t *frame = p.fsrc[sc] + size_t((fd == 1u ? nd : nd / fd) - p.fsub[sc]) * p.fstride[sc] +
+                               (4 * oy) * 84 + 4 * ox;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (FP8) {
+            const uint8_t *src = frame + 2 * j * 84;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) w[j][k] = 0u;
+            if (live) {
+              w[j][0] = __ldg(reinterpret_cast<const uint32_t *>(src));
+              w[j][1] = __ldg(reinterpret_cast<const uint32_t *>(src + 4));
+              w[j][NW > 2 ? 2 : 0] = __ldg(reinterpret_cast<const uint32_t *>(src + 84));
+              w[j][NW > 3 ? 3 : 0] = __ldg(reinterpret_cast<const uint32_t *>(src + 88));
+            }
+          } else {
+            const uint8_t *src = frame + (4 * half + j) * 84;
+            w[j][0] = __ldg(reinterpret_cast<const uint32_t *>(src));
+            w[j][1] = __ldg(reinterpret_cast<const uint32_t *>(src + 4));
+          }
+        }
+      };
+      // stage positions (tile, K block) in issue order; two stages' loads stay in
+      // flight ahead of the one being stored (three register buffers in rotation)
+      struct Pos {
+        int t, kb;
+      };
+      auto adv = [&](Pos q) {
+        if (++q.kb == KB) {
+          q.kb = 0;
+          q.t += TS;
+        }
+        return q;
+      };
+      int g = 0;
+      auto consume = [&](const Pos &q, const uint32_t(&w)[4][NW]) {
+        const int s = g % S;
+        if (!wait_bar(empty_bar(s), uint32_t((g / S) & 1) ^ 1u, abort_flag, p.d_err, 1)) return false;
+        const uint32_t sA = sA_of(s);
+        const bool live = live_of(q.kb);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          if (FP8) {
+            if (live) {
+              const uint32_t w4[4] = {w[j][0], w[j][1], w[j][NW > 2 ? 2 : 0], w[j][NW > 3 ? 3 : 0]};
+              v = pixels16_to_e4m3(w4);
+            }
+          } else {
+            v = pixels8_to_bf16(w[j][0], w[j][1]);
+          }
+          st_shared16(sA + sw128_off(row, 4 * half + j), v);
+        }
+        fence_proxy_async();
+        mbar_arrive(full_bar(s));
+        ++g;
+        return true;
+      };
+      uint32_t b0[4][NW], b1[4][NW], b2[4][NW];
+      Pos p0{T0, 0}, p1 = adv(p0), p2 = adv(p1);
+      if (p0.t < TE) load_stage(p0.t, p0.kb, b0);
+      if (p1.t < TE) load_stage(p1.t, p1.kb, b1);
+      for (;;) {
+        if (p0.t >= TE) break;
+        if (p2.t < TE) load_stage(p2.t, p2.kb, b2);
+        if (!consume(p0, b0)) break;
+        p0 = p1, p1 = p2, p2 = adv(p2);
+        if (p0.t >= TE) break;
+        if (p2.t < TE) load_stage(p2.t, p2.kb, b0);
+        if (!consume(p0, b1)) break;
+        p0 = p1, p1 = p2, p2 = adv(p2);
+        if (p0.t >= TE) break;
+        if (p2.t < TE) load_stage(p2.t, p2.kb, b1);
+        if (!consume(p0, b2)) break;
+        p0 = p1, p1 = p2, p2 = adv(p2);
+      }
     } else {
       // every stage's copies stay in flight until they land; the full barrier
       // counts one hardware arrival per producer thread at that moment
@@ -372,10 +503,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
           if (m > p.M - 1u) m = p.M - 1u;
           const uint32_t leaf = m / uint32_t(G::P);
           const int px = int(m - leaf * uint32_t(G::P));
-          if (LAYER == 1) {
-            const int oy = px / 20, ox = px - oy * 20;
-            rowoff[i] = (long long)leaf * kFrameBytes + (4 * oy) * 84 + 4 * ox;
-          } else if (LAYER == 2) {
+          if (LAYER == 2) {
             const int oy = px / 9, ox = px - oy * 9;
             rowoff[i] = (long long)leaf * (kP1 * kC1) + (2 * oy * 20 + 2 * ox) * kC1;
           } else if (LAYER == 3) {
@@ -391,34 +519,6 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
           if (!wait_bar(empty_bar(s), (round & 1u) ^ 1u, abort_flag, p.d_err, 1)) {
             ok = false;
             break;
-          }
-          if (LAYER == 1) {
-            const int kb = ks;  // one K block per stage
-            const uint32_t sA = sA_of(s);
-            // conv1 from uint8 frame stacks: 8 pixels of kernel row ch (bf16), or
-            // 16 pixels of kernel rows 2(ch%4), 2(ch%4)+1 of slot 2 kb + ch/4 (E4M3)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              uint4 v;
-              if (FP8) {
-                const uint8_t *src = static_cast<const uint8_t *>(p.a_hi) + rowoff[i] +
-                                     (2 * kb + (ch >> 2)) * 7056 + 2 * (ch & 3) * 84;
-                const uint32_t w[4] = {__ldg(reinterpret_cast<const uint32_t *>(src)),
-                                       __ldg(reinterpret_cast<const uint32_t *>(src + 4)),
-                                       __ldg(reinterpret_cast<const uint32_t *>(src + 84)),
-                                       __ldg(reinterpret_cast<const uint32_t *>(src + 88))};
-                v = pixels16_to_e4m3(w);
-              } else {
-                const uint8_t *src = static_cast<const uint8_t *>(p.a_hi) + rowoff[i] + kb * 7056 + ch * 84;
-                v = pixels8_to_bf16(__ldg(reinterpret_cast<const uint32_t *>(src)),
-                                    __ldg(reinterpret_cast<const uint32_t *>(src + 4)));
-              }
-              st_shared16(sA + sw128_off(r0 + 32 * i, ch), v);
-            }
-            fence_proxy_async();
-            mbar_arrive(full_bar(s));
-            ++g;
-            continue;
           }
 #pragma unroll
           for (int kk = 0; kk < C::KPS; ++kk) {
@@ -492,7 +592,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
         // hardware arrival carries no proxy fence: one fence per group of F
         // stages orders them before the tensor core's async-proxy reads.  conv1's
         // producers write with st.shared and fence themselves.
-        constexpr bool kFence = LAYER != 1;
+        constexpr bool kFence = !C::C1;
         constexpr int F = (kFence && S >= 4) ? C::FGROUP : 1;
         constexpr bool kTileCommit = LAYER == 1 && FUSED;  // one commit frees the tile's stages
         for (int ks0 = 0; ks0 < C::NKS && ok; ks0 += F) {
@@ -566,13 +666,13 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
     float *scale_s = bias_s + G::NTOT;
     const int eg = (warp - kEpiWarp0) >> 2;  // warpgroup: tiles it with it % EPI_WG == eg
     for (int i = threadIdx.x - 32 * kEpiWarp0; i < G::NTOT; i += 128 * C::EPI_WG) {
-      bias_s[i] = p.bias[i];
+      bias_s[i] = LAYER == 6 ? 0.f : p.bias[i];  // layer 6: the parent's partial map carries the bias
       scale_s[i] = FP8 ? p.colscale[i] : 1.f;
     }
     named_bar_sync(2, 128 * C::EPI_WG);
     uint8_t *stg = reinterpret_cast<uint8_t *>(bias_s + 2 * G::NTOT) + (warp - kEpiWarp0) * (32 * kStgRow);
     // output row bytes of one array (conv layers: whole rows; fc1: one 16-column chunk)
-    constexpr int ROWB = LAYER == 4 ? 64 : (FP8 ? BN : BN * 2);
+    constexpr int ROWB = LAYER == 4 ? 64 : (LAYER == 5 ? BN * 4 : (FP8 ? BN : BN * 2));
     constexpr int SEGS = ROWB / 16;  // 16-byte segments per row
     static_assert(ROWB + 16 <= kStgRow && kC1 * 4 + 16 <= kStgRow, "staging row");
     // write the warp's 32 staged rows (ROWB bytes each) to dst rows of `stride` bytes
@@ -591,8 +691,37 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
     int it = eg;
     for (int t = T0 + eg * TS; t < TE; t += EW * TS, it += EW) {
       const int acc = it % NA;
+      // layer 6: the warp's 32 rows of their parents' partial maps (FP32, 32
+      // columns = 128 bytes a row), loaded before the wait so that the latency
+      // overlaps the MMAs, and coalesced: load i of lane l is the 16-byte piece
+      // l % 8 of row l / 8 + 4 i; the pieces pass through the staging rows to
+      // their owners
+      float4 zr[LAYER == 6 ? 8 : 1];
+      if constexpr (LAYER == 6) {
+        uint32_t m = uint32_t(t / NT) * 128u + uint32_t(q * 32 + lane);
+        if (m > p.M - 1u) m = p.M - 1u;
+        const uint32_t node = m / uint32_t(kP1), px = m - node * uint32_t(kP1);
+        const uint32_t par = p.zparent ? __ldg(p.zparent + p.zleaf0 + node) : (p.zleaf0 + node) / p.zbranch;
+        const float4 *zrow = reinterpret_cast<const float4 *>(p.zmap + (size_t(par) * kP1 + px) * kC1);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float4 *src = reinterpret_cast<const float4 *>(
+              __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(zrow), (lane >> 3) + 4 * i));
+          zr[i] = __ldg(src + (lane & 7));
+        }
+      }
       if (!wait_bar(tfull_bar(acc), uint32_t((it / NA) & 1), abort_flag, p.d_err, 4)) break;
       tc_fence_after();
+      if constexpr (LAYER == 6) {
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          *reinterpret_cast<float4 *>(stg + ((lane >> 3) + 4 * i) * kStgRow + (lane & 7) * 16) = zr[i];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) zr[k] = *reinterpret_cast<const float4 *>(stg + lane * kStgRow + k * 16);
+        __syncwarp();
+      }
       const uint32_t mw0 = uint32_t(t / NT) * 128u + uint32_t(q * 32);
       const int n0 = (t % NT) * BN;
       const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * C::ACC_N);
@@ -633,8 +762,18 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
             v[2 * e] = add2(v[2 * e], c0);
             v[2 * e + 1] = add2(v[2 * e + 1], c1);
           }
+          if constexpr (LAYER == 6) {  // + the parent's partial map (it holds the bias)
+            const float4 z4 = zr[j * 4 + e];
+            v[2 * e] = add2(v[2 * e], make_float2(z4.x, z4.y));
+            v[2 * e + 1] = add2(v[2 * e + 1], make_float2(z4.z, z4.w));
+          }
         }
-        if constexpr (LAYER == 4) {
+        if constexpr (LAYER == 5) {  // partial map: FP32, no ReLU
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            *reinterpret_cast<float4 *>(stg + lane * kStgRow + j * 64 + e * 16) =
+                make_float4(v[2 * e].x, v[2 * e].y, v[2 * e + 1].x, v[2 * e + 1].y);
+        } else if constexpr (LAYER == 4) {
 #pragma unroll
           for (int e = 0; e < 4; ++e)
             *reinterpret_cast<float4 *>(stg + lane * kStgRow + e * 16) =
@@ -670,7 +809,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
       }
       if constexpr (LAYER != 4) {
         flush(static_cast<uint8_t *>(p.out_hi), size_t(ROWB), mw0);
-        if constexpr (SPLIT) {
+        if constexpr (SPLIT && LAYER != 5) {
 #pragma unroll
           for (int i = 0; i < OW / 4; ++i)
             *reinterpret_cast<uint4 *>(stg + lane * kStgRow + i * 16) =
@@ -942,10 +1081,20 @@ void tc_weights_destroy(TcWeights *w) {
 }
 
 namespace {
+void set_frames(tc::GemmParams &p, const FrameSrc &f) {
+  for (int h = 0; h < kHist; ++h) {
+    p.fsrc[h] = f.src[h];
+    p.fdiv[h] = f.div[h] ? f.div[h] : 1u;
+    p.fsub[h] = f.sub[h];
+    p.fstride[h] = f.stride[h];
+  }
+  p.node0 = f.node0;
+}
+
 template <int MODE>
 int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n,
                     float *q, float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A,
-                    const ZLeaf *zl, int conv_tma_mask) {
+                    const ZLeaf *zl, int conv_tma_mask, const FrameSrc *fs) {
   constexpr bool SPLIT = MODE == 1;
   const size_t eb = MODE == 2 ? 1 : 2;
   uint8_t *s = static_cast<uint8_t *>(scratch);
@@ -974,7 +1123,23 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
     p.out_lo = o_lo;
   };
   layer(0, states ? static_cast<const void *>(states) : static_cast<const void *>(frames), nullptr, a1, a1l);
-  if (zl && states) {
+  // frame sources of the conv1 producers: the given ones, or contiguous stacks
+  FrameSrc cont;
+  if (!fs && frames) {
+    for (int h = 0; h < kHist; ++h) {
+      cont.src[h] = frames + h * kSlotBytes;
+      cont.stride[h] = kFrameBytes;
+    }
+  }
+  set_frames(p, fs ? *fs : cont);
+  if (fs && fs->zmap) {
+    // the leaves' conv1 from their newest frame plus the parent's partial map
+    p.zmap = fs->zmap;
+    p.zparent = fs->zparent;
+    p.zleaf0 = fs->zleaf0;
+    p.zbranch = fs->zbranch;
+    rc = tc::launch<6, MODE, false>(p, (long long)n * kP1, K_CONV1_LEAF, st);
+  } else if (zl && states) {
     // the newest slot: weight channel 3
     rc = launch_leaf_conv1(MODE, states, n, *zl, w->c1T + 3 * (kObj * 4 * kC1), w->c1W + 3 * (64 * kC1),
                            w->out_inv_scale[0], a1, a1l, st);
@@ -1031,14 +1196,30 @@ int tc_default_conv_mask(int precision) {
 
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
                     float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A,
-                    const ZLeaf *zl, int conv_tma_mask) {
+                    const ZLeaf *zl, int conv_tma_mask, const FrameSrc *fs) {
   if (n <= 0) return BCTS_OK;
   if (conv_tma_mask < 0) conv_tma_mask = tc_default_conv_mask(w->precision);
   if (w->precision == BCTS_PREC_FP32)
-    return tc_forward_impl<1>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl, conv_tma_mask);
+    return tc_forward_impl<1>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl, conv_tma_mask, fs);
   if (w->precision == BCTS_PREC_FP8)
-    return tc_forward_impl<2>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl, conv_tma_mask);
-  return tc_forward_impl<0>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl, conv_tma_mask);
+    return tc_forward_impl<2>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl, conv_tma_mask, fs);
+  return tc_forward_impl<0>(w, A, frames, states, n, q, maxq, scratch, st, d_err, node_A, zl, conv_tma_mask, fs);
+}
+
+int tc_conv1_zmap_frames(const TcWeights *w, const FrameSrc &fs, int64_t n, float *z, cudaStream_t st, int *d_err) {
+  if (n <= 0) return BCTS_OK;
+  tc::GemmParams p{};
+  p.d_err = d_err;
+  p.b_hi = w->w_hi[0];
+  p.b_lo = w->w_lo[0];
+  p.bias = w->bias[0];
+  p.colscale = w->colscale[0];
+  p.out_hi = z;
+  set_frames(p, fs);
+  const long long M = (long long)n * kP1;
+  if (w->precision == BCTS_PREC_FP32) return tc::launch<5, 1, false>(p, M, K_CONV1_PARTIAL, st);
+  if (w->precision == BCTS_PREC_FP8) return tc::launch<5, 2, false>(p, M, K_CONV1_PARTIAL, st);
+  return tc::launch<5, 0, false>(p, M, K_CONV1_PARTIAL, st);
 }
 
 bool tc_has_partial(const TcWeights *w) {

@@ -364,6 +364,24 @@ int Ctx::eval_nodes_ref(const bcts_state *states, int64_t count, float *q, float
   return rc;
 }
 
+int Ctx::eval_frames(const FrameSrc &f, int64_t count, float *q, float *maxq, cudaStream_t st, bool ref) {
+  const bool r = ref && tc_ref;
+  const int64_t chunk = chunk_nodes();
+  int rc;
+  for (int64_t off = 0; off < count; off += chunk) {
+    const int64_t cnt = count - off < chunk ? count - off : chunk;
+    if ((rc = ensure(scratch_buf, tc_scratch_bytes(cnt, r ? int(BCTS_PREC_FP32) : precision))) != BCTS_OK) return rc;
+    FrameSrc fc = f;
+    fc.node0 = f.node0 + uint32_t(off);
+    if (f.zmap) fc.zleaf0 = f.zleaf0 + uint32_t(off);
+    rc = tc_qnet_forward(r ? tc_ref : tc, A, nullptr, nullptr, cnt, q ? q + off * A : nullptr,
+                         maxq ? maxq + off : nullptr, scratch_buf.p, st, d_err, nullptr, nullptr, r ? -1 : conv_mask,
+                         &fc);
+    if (rc != BCTS_OK) return fail(rc, "tensor-core Q-network launch failed");
+  }
+  return BCTS_OK;
+}
+
 // Q-network on at most one chunk of nodes, given either states (rendered here)
 // or frames.
 int Ctx::qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
@@ -446,8 +464,50 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
     float *q0 = static_cast<float *>(q0_buf.p);
     float *maxq1 = static_cast<float *>(maxq1_buf.p);
     float *V = static_cast<float *>(V_buf.p);
+    // Frame path (a tensor-core context with BCTS_FLAG_FRAMES): every node's
+    // newest frame is rendered into device memory when its level is expanded
+    // (the roots' whole stacks up front), and conv1 reads the stacks those frames
+    // form (frame stacking, Sec. 5: slot h of a node at level i is the newest
+    // frame of its ancestor 3 - h levels up, Alg. 1's parent being x / A).
+    const bool fpath = tc && !tc_fused_render;
+    const uint8_t *rootfr = nullptr;
+    // slot h of the nodes of level i as frame source s of f
+    auto slot_src = [&](int i, int h, FrameSrc &f, int sidx) {
+      const int j = 3 - h;
+      uint32_t div = 1;
+      for (int k = 0; k < (i - j >= 1 ? j : i); ++k) div *= uint32_t(A_);
+      f.div[sidx] = div;
+      f.sub[sidx] = 0;
+      if (i - j >= 1) {
+        f.src[sidx] = static_cast<const uint8_t *>(lvlfr_buf[i - j].p);
+        f.stride[sidx] = kSlotBytes;
+      } else {
+        f.src[sidx] = rootfr + (h + i) * kSlotBytes;
+        f.stride[sidx] = kFrameBytes;
+      }
+    };
+    if (fpath) {
+      if ((rc = ensure(rootfr_buf, size_t(n) * kFrameBytes)) != BCTS_OK) break;
+      rootfr = static_cast<const uint8_t *>(rootfr_buf.p);
+      if ((rc = launch_render(d_roots, n, static_cast<uint8_t *>(rootfr_buf.p), st)) != BCTS_OK) {
+        rc = fail(rc, "render launch failed");
+        break;
+      }
+      size_t need = 0;  // inner levels' frames
+      for (int i = 1; i < d_; ++i) need += size_t(N[i]) * kSlotBytes;
+      if (need > (size_t(24) << 30)) {
+        rc = fail(BCTS_ENOMEM, "frame path: the inner levels' frames exceed 24 GiB for this tree");
+        break;
+      }
+    }
     // a1: root evaluation, pi_o (FP32-class in every precision)
-    if ((rc = eval_nodes_ref(d_roots, n, q0, nullptr, st)) != BCTS_OK) break;
+    if (fpath) {
+      FrameSrc f0;
+      for (int h = 0; h < kHist; ++h) slot_src(0, h, f0, h);
+      if ((rc = eval_frames(f0, n, q0, nullptr, st, true)) != BCTS_OK) break;
+    } else if ((rc = eval_nodes_ref(d_roots, n, q0, nullptr, st)) != BCTS_OK) {
+      break;
+    }
     if (d_ == 0) {
       rc = launch_finalize(q0, nullptr, nullptr, nullptr, n, A_, 0, A_stride, gamma, 1.f, corr, d_action,
                            d_values, st);
@@ -470,7 +530,18 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
       BCTS_CUDA_TRY(cudaMemcpyAsync(tree_R, r1, size_t(N[1]) * sizeof(float), cudaMemcpyDeviceToDevice, st), err);
     // a3: depth-1 evaluation (for d = 1 these are the leaves), FP32-class in every
     // precision: these Q-values enter the Bellman errors of Prop. 1
-    if ((rc = eval_nodes_ref(L1, N[1], nullptr, maxq1, st)) != BCTS_OK) break;
+    if (fpath) {
+      if ((rc = ensure(lvlfr_buf[1], size_t(N[1]) * kSlotBytes)) != BCTS_OK) break;
+      if ((rc = launch_render_newest(L1, N[1], static_cast<uint8_t *>(lvlfr_buf[1].p), st)) != BCTS_OK) {
+        rc = fail(rc, "render launch failed");
+        break;
+      }
+      FrameSrc f1;
+      for (int h = 0; h < kHist; ++h) slot_src(1, h, f1, h);
+      if ((rc = eval_frames(f1, N[1], nullptr, maxq1, st, true)) != BCTS_OK) break;
+    } else if ((rc = eval_nodes_ref(L1, N[1], nullptr, maxq1, st)) != BCTS_OK) {
+      break;
+    }
     const float *leafR = r1;
     const float *leafMax = maxq1;
     if (d_ >= 2) {
@@ -495,6 +566,14 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
             break;
           }
         }
+        if (fpath && i + 1 < d_) {  // an inner level: its newest frames
+          if ((rc = ensure(lvlfr_buf[i + 1], size_t(N[i + 1]) * kSlotBytes)) != BCTS_OK) break;
+          if ((rc = launch_render_newest(nxt, N[i + 1], static_cast<uint8_t *>(lvlfr_buf[i + 1].p), st)) !=
+              BCTS_OK) {
+            rc = fail(rc, "render launch failed");
+            break;
+          }
+        }
         cur = nxt;
         curR = nxtR;
       }
@@ -504,6 +583,59 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
       // newer slots (the leaves' older three) enter as partial maps computed
       // once per parent (when they fit: 51.2 KB per parent).
       if ((rc = ensure(leafmax_buf, size_t(N[d_]) * sizeof(float))) != BCTS_OK) break;
+      if (fpath) {
+        // the parents' partial conv1 maps on the tensor cores (weight channels 0-2
+        // over their slots 1-3) when they fit, then per chunk of leaves: render
+        // the leaves' newest frames, conv1 of that slot plus the parent's map
+        const size_t zb = size_t(N[d_ - 1]) * kP1 * kC1 * sizeof(float);
+        float *z = nullptr;
+        if (zb <= (size_t(8) << 30)) {
+          if ((rc = ensure(z_buf, zb)) != BCTS_OK) break;
+          z = static_cast<float *>(z_buf.p);
+          FrameSrc fz;
+          for (int h = 1; h < kHist; ++h) slot_src(d_ - 1, h, fz, h - 1);
+          const int64_t chunk = chunk_nodes();
+          for (int64_t off = 0; off < N[d_ - 1] && rc == BCTS_OK; off += chunk) {
+            const int64_t cnt = N[d_ - 1] - off < chunk ? N[d_ - 1] - off : chunk;
+            fz.node0 = uint32_t(off);
+            rc = tc_conv1_zmap_frames(tc, fz, cnt, z + size_t(off) * kP1 * kC1, st, d_err);
+          }
+          if (rc != BCTS_OK) {
+            rc = fail(rc, "conv1 partial launch failed");
+            break;
+          }
+        }
+        const int64_t chunk = chunk_nodes();
+        if ((rc = ensure(frames_buf, size_t(std::min<int64_t>(chunk, N[d_])) * kSlotBytes)) != BCTS_OK) break;
+        uint8_t *lf = static_cast<uint8_t *>(frames_buf.p);
+        float *lm = static_cast<float *>(leafmax_buf.p);
+        for (int64_t off = 0; off < N[d_] && rc == BCTS_OK; off += chunk) {
+          const int64_t cnt = N[d_] - off < chunk ? N[d_] - off : chunk;
+          if ((rc = launch_render_newest(cur + off, cnt, lf, st)) != BCTS_OK) {
+            rc = fail(rc, "render launch failed");
+            break;
+          }
+          FrameSrc fl;
+          if (z) {  // slot 3 only, plus the parent's partial map
+            fl.src[0] = lf;
+            fl.stride[0] = kSlotBytes;
+            fl.zmap = z;
+            fl.zleaf0 = uint32_t(off);
+            fl.zbranch = uint32_t(A_);
+          } else {  // the whole stack: slot 3 from this chunk, slots 0-2 from the ancestors
+            for (int h = 0; h < kHist - 1; ++h) slot_src(d_, h, fl, h);
+            fl.src[3] = lf;
+            fl.stride[3] = kSlotBytes;
+            fl.div[3] = 1;
+            fl.sub[3] = uint32_t(off);
+            fl.node0 = uint32_t(off);
+          }
+          rc = eval_frames(fl, cnt, nullptr, lm + off, st, false);
+        }
+        if (rc != BCTS_OK) break;
+        leafR = curR;
+        leafMax = lm;
+      } else {
       const float *zmap = nullptr;
       const size_t zbytes = size_t(N[d_ - 1]) * kP1 * kC1 * sizeof(float);
       if (tc && tc_fused_render && tc_has_partial(tc) && zbytes <= (size_t(8) << 30)) {
@@ -527,6 +659,7 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
         break;
       leafR = curR;
       leafMax = static_cast<float *>(leafmax_buf.p);
+      }
     }
     // a6: backup
     double gd = 1.0;
@@ -550,7 +683,9 @@ int Ctx::run_search(const bcts_state *d_roots, int n, int A_, int d_, int32_t *d
 
 Ctx::~Ctx() {
   if (stream) cudaStreamSynchronize(stream);
-  DevBuf *bufs[] = {&frames_buf, &scratch_buf, &q0_buf, &maxq1_buf, &V_buf, &r1_buf, &leafmax_buf,
+  for (DevBuf &b : lvlfr_buf)
+    if (b.p) cudaFree(b.p);
+  DevBuf *bufs[] = {&rootfr_buf, &frames_buf, &scratch_buf, &q0_buf, &maxq1_buf, &V_buf, &r1_buf, &leafmax_buf,
                     &lvl_buf[0], &lvl_buf[1], &R_buf[0], &R_buf[1], &io_roots, &io_action, &io_values,
                     &simt_w, &mixed_buf, &z_buf, &pr_cand, &pr_candR, &pr_candQ, &pr_par, &pr_parR, &pr_idx};
   for (DevBuf *b : bufs)

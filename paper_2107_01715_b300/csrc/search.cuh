@@ -53,6 +53,9 @@ struct Ctx {
   DevBuf simt_w, frames_buf, scratch_buf, q0_buf, maxq1_buf, V_buf, r1_buf, leafmax_buf;
   DevBuf lvl_buf[2], R_buf[2];
   DevBuf io_roots, io_action, io_values, mixed_buf, z_buf;
+  // rendered frames of a search on the frame path (BCTS_FLAG_FRAMES): the roots'
+  // full stacks and each inner level's newest frames
+  DevBuf rootfr_buf, lvlfr_buf[kMaxDepth + 1];
   DevBuf pr_cand, pr_candR, pr_candQ, pr_par, pr_parR, pr_idx;  // pruned search
   int prune_keep = 0;  // > 0: run_search keeps this many nodes per root action and level (d >= 3)
   // plain searches replayed from CUDA graphs, keyed by (root count, the caller's
@@ -87,6 +90,9 @@ struct Ctx {
   // eval_nodes with the FP32-class weights (tc_ref) when the context has them
   int eval_nodes_ref(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st,
                      const uint8_t *node_A = nullptr);
+  // Q-network over nodes whose conv1 input is described by frame sources
+  // (chunked; f.node0 is advanced per chunk)
+  int eval_frames(const FrameSrc &f, int64_t count, float *q, float *maxq, cudaStream_t st, bool ref);
   int qnet_nodes(const bcts_state *states, const uint8_t *frames, int64_t cnt, float *q, float *maxq,
                  cudaStream_t st, const uint8_t *node_A = nullptr, const ZLeaf *zl = nullptr);
   int export_tree(const std::vector<int64_t> &N, int A_, int d_, const float *leafMax, cudaStream_t st);

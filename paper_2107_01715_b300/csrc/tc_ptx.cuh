@@ -113,9 +113,10 @@ __device__ __forceinline__ uint4 pixels8_to_bf16(uint32_t w0, uint32_t w1) {
   for (int h = 0; h < 4; ++h) {
     const uint32_t w = h < 2 ? w0 : w1;
     const uint32_t j = 2 * (h & 1);
-    const float f0 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + j)) - 8388608.0f;
-    const float f1 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + j + 1)) - 8388608.0f;
-    o[h] = (__float_as_uint(f0) >> 16) | (__float_as_uint(f1) & 0xFFFF0000u);
+    float2 f = make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + j)),
+                           __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + j + 1)));
+    f = __fadd2_rn(f, make_float2(-8388608.0f, -8388608.0f));  // both exact
+    o[h] = __byte_perm(__float_as_uint(f.x), __float_as_uint(f.y), 0x7632);  // the two upper halves
   }
   return make_uint4(o[0], o[1], o[2], o[3]);
 }

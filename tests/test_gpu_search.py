@@ -181,6 +181,47 @@ def test_precision_config_all_roots(dev, precision):
 
 
 @pytest.mark.parametrize("precision", [p for p in PRECISIONS if p in ("fp32", "bf16", "fp8")])
+@pytest.mark.parametrize("A,d,n,chunk", [(9, 1, 3, 0), (6, 2, 2, 0), (4, 3, 2, 0), (3, 4, 2, 0), (2, 6, 1, 0),
+                                         (4, 3, 3, 50), (18, 2, 2, 100)])
+def test_frame_path_matches_oracle(oracle_lib, dev, precision, A, d, n, chunk):
+    """BCTS_FLAG_FRAMES: every node's newest frame rendered to device memory as its
+    level is expanded, conv1 on the tensor cores over the stacks those frames form
+    (roots and depth-1 nodes whole; the parents' partial maps over their slots 1-3;
+    each leaf's newest slot plus its parent's map), against the oracle.  Depths 1-6
+    reach every case of a slot coming from a root's stack or an inner level's
+    frames; a leaf chunk below the leaf count makes ragged chunks."""
+    torch, bcts = dev
+    gamma, c = 0.99, 1.0
+    kw = {"flags": bcts.BCTS_FLAG_FRAMES}
+    if chunk:
+        kw["leaf_chunk"] = chunk
+    ctx, W = _ctx(bcts, A, d, gamma, c, precision, **kw)
+    roots = inputs.root_states(range(600, 600 + n))
+    act, val = bcts.bcts_search(ctx, roots)
+    ref = oracle_lib.search(roots, W, A, d, float(np.float32(gamma)), c)
+    tol = TOL[precision]
+    keep = [i for i in range(n) if pi_o_decided(ref["q0"][i], TOL["fp32"])]
+    assert value_close(val[keep], ref["values"][keep], tol).all(), np.abs(val[keep] - ref["values"][keep]).max()
+    check_actions(act[keep], ref["values"][keep], tol)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [p for p in PRECISIONS if p in ("fp32", "bf16", "fp8")])
+def test_frame_path_atari_scale_all_roots(dev, precision):
+    """The frame path at the bench workload (32 roots, A = 18, d = 3): every root
+    against the stored FP64 oracle values."""
+    torch, bcts = dev
+    g, ref = _stored("oracle_atari32_a18_d3.json")
+    A, d, c = g["A"], g["d"], g["correction"]
+    ctx, W = _ctx(bcts, A, d, 0.99, c, precision, flags=bcts.BCTS_FLAG_FRAMES)
+    act, val = bcts.bcts_search(ctx, inputs.root_states(g["seeds"]))
+    ctx.close()
+    tol = TOL[precision]
+    assert value_close(val, ref["values"], tol).all(), np.abs(val - ref["values"]).max()
+    check_actions(act, ref["values"], tol)
+
+
+@pytest.mark.parametrize("precision", [p for p in PRECISIONS if p in ("fp32", "bf16", "fp8")])
 @pytest.mark.parametrize("d", [1, 2])
 def test_fused_render_equals_materialised_frames(oracle_lib, dev, precision, d):
     """conv1 rendering its operand from node states must see exactly the pixels
