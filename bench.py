@@ -169,6 +169,8 @@ def parse():
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the other forms' measurements on the line")
     ap.add_argument("--frames", action="store_true",
                     help="the frame path: every node's frame rendered to device memory, conv1 on the tensor cores")
     ap.add_argument("--roots", type=int, default=None, help="override the root count (smaller profiling cases)")
@@ -462,18 +464,15 @@ def run_pruned(args, wl):
     ctx.close()
 
 
-def run_stream(args, wl):
+def stream_measure(bcts, torch, wl, warmup, steps, roots_override=None, rank=0, local=0, world=1):
     """The HBM-bound kernels on their own, at sizes where bandwidth rather than launch
     latency decides: the expansion (one thread per child: read the parent's 80-byte
-    state and R, write the child's state and R) through bcts_expand, and the renderer
-    (read a state, write its 28,224-byte frame stack) through bcts_render.  Inside a
-    search both run on the levels' node counts (0.5 % of the default step); here each
-    is timed alone with CUDA events, inputs and outputs larger than L2."""
-    import torch
-    world, rank, local = dist_setup(args.gpus)
+    state and R, write the child's state and R) through bcts_expand, the renderer
+    (read a state, write its 28,224-byte frame stack) through bcts_render, and the
+    backup with the BCTS correction through bcts_backup (8 bytes per leaf).  Inside a
+    search they run on the levels' node counts; here each is timed alone with CUDA
+    events, inputs and outputs larger than L2."""
     dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    from paper_2107_01715_b300 import bcts
     P, A = wl["n"], wl["A"]
     F = min(wl["frames"], P // 10)  # rendered from the first children (a reduced --roots case shrinks both)
     base = inputs.root_states(range(rank * 4096, rank * 4096 + 4096))
@@ -484,15 +483,15 @@ def run_stream(args, wl):
     d_childR = torch.empty(P * A, dtype=torch.float32, device=dev)
     d_frames = torch.empty(F * inputs.FRAME_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    reps = max(1, min(args.steps, 20))
+    reps = max(1, min(steps, 20))
     ops = {"expand": (lambda: bcts.bcts_expand(d_par, d_parR, P, A, 0.99, d_child, d_childR, None, stream),
                       P * (80 + 4) + P * A * (80 + 4), P * A, "children"),
            "render": (lambda: bcts.bcts_render(d_child, F, d_frames, stream),
                       F * (80 + inputs.FRAME_BYTES), F, "frame stacks")}
     # backup: seeded leaf rewards and max-Q values of nb roots x A^db leaves (Alg. 1 order)
     nb, db = wl["backup_roots"], wl["backup_d"]
-    if args.roots:
-        nb = max(1, nb * args.roots // WORKLOADS["stream"]["n"])
+    if roots_override:
+        nb = max(1, nb * roots_override // WORKLOADS["stream"]["n"])
     LB = nb * A ** db
     gen = torch.Generator(device=dev).manual_seed(5)
     b_R = torch.randint(-1, 2, (LB,), device=dev, generator=gen).float() * 0.99
@@ -508,7 +507,7 @@ def run_stream(args, wl):
     with torch.cuda.stream(stream):
         with ClockSampler(local) as clk:
             for name, (fn, nbytes, units, unit_name) in ops.items():
-                for _ in range(args.warmup):
+                for _ in range(warmup):
                     fn()
                 stream.synchronize()
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
@@ -525,19 +524,30 @@ def run_stream(args, wl):
                              "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                                           "frac": ach / pk["hbm_gbs"],
                                           "peak_note": f"STREAM-style copy bandwidth (of {pk_kind})"}}
+    del d_child, d_frames, b_R, b_q
+    return {"kernels": out, "parents": P, "A": A, "render_states": F, "backup_leaves": LB, "reps": reps,
+            "clocks": clk.summary(pk.get("sm_max_mhz", 2032.0))}
+
+
+def run_stream(args, wl):
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(torch.device("cuda", local))
+    from paper_2107_01715_b300 import bcts
+    m = stream_measure(bcts, torch, wl, args.warmup, args.steps, args.roots, rank, local, world)
     if rank != 0:
         return
-    e = out["expand"]
-    line = {"metric": "expansion children/s and render frame stacks/s (the search's HBM-bound kernels alone)",
-            "value": e["rate_per_s"], "unit": "children/s", "n_gpus": world, "steps": reps, "warmup": args.warmup,
-            "ms_per_step": e["avg_launch_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "int16 states, uint8 frames", "data": "synthetic",
-            "config": {"workload": wl["name"], "parents": P, "A": A, "render_states": F,
-                       "backup_leaves": LB,
+    e = m["kernels"]["expand"]
+    line = {"metric": "expansion children/s, render frame stacks/s and backup decisions/s (the search's HBM-bound "
+                      "kernels alone)",
+            "value": e["rate_per_s"], "unit": "children/s", "n_gpus": world, "steps": m["reps"],
+            "warmup": args.warmup, "ms_per_step": e["avg_launch_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int16 states, uint8 frames, f32 values", "data": "synthetic",
+            "config": {"workload": wl["name"], "parents": m["parents"], "A": m["A"], "render_states": m["render_states"],
+                       "backup_leaves": m["backup_leaves"],
                        "l2": "no flush: every launch reads and writes more than the 126 MB L2"},
-            "roofline": dict(e["roofline"], kernel="expand_kernel"), "kernels": out,
-            "gpu_launches": 4 * (reps + args.warmup), "clocks": clk.summary(pk.get("sm_max_mhz", 2032.0)),
-            "e2e": None, "cpu_baseline": None}
+            "roofline": dict(e["roofline"], kernel="expand_kernel"), "kernels": m["kernels"],
+            "gpu_launches": 4 * (m["reps"] + args.warmup), "clocks": m["clocks"], "e2e": None, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
 
 
@@ -817,6 +827,9 @@ def run_ours(args, wl):
     precision_report = None
     if args.workload == "precision":
         precision_report = report_vs_oracle(bcts, W, wl)
+    forms = None
+    if args.workload == "atari" and not args.no_extras and not args.frames and args.roots is None:
+        forms = forms_measure(bcts, torch, wl)
 
     lat = sorted(step_ms)
     p50 = lat[len(lat) // 2]
@@ -845,6 +858,7 @@ def run_ours(args, wl):
         "speedup_vs_plain_fp32": (value / plain["value"]) if plain else None,
         "cpu_baseline": cb,
         "precision_report": precision_report,
+        "forms": forms,
         "clocks": clocks,
         "wall_s_timed": t_wall,
     }
@@ -856,60 +870,144 @@ def _clock_line(clk, pk):
     return clk.summary(pk.get("sm_max_mhz"))
 
 
-def run_batched(args, wl):
-    """Batched form: one bcts_search_mixed call per step over 256 mixed roots."""
-    import torch
-    world, rank, local = dist_setup(args.gpus)
-    torch.cuda.set_device(local)
-    from paper_2107_01715_b300 import bcts
-    precision = args.precision or wl["precision"]
+def batched_measure(bcts, wl, precision, steps, warmup, rank=0, local=0, world=1):
+    """Batched form: one bcts_search_mixed call per step over 256 mixed roots (d uniform
+    in {1,2,3,4}, |A| in {4,9,18}); host wall clock per call, inputs and outputs
+    through host memory."""
     W = inputs.qnet_weights(18, seed=1234)
     ctx = bcts.bcts_create(W, 18, 4, wl["gamma"], wl["c"], precision=precision)
     roots, ds, As = inputs.mixed_roots(wl["n"], seed=7 + rank)
     leaves = int(sum(int(a) ** int(d) for a, d in zip(As, ds)))
-    for _ in range(args.warmup):
-        bcts.bcts_search_mixed(ctx, roots, ds, As)  # eager, captured, then replayed
+    for _ in range(warmup):
+        bcts.bcts_search_mixed(ctx, roots, ds, As)  # eager, tuned, captured, then replayed
     bcts.bcts_profile(ctx, False)
     pk, _ = peaks()
     barrier(world)
     with ClockSampler(local) as clk:
         times = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             t0 = time.perf_counter()
             bcts.bcts_search_mixed(ctx, roots, ds, As)
             times.append(time.perf_counter() - t0)
     _, _, launches = bcts.bcts_profile(ctx, False)
-    total = max_over_ranks(world, sum(times), torch.device("cuda", local))
-    if rank == 0:
-        lat = sorted(times)
-        line = {"metric": METRIC, "value": world * leaves * args.steps / total, "unit": "leaf nodes/s",
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": precision, "data": "synthetic",
-                "config": {"workload": wl["name"], "roots_per_step": wl["n"], "leaves_per_step": leaves,
-                           "depth_hist": {str(k): int((ds == k).sum()) for k in (1, 2, 3, 4)},
-                           "A_hist": {str(k): int((As == k).sum()) for k in (4, 9, 18)},
-                           "l2": f"{leaves} leaves per step, working set far above the 126 MB L2"},
-                "decisions_per_s": world * wl["n"] * args.steps / total,
-                "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[-1],
-                               "what": "one bcts_search_mixed call of the 256-root batch, host wall clock"},
-                "e2e": {"value": world * leaves * args.steps / total, "unit": "leaf nodes/s",
-                        "h2d_bytes_per_step": wl["n"] * 80, "d2h_bytes_per_step": wl["n"] * (4 + 18 * 4)},
-                "gpu_launches": launches, "clocks": _clock_line(clk, pk)}
-        print(json.dumps(line), flush=True)
     ctx.close()
+    lat = sorted(times)
+    return {"leaves_per_step": leaves, "roots_per_step": wl["n"], "precision": precision, "steps": steps,
+            "total_s": sum(times), "leaf_nodes_per_s": leaves * steps / sum(times),
+            "decisions_per_s": wl["n"] * steps / sum(times),
+            "depth_hist": {str(k): int((ds == k).sum()) for k in (1, 2, 3, 4)},
+            "A_hist": {str(k): int((As == k).sum()) for k in (4, 9, 18)},
+            "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[-1],
+                           "what": "one bcts_search_mixed call of the 256-root batch, host wall clock"},
+            "gpu_launches": launches, "clocks": _clock_line(clk, pk)}
 
 
-def run_serving(args, wl):
-    """Serving form: Poisson arrivals from simulated episodes through bcts_submit /
-    bcts_poll; episodes advance by the returned action (bcts_env_step)."""
+def run_batched(args, wl):
     import torch
     world, rank, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     from paper_2107_01715_b300 import bcts
     precision = args.precision or wl["precision"]
-    rate = args.rate or wl["rate"]
-    seconds = args.seconds or wl["seconds"]
+    m = batched_measure(bcts, wl, precision, args.steps, args.warmup, rank, local, world)
+    total = max_over_ranks(world, m["total_s"], torch.device("cuda", local))
+    if rank == 0:
+        leaves = m["leaves_per_step"]
+        line = {"metric": METRIC, "value": world * leaves * args.steps / total, "unit": "leaf nodes/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": precision, "data": "synthetic",
+                "config": {"workload": wl["name"], "roots_per_step": wl["n"], "leaves_per_step": leaves,
+                           "depth_hist": m["depth_hist"], "A_hist": m["A_hist"],
+                           "l2": f"{leaves} leaves per step, working set far above the 126 MB L2"},
+                "decisions_per_s": world * wl["n"] * args.steps / total, "latency_ms": m["latency_ms"],
+                "e2e": {"value": world * leaves * args.steps / total, "unit": "leaf nodes/s",
+                        "h2d_bytes_per_step": wl["n"] * 80, "d2h_bytes_per_step": wl["n"] * (4 + 18 * 4)},
+                "gpu_launches": m["gpu_launches"], "clocks": m["clocks"]}
+        print(json.dumps(line), flush=True)
+
+
+def search_measure(bcts, torch, W, A, d, n, gamma, c, precision, steps, warmup, flags=0, seed0=0):
+    """Device-time throughput of bcts_search_device over n seeded roots (inputs in
+    device memory, L2 flushed between steps), with per-kernel-class time from a
+    second, profiled pass."""
+    ctx = bcts.bcts_create(W, A, d, gamma, c, precision=precision, flags=flags)
+    roots = inputs.root_states(range(seed0, seed0 + n))
+    d_roots = torch.from_numpy(roots.view(np.uint8).copy()).cuda()
+    d_act = torch.empty(n, dtype=torch.int32, device="cuda")
+    d_val = torch.empty(n * A, dtype=torch.float32, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        for _ in range(warmup):
+            bcts.bcts_search_device(ctx, d_roots, n, d_act, d_val, st)
+        st.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(st)
+            bcts.bcts_search_device(ctx, d_roots, n, d_act, d_val, st)
+            ev[i][1].record(st)
+        st.synchronize()
+        bcts.bcts_profile(ctx, True)
+        for i in range(steps):
+            flush.zero_()
+            bcts.bcts_search_device(ctx, d_roots, n, d_act, d_val, st)
+        st.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    kms, kcnt, _ = bcts.bcts_profile(ctx, False)
+    ctx.close()
+    leaves = n * A ** d
+    return {"leaf_nodes_per_s": leaves * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
+            "decisions_per_s": n * steps / (sum(ms) / 1e3), "leaves_per_step": leaves, "steps": steps,
+            "kernel_ms_per_step": {k: v / steps for k, v in kms.items() if v > 0},
+            "kernel_launches_per_step": {k: v / steps for k, v in kcnt.items() if v > 0}}
+
+
+def forms_measure(bcts, torch, wl_default):
+    """The other configurations the metric names, measured in the default run so that
+    they appear on its line: the frame path of the headline workload, the precision
+    form (8 roots, A = 18, d = 4) in BF16 / FP8 / FP32-class with its report against
+    the stored oracle values, the batched form, the serving form at a rate below
+    saturation, and the streaming kernels (expansion, renderer, backup) alone."""
+    out = {}
+    pk, pk_kind = peaks()
+    g, cc = wl_default["gamma"], wl_default["c"]
+    W18 = inputs.qnet_weights(18, seed=1234)
+    # frame path: every node's frame rendered to device memory, conv1 on the tensor cores
+    fp = search_measure(bcts, torch, W18, 18, 3, 32, g, cc, "fp32", 20, 3, flags=bcts.BCTS_FLAG_FRAMES)
+    # frames it renders per step: the roots' stacks, then every inner node's and leaf's newest frame
+    fr_bytes = 32 * 28224 + sum(32 * 18 ** i for i in range(1, 4)) * 7056
+    rms = fp["kernel_ms_per_step"].get("render", 0.0)
+    fp["render_in_search"] = {"bytes_written_per_step": fr_bytes, "ms_per_step": rms,
+                              "gbs": fr_bytes / (rms / 1e3) / 1e9 if rms else None,
+                              "frac_of_copy_bandwidth": fr_bytes / (rms / 1e3) / 1e9 / pk["hbm_gbs"] if rms else None}
+    fp["what"] = ("the headline workload (32 roots, A=18, d=3, FP32-class) with BCTS_FLAG_FRAMES: node frames "
+                  "rendered per level, conv1 as tcgen05 GEMMs over them (roots / depth-1 whole stacks, parents' "
+                  "partial maps, leaves' newest slot)")
+    out["frame_path"] = fp
+    # precision form: 8 roots, A = 18, d = 4
+    wp = WORKLOADS["precision"]
+    prec = {}
+    for p in ("bf16", "fp8", "fp32"):
+        prec[p] = search_measure(bcts, torch, W18, 18, wp["d"], wp["n"], g, cc, p, 10, 3)
+    prec["vs_oracle"] = report_vs_oracle(bcts, W18, wp)
+    out["precision_form"] = prec
+    # batched form
+    out["batched_form"] = batched_measure(bcts, WORKLOADS["batched"], "bf16", 5, 3)
+    # serving form, below saturation
+    ws = WORKLOADS["serving"]
+    out["serving_form"] = serving_measure(bcts, ws, "bf16", 300.0, 2.0)
+    # the streaming kernels alone (a quarter of the stream workload's sizes)
+    out["streaming_kernels"] = stream_measure(bcts, torch, dict(WORKLOADS["stream"], n=1 << 18, frames=25_000,
+                                                                backup_roots=256), 2, 10)
+    return out
+
+
+def serving_measure(bcts, wl, precision, rate, seconds, rank=0, local=0, world=1):
+    """Serving form: Poisson arrivals from simulated episodes through bcts_submit /
+    bcts_poll; episodes advance by the returned action (bcts_env_step).  Returns the
+    measurement (decisions/s, leaf nodes/s, p50/p99 latency, the plain FP32
+    one-request-at-a-time baseline on a bounded sample, launches, clocks)."""
     A = 18
     W = inputs.qnet_weights(A, seed=1234)
     ctx = bcts.bcts_create(W, A, 4, wl["gamma"], wl["c"], precision=precision,
@@ -921,7 +1019,7 @@ def run_serving(args, wl):
         return (next(g) >> 11) / float(1 << 53)
 
     # warm-up: every depth alone, then two full-size mixed bursts, so that both
-    # workers have sized their buffers and tuned their leaf chunks before the clock
+    # workers have sized their buffers before the clock
     for d in (2, 3, 4):
         t = bcts.bcts_submit(ctx, episodes[:1], d, A)
         bcts.bcts_poll(ctx, t, A, timeout_us=-1)
@@ -973,6 +1071,7 @@ def run_serving(args, wl):
             time.sleep(0.0002)
         wall = time.perf_counter() - t0
     _, _, served_launches = bcts.bcts_profile(ctx, False)
+    ctx.close()
     # plain FP32 sequential baseline on a bounded sample of the same kind of requests
     pctx = bcts.bcts_create(W, A, 4, wl["gamma"], wl["c"], precision="fp32_simt")
     seq_roots = inputs.root_states(range(20000, 20012))
@@ -985,25 +1084,39 @@ def run_serving(args, wl):
     tseq = time.perf_counter() - tseq0
     pctx.close()
     lat.sort()
+    return {"offered_rate_req_s": rate, "arrival_seconds": seconds, "episodes": wl["n"], "precision": precision,
+            "decisions": completed, "wall_s": wall, "decisions_per_s": completed / wall,
+            "leaf_nodes_per_s": done_leaves / wall,
+            "latency_ms": {"p50": 1e3 * lat[len(lat) // 2] if lat else None,
+                           "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
+                           "what": "submit to completion seen by the poller, host wall clock"},
+            "plain_fp32_sequential": {"decisions_per_s": len(seq_roots) / tseq,
+                                      "leaf_nodes_per_s": seq_leaves / tseq,
+                                      "how": "one request at a time, FP32 CUDA-core Q-network, d cycling 2,3,4"},
+            "gpu_launches": served_launches, "clocks": _clock_line(clk, pk)}
+
+
+def run_serving(args, wl):
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_2107_01715_b300 import bcts
+    precision = args.precision or wl["precision"]
+    m = serving_measure(bcts, wl, precision, args.rate or wl["rate"], args.seconds or wl["seconds"], rank, local,
+                        world)
     if rank == 0:
-        line = {"metric": METRIC, "value": completed / wall, "unit": "decisions/s", "n_gpus": world,
-                "steps": completed, "warmup": 3, "ms_per_step": 1e3 * wall / max(completed, 1),
+        line = {"metric": METRIC, "value": m["decisions_per_s"], "unit": "decisions/s", "n_gpus": world,
+                "steps": m["decisions"], "warmup": 3, "ms_per_step": 1e3 * m["wall_s"] / max(m["decisions"], 1),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": precision,
                 "data": "synthetic",
-                "config": {"workload": wl["name"], "offered_rate_req_s": rate, "arrival_seconds": seconds,
-                           "episodes": wl["n"]},
-                "leaf_nodes_per_s": done_leaves / wall,
-                "latency_ms": {"p50": 1e3 * lat[len(lat) // 2] if lat else None,
-                               "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
-                               "what": "submit to completion seen by the poller, host wall clock"},
-                "plain_fp32_sequential": {"decisions_per_s": len(seq_roots) / tseq,
-                                          "leaf_nodes_per_s": seq_leaves / tseq,
-                                          "how": "one request at a time, FP32 CUDA-core Q-network, d cycling 2,3,4"},
-                "e2e": {"value": completed / wall, "unit": "decisions/s", "h2d_bytes_per_step": 80,
-                        "d2h_bytes_per_step": 4 + A * 4},
-                "gpu_launches": served_launches, "clocks": _clock_line(clk, pk)}
+                "config": {"workload": wl["name"], "offered_rate_req_s": m["offered_rate_req_s"],
+                           "arrival_seconds": m["arrival_seconds"], "episodes": wl["n"]},
+                "leaf_nodes_per_s": m["leaf_nodes_per_s"], "latency_ms": m["latency_ms"],
+                "plain_fp32_sequential": m["plain_fp32_sequential"],
+                "e2e": {"value": m["decisions_per_s"], "unit": "decisions/s", "h2d_bytes_per_step": 80,
+                        "d2h_bytes_per_step": 4 + 18 * 4},
+                "gpu_launches": m["gpu_launches"], "clocks": m["clocks"]}
         print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 def main():

@@ -85,7 +85,7 @@ typedef struct bcts_env_desc {
 
 typedef struct bcts_options {
     int precision;              /* BCTS_PREC_* (default BCTS_PREC_FP32) */
-    size_t frame_budget_bytes;  /* serving admission budget for in-flight leaf work (0 = 8 GiB) */
+    size_t frame_budget_bytes;  /* serving admission budget: device bytes of in-flight requests (0 = 8 GiB) */
     int max_roots;              /* serving: requests fused per pass (0 = 64) */
     int flags;                  /* BCTS_FLAG_* bits, 0 = defaults */
     int leaf_chunk;             /* leaves rendered + scored per pass (0 = automatic) */
@@ -217,17 +217,19 @@ BCTS_API int bcts_search_mixed(bcts_ctx *ctx, const bcts_state *roots, const int
 /*
  * Serving form: continuous batching.  bcts_submit queues one decision request
  * (root, depth d in [0, 6], A in [1, context A]) and returns at once with a
- * ticket.  Two worker threads (each with its own stream and buffers, sharing
- * the context's weights) take queued requests in arrival order while their
- * leaf work fits the frame budget (A^d x 28,224 bytes per request, default
- * 8 GiB, at most max_roots per pass, default 64) and run each admitted set as
- * one batched pass (bcts_search_mixed); while one pass is on the device, a
- * worker with fewer than about 1M queued leaves waits up to 2 ms for more.
- * Requests complete independently.  bcts_poll waits up to timeout_us
- * microseconds (0 = do not wait, <0 = wait without limit) for a ticket:
- * BCTS_OK with out_action (1 int32) and out_root_values (A floats, host)
- * filled and the ticket released; BCTS_PENDING if not finished; BCTS_ENOTICKET
- * for unknown tickets.  Both are thread-safe.
+ * ticket.  Three worker threads (each with its own stream and buffers, sharing
+ * the context's weights) take queued requests in arrival order while the
+ * device bytes they occupy in a pass fit the budget (frame_budget_bytes,
+ * default 8 GiB; per request its node levels, per-leaf values and tables and
+ * its leaves' parents' partial conv1 maps, about 310 MB at A = 18, d = 4; at
+ * most max_roots per pass, default 64) and run each admitted set as one batched
+ * pass (bcts_search_mixed), so up to three passes overlap on the device; while
+ * one pass is on the device, a worker with fewer than about 1M queued leaves
+ * waits up to 2 ms for more.  Requests complete independently.  bcts_poll waits
+ * up to timeout_us microseconds (0 = do not wait, <0 = wait without limit) for
+ * a ticket: BCTS_OK with out_action (1 int32) and out_root_values (A floats,
+ * host) filled and the ticket released; BCTS_PENDING if not finished;
+ * BCTS_ENOTICKET for unknown tickets.  Both are thread-safe.
  */
 BCTS_API int bcts_submit(bcts_ctx *ctx, const bcts_state *root, int d, int A, uint64_t *out_ticket);
 BCTS_API int bcts_poll(bcts_ctx *ctx, uint64_t ticket, int32_t *out_action, float *out_root_values, int timeout_us);

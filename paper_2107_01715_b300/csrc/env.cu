@@ -110,16 +110,14 @@ __host__ __device__ __forceinline__ int sprite_step(const bcts_state &s, int a, 
 
 constexpr int kExpandThreads = 256;
 
-__global__ void __launch_bounds__(kExpandThreads) expand_kernel(const uint4 *__restrict__ parents,
-                                                                const float *__restrict__ parent_R, uint32_t n_child,
-                                                                int A, float gamma_pow, uint4 *__restrict__ children,
-                                                                float *__restrict__ child_R,
-                                                                int8_t *__restrict__ child_reward) {
-  // the block's children pass through shared memory, so that their 80-byte
-  // states leave as whole consecutive 16-byte chunks (a thread's own five
-  // stores would each touch 32 scattered half sectors)
-  __shared__ uint4 stage[kExpandThreads * 5];
-  const uint32_t c0 = blockIdx.x * kExpandThreads;
+// Children c0 .. c0 + 255 of one level (one block): the block's children pass
+// through shared memory, so that their 80-byte states leave as whole consecutive
+// 16-byte chunks (a thread's own five stores would each touch 32 scattered half
+// sectors).
+__device__ __forceinline__ void expand_block(const uint4 *__restrict__ parents, const float *__restrict__ parent_R,
+                                             uint32_t n_child, int A, float gamma_pow, uint4 *__restrict__ children,
+                                             float *__restrict__ child_R, int8_t *__restrict__ child_reward,
+                                             uint32_t c0, uint4 *stage) {
   const uint32_t c = c0 + threadIdx.x;
   if (c < n_child) {
     const uint32_t p = c / uint32_t(A);
@@ -139,6 +137,28 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(const uint4 *__r
   __syncthreads();
   const uint32_t nb = n_child - c0 < uint32_t(kExpandThreads) ? n_child - c0 : uint32_t(kExpandThreads);
   for (uint32_t i = threadIdx.x; i < nb * 5; i += kExpandThreads) children[size_t(c0) * 5 + i] = stage[i];
+}
+
+__global__ void __launch_bounds__(kExpandThreads) expand_kernel(const uint4 *__restrict__ parents,
+                                                                const float *__restrict__ parent_R, uint32_t n_child,
+                                                                int A, float gamma_pow, uint4 *__restrict__ children,
+                                                                float *__restrict__ child_R,
+                                                                int8_t *__restrict__ child_reward) {
+  __shared__ uint4 stage[kExpandThreads * 5];
+  expand_block(parents, parent_R, n_child, A, gamma_pow, children, child_R, child_reward,
+               blockIdx.x * kExpandThreads, stage);
+}
+
+// One level of several independent trees (the batched form's (A, d) groups) in
+// one launch: group k owns blocks block_end[k - 1] .. block_end[k] - 1.
+__global__ void __launch_bounds__(kExpandThreads) expand_list_kernel(const __grid_constant__ ExpandList L) {
+  __shared__ uint4 stage[kExpandThreads * 5];
+  int k = 0;
+  while (k < L.n - 1 && blockIdx.x >= L.block_end[k]) ++k;
+  const uint32_t b0 = k ? L.block_end[k - 1] : 0u;
+  expand_block(reinterpret_cast<const uint4 *>(L.parents[k]), L.parent_R[k], L.n_child[k], L.A[k], L.gamma_pow[k],
+               reinterpret_cast<uint4 *>(L.children[k]), L.child_R[k], nullptr, (blockIdx.x - b0) * kExpandThreads,
+               stage);
 }
 
 // Frame layout per state: [4 slots][84 rows][21 words]; word (h, y, cx) holds the
@@ -214,6 +234,15 @@ int launch_render_newest(const bcts_state *states, int64_t n, uint8_t *frames, c
   ProfScope ps(K_RENDER, stream);
   render_newest_kernel<<<blocks, kRenderThreads, 0, stream>>>(reinterpret_cast<const uint4 *>(states), uint64_t(n),
                                                               reinterpret_cast<uint4 *>(frames));
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
+
+int launch_expand_list(const ExpandList &L, cudaStream_t stream) {
+  if (L.n <= 0) return BCTS_OK;
+  const uint32_t blocks = L.block_end[L.n - 1];
+  if (blocks == 0) return BCTS_OK;
+  ProfScope ps(K_EXPAND, stream);
+  expand_list_kernel<<<blocks, kExpandThreads, 0, stream>>>(L);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 

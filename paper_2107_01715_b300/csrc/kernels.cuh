@@ -9,6 +9,23 @@ namespace bcts {
 int launch_expand(const bcts_state *parents, const float *parent_R, int64_t n_parents, int A, float gamma_pow,
                   bcts_state *children, float *child_R, int8_t *child_reward, cudaStream_t stream);
 int launch_render(const bcts_state *states, int64_t n, uint8_t *frames, cudaStream_t stream);
+// One expansion level of up to kMaxListGroups independent trees in one launch
+// (the batched form's (A, d) groups): group k expands n_child[k] children of
+// parents[k] into children[k]; block_end is the running total of its blocks of
+// 256 children.
+constexpr int kMaxListGroups = 24;
+struct ExpandList {
+  int n = 0;
+  const bcts_state *parents[kMaxListGroups];
+  const float *parent_R[kMaxListGroups];
+  bcts_state *children[kMaxListGroups];
+  float *child_R[kMaxListGroups];
+  uint32_t n_child[kMaxListGroups];
+  uint32_t block_end[kMaxListGroups];
+  int A[kMaxListGroups];
+  float gamma_pow[kMaxListGroups];
+};
+int launch_expand_list(const ExpandList &L, cudaStream_t stream);
 // The newest history slot only: frames [n][84][84] (7,056 bytes per state).
 int launch_render_newest(const bcts_state *states, int64_t n, uint8_t *frames, cudaStream_t stream);
 constexpr int kSlotBytes = kPix * kPix;  // 7,056
@@ -115,5 +132,27 @@ int launch_segment_max(const float *R, const float *maxq, int64_t n_seg, int64_t
 int launch_finalize(const float *q0, const float *maxq1, const float *r1, const float *V, int n, int A,
                     int depth, int A_stride, float gamma, float gamma_d, float corr, int32_t *action,
                     float *values, cudaStream_t stream, int q_stride = 0, int exact_gev = 0);
+
+// Backup of several groups in one launch each for the segment maxima and the
+// finalize step (the batched form): group k has roots root_end[k-1] ..
+// root_end[k] - 1 and segments seg_end[k-1] .. seg_end[k] - 1 (n_k A_k each of
+// seg_len[k] = A_k^(d_k - 1) leaves; none for d_k = 0), writes V[k] (order keys,
+// n_k A_k words of storage), action[k], values[k] (rows A_stride apart).
+// Segments must be shorter than the split threshold of launch_segment_max.
+struct BackupList {
+  int n = 0;
+  const float *R[kMaxListGroups], *maxq[kMaxListGroups];
+  float *V[kMaxListGroups];
+  const float *q0[kMaxListGroups], *maxq1[kMaxListGroups], *r1[kMaxListGroups];
+  int32_t *action[kMaxListGroups];
+  float *values[kMaxListGroups];
+  int64_t seg_end[kMaxListGroups], root_end[kMaxListGroups];
+  uint32_t seg_len[kMaxListGroups];
+  int A[kMaxListGroups], depth[kMaxListGroups];
+  float gamma_d[kMaxListGroups], gev_e[kMaxListGroups], gev_o[kMaxListGroups];
+  int A_stride = 0, q_stride = 0, exact_gev = 0;
+  float gamma = 0.f, corr = 0.f;
+};
+int launch_backup_list(BackupList &L, cudaStream_t st);
 
 }  // namespace bcts

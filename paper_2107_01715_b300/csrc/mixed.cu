@@ -8,9 +8,12 @@
 // tensor-core layer kernel sees the whole batch.  The max over actions uses
 // each node's own A (FC2 rows 0..A-1).  Backup and the Eq. 7 correction run
 // per group.  For a composition seen before, the whole device part of the pass
-// (copies included) is replayed from a captured CUDA graph.  The leaf chunk
-// size of the union evaluation is picked by timing the candidates on the first
-// pass of a new leaf-count bucket (optionally persisted as JSON).
+// (copies included) is replayed from a captured CUDA graph.  The kernel
+// configuration of the union leaf evaluation -- the leaf chunk and, for conv2
+// and conv3 each, the TMA im2col kernel (taps per stage) or the cp.async gather
+// (K blocks per stage) -- is picked by timing every candidate on the plan's own
+// leaves on the first pass of a new (precision, leaf-count) bucket, and kept in
+// memory (and in the file named by BCTS_TUNE_FILE).
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -19,6 +22,7 @@
 #include <map>
 #include <sstream>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "search.cuh"
@@ -31,7 +35,7 @@ struct MixedGroup {
   int64_t l1_off = 0;     // first depth-1 node in the union level-1 buffer
   int64_t leaf_off = 0;   // first leaf in the union leaf buffer (d >= 2)
   int64_t nleaf = 0;      // n * A^d for d >= 2
-  int64_t mid_max = 0;    // largest intermediate level (depths 2 .. d-1)
+  int64_t mid_off[kMaxDepth + 1] = {};  // first node of its level i (2 .. d-1) in the shared level buffer
   int64_t zoff = 0;       // first of its leaves' parents in the union partial-map buffer (d >= 2)
 };
 
@@ -40,6 +44,7 @@ struct MixedPlan {
   std::vector<int> order;  // sorted position -> caller's root index
   std::vector<MixedGroup> groups;
   int64_t n1 = 0, nleaf = 0, mid = 0;
+  int64_t mid_fill[kMaxDepth + 1] = {};  // nodes of all groups at each intermediate level
   int64_t nz = 0;       // leaves' parents of all groups (one partial conv1 map each)
   bool use_z = false;   // leaves' conv1 from the parents' partial maps
   std::string key;
@@ -68,7 +73,11 @@ struct MixedState {
   std::map<std::string, int> seen;
   std::map<std::string, GraphEntry> graphs;
   uint64_t use_clock = 0;
-  std::map<std::string, int64_t> tuned_chunk;  // leaf-count bucket -> chunk
+  struct Tuned {
+    int64_t chunk;
+    int conv_mask;
+  };
+  std::map<std::string, Tuned> tuned;  // (precision, leaf-count bucket) -> configuration
   bool tune_loaded = false;
   ~MixedState() {
     for (auto &kv : graphs)
@@ -166,29 +175,72 @@ static int mixed_enqueue(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_
   bcts_state *L1 = static_cast<bcts_state *>(m->L1.p);
   float *r1 = static_cast<float *>(m->r1.p);
   uint8_t *nA1 = static_cast<uint8_t *>(m->nodeA1.p);
-  for (const MixedGroup &g : pl.groups) {
-    if (g.d < 1) continue;
-    if ((rc = launch_expand(roots + g.root_off, nullptr, g.n, g.A, 1.f, L1 + g.l1_off, r1 + g.l1_off, nullptr,
-                            st)) != BCTS_OK)
-      return c->fail(rc, "expand launch failed");
-    BCTS_CUDA_TRY(cudaMemsetAsync(nA1 + g.l1_off, g.A, size_t(g.n) * g.A, st), c->err);
+  // One expansion launch per level for all groups that reach it (work lists of up
+  // to kMaxListGroups groups).  dst(g) gives a group's destination states and R.
+  auto expand_level = [&](const std::vector<const MixedGroup *> &gs, auto src, auto dst, double gp) -> int {
+    for (size_t s0 = 0; s0 < gs.size(); s0 += kMaxListGroups) {
+      ExpandList L;
+      uint32_t blocks = 0;
+      for (size_t k = s0; k < gs.size() && L.n < kMaxListGroups; ++k) {
+        const MixedGroup &g = *gs[k];
+        const auto sp = src(g);
+        const auto dp = dst(g);
+        L.parents[L.n] = sp.first;
+        L.parent_R[L.n] = sp.second;
+        L.children[L.n] = dp.first;
+        L.child_R[L.n] = dp.second;
+        L.A[L.n] = g.A;
+        L.gamma_pow[L.n] = float(gp);
+        L.n_child[L.n] = uint32_t(dp.count);
+        blocks += uint32_t((dp.count + 255) / 256);
+        L.block_end[L.n] = blocks;
+        ++L.n;
+      }
+      if (launch_expand_list(L, st) != BCTS_OK) return c->fail(BCTS_ECUDA, "expand launch failed");
+    }
+    return BCTS_OK;
+  };
+  struct Dst {
+    bcts_state *first;
+    float *second;
+    int64_t count;
+  };
+  {
+    std::vector<const MixedGroup *> gs;
+    for (const MixedGroup &g : pl.groups)
+      if (g.d >= 1) gs.push_back(&g);
+    rc = expand_level(
+        gs, [&](const MixedGroup &g) { return std::make_pair(roots + g.root_off, static_cast<const float *>(nullptr)); },
+        [&](const MixedGroup &g) { return Dst{L1 + g.l1_off, r1 + g.l1_off, int64_t(g.n) * g.A}; }, 1.0);
+    if (rc != BCTS_OK) return rc;
+    for (const MixedGroup *g : gs)
+      BCTS_CUDA_TRY(cudaMemsetAsync(nA1 + g->l1_off, g->A, size_t(g->n) * g->A, st), c->err);
   }
   float *maxq1 = static_cast<float *>(m->maxq1.p);
   if (pl.n1 > 0 && (rc = c->eval_nodes_ref(L1, pl.n1, nullptr, maxq1, st, nA1)) != BCTS_OK) return rc;
   bcts_state *leaves = static_cast<bcts_state *>(m->leaves.p);
   float *Rleaf = static_cast<float *>(m->Rleaf.p);
   uint8_t *nAl = static_cast<uint8_t *>(m->nodeA_leaf.p);
-  for (const MixedGroup &g : pl.groups) {
-    if (g.d < 2) continue;
-    const bcts_state *cur = L1 + g.l1_off;
-    const float *curR = r1 + g.l1_off;
-    int64_t cnt = int64_t(g.n) * g.A;
-    double gp = 1.0;
-    for (int i = 1; i < g.d; ++i) {
-      gp *= double(c->gamma);
-      const bool last = i == g.d - 1;
-      if (last && pl.use_z) {
+  // levels 1 .. d-1 -> 2 .. d: a group's level i lives in L1 (i = 1) or at its
+  // offset in mid[i & 1] (2 <= i < d); its last expansion writes its leaves
+  int maxd = 0;
+  for (const MixedGroup &g : pl.groups) maxd = std::max(maxd, g.d);
+  double gp = 1.0;
+  auto level_src = [&](const MixedGroup &g, int i) {
+    if (i == 1) return std::make_pair(static_cast<const bcts_state *>(L1 + g.l1_off), static_cast<const float *>(r1 + g.l1_off));
+    return std::make_pair(static_cast<const bcts_state *>(static_cast<bcts_state *>(m->mid[i & 1].p) + g.mid_off[i]),
+                          static_cast<const float *>(static_cast<float *>(m->Rmid[i & 1].p) + g.mid_off[i]));
+  };
+  for (int i = 1; i < maxd; ++i) {
+    gp *= double(c->gamma);
+    std::vector<const MixedGroup *> gs;
+    for (const MixedGroup &g : pl.groups) {
+      if (g.d <= i) continue;
+      gs.push_back(&g);
+      if (i == g.d - 1 && pl.use_z) {
         // the leaves' parents: their partial conv1 maps, and each leaf's parent index
+        const int64_t cnt = int64_t(g.n) * ipow(g.A, i);
+        const bcts_state *cur = level_src(g, i).first;
         float *z = static_cast<float *>(m->zbuf.p) + size_t(g.zoff) * kP1 * kC1;
         const int64_t chunk = c->chunk_nodes();
         for (int64_t off = 0; off < cnt; off += chunk) {
@@ -200,46 +252,80 @@ static int mixed_enqueue(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_
             static_cast<uint32_t *>(m->zparent.p) + g.leaf_off, g.nleaf, g.A, uint32_t(g.zoff));
         if (cudaGetLastError() != cudaSuccess) return c->fail(BCTS_ECUDA, "parent table launch failed");
       }
-      bcts_state *nxt = last ? leaves + g.leaf_off : static_cast<bcts_state *>(m->mid[i & 1].p);
-      float *nxtR = last ? Rleaf + g.leaf_off : static_cast<float *>(m->Rmid[i & 1].p);
-      if ((rc = launch_expand(cur, curR, cnt, g.A, float(gp), nxt, nxtR, nullptr, st)) != BCTS_OK)
-        return c->fail(rc, "expand launch failed");
-      cur = nxt;
-      curR = nxtR;
-      cnt *= g.A;
     }
-    BCTS_CUDA_TRY(cudaMemsetAsync(nAl + g.leaf_off, g.A, size_t(g.nleaf), st), c->err);
+    rc = expand_level(
+        gs, [&](const MixedGroup &g) { return level_src(g, i); },
+        [&](const MixedGroup &g) {
+          const int64_t cnt = int64_t(g.n) * ipow(g.A, i + 1);
+          if (i + 1 == g.d) return Dst{leaves + g.leaf_off, Rleaf + g.leaf_off, cnt};
+          return Dst{static_cast<bcts_state *>(m->mid[(i + 1) & 1].p) + g.mid_off[i + 1],
+                     static_cast<float *>(m->Rmid[(i + 1) & 1].p) + g.mid_off[i + 1], cnt};
+        },
+        gp);
+    if (rc != BCTS_OK) return rc;
   }
+  for (const MixedGroup &g : pl.groups)
+    if (g.d >= 2) BCTS_CUDA_TRY(cudaMemsetAsync(nAl + g.leaf_off, g.A, size_t(g.nleaf), st), c->err);
   float *maxq_leaf = static_cast<float *>(m->maxq_leaf.p);
   if (pl.nleaf > 0 &&
       (rc = c->eval_nodes(leaves, pl.nleaf, nullptr, maxq_leaf, st, nAl,
                           pl.use_z ? static_cast<const float *>(m->zbuf.p) : nullptr, 0,
                           pl.use_z ? static_cast<const uint32_t *>(m->zparent.p) : nullptr)) != BCTS_OK)
     return rc;
-  // backup per group
+  // backup of every group: one segment-max and one finalize launch per work list
   float *V = static_cast<float *>(m->V.p);
   int32_t *act = static_cast<int32_t *>(m->act.p);
   float *val = static_cast<float *>(m->val.p);
+  // groups whose subtrees are too long for one warp per segment (A^(d-1) >= 8192
+  // leaves) back up with their own launches
+  std::vector<const MixedGroup *> listed;
   for (const MixedGroup &g : pl.groups) {
-    const float *gq0 = q0 + size_t(g.root_off) * As;
-    int32_t *gact = act + g.root_off;
-    float *gval = val + size_t(g.root_off) * As;
-    if (g.d == 0) {
-      if ((rc = launch_finalize(gq0, nullptr, nullptr, nullptr, g.n, g.A, 0, As, c->gamma, 1.f, c->corr, gact, gval,
-                                st, As)) != BCTS_OK)
-        return c->fail(rc, "finalize launch failed");
-      continue;
+    if (g.d >= 1 && ipow(g.A, g.d - 1) >= 8192) {
+      double gd = 1.0;
+      for (int i = 0; i < g.d; ++i) gd *= double(c->gamma);
+      float *gV = V + size_t(g.root_off) * As;
+      if ((rc = launch_segment_max(Rleaf + g.leaf_off, maxq_leaf + g.leaf_off, int64_t(g.n) * g.A,
+                                   ipow(g.A, g.d - 1), float(gd), gV, st)) != BCTS_OK ||
+          (rc = launch_finalize(q0 + size_t(g.root_off) * As, maxq1 + g.l1_off, r1 + g.l1_off, gV, g.n, g.A, g.d,
+                                As, c->gamma, float(gd), c->corr, act + g.root_off, val + size_t(g.root_off) * As,
+                                st, As, c->exact_gev ? 1 : 0)) != BCTS_OK)
+        return c->fail(rc, "backup launch failed");
+    } else {
+      listed.push_back(&g);
     }
-    double gd = 1.0;
-    for (int i = 0; i < g.d; ++i) gd *= double(c->gamma);
-    const float *lR = g.d == 1 ? r1 + g.l1_off : Rleaf + g.leaf_off;
-    const float *lM = g.d == 1 ? maxq1 + g.l1_off : maxq_leaf + g.leaf_off;
-    float *gV = V + size_t(g.root_off) * As;  // [n_g][A_g] inside the group's rows
-    if ((rc = launch_segment_max(lR, lM, int64_t(g.n) * g.A, ipow(g.A, g.d - 1), float(gd), gV, st)) != BCTS_OK)
-      return c->fail(rc, "backup launch failed");
-    if ((rc = launch_finalize(gq0, maxq1 + g.l1_off, r1 + g.l1_off, gV, g.n, g.A, g.d, As, c->gamma, float(gd),
-                              c->corr, gact, gval, st, As, c->exact_gev ? 1 : 0)) != BCTS_OK)
-      return c->fail(rc, "finalize launch failed");
+  }
+  for (size_t s0 = 0; s0 < listed.size(); s0 += kMaxListGroups) {
+    BackupList L;
+    L.A_stride = As;
+    L.q_stride = As;
+    L.exact_gev = c->exact_gev ? 1 : 0;
+    L.gamma = c->gamma;
+    L.corr = c->corr;
+    int64_t segs = 0, nroots = 0;
+    for (size_t k = s0; k < listed.size() && L.n < kMaxListGroups; ++k) {
+      const MixedGroup &g = *listed[k];
+      double gd = 1.0;
+      for (int i = 0; i < g.d; ++i) gd *= double(c->gamma);
+      const int j = L.n;
+      L.R[j] = g.d == 1 ? r1 + g.l1_off : (g.d >= 2 ? Rleaf + g.leaf_off : nullptr);
+      L.maxq[j] = g.d == 1 ? maxq1 + g.l1_off : (g.d >= 2 ? maxq_leaf + g.leaf_off : nullptr);
+      L.V[j] = V + size_t(g.root_off) * As;  // [n_g][A_g] inside the group's rows
+      L.q0[j] = q0 + size_t(g.root_off) * As;
+      L.maxq1[j] = g.d >= 1 ? maxq1 + g.l1_off : nullptr;
+      L.r1[j] = g.d >= 1 ? r1 + g.l1_off : nullptr;
+      L.action[j] = act + g.root_off;
+      L.values[j] = val + size_t(g.root_off) * As;
+      L.A[j] = g.A;
+      L.depth[j] = g.d;
+      L.seg_len[j] = g.d >= 1 ? uint32_t(ipow(g.A, g.d - 1)) : 1u;
+      L.gamma_d[j] = float(gd);
+      segs += g.d >= 1 ? int64_t(g.n) * g.A : 0;
+      nroots += g.n;
+      L.seg_end[j] = segs;
+      L.root_end[j] = nroots;
+      ++L.n;
+    }
+    if ((rc = launch_backup_list(L, st)) != BCTS_OK) return c->fail(rc, "backup launch failed");
   }
   BCTS_CUDA_TRY(cudaMemcpyAsync(hs + in_b, act, size_t(pl.n) * 4, cudaMemcpyDeviceToHost, st), c->err);
   BCTS_CUDA_TRY(
@@ -254,11 +340,12 @@ static void load_tune(MixedState *m) {
   if (f.empty()) return;
   std::ifstream in(f);
   std::string line;
-  while (std::getline(in, line)) {  // lines: "<precision>:<bucket> <chunk>" (one JSON-free record per line)
+  while (std::getline(in, line)) {  // lines: "<precision>:<bucket> <chunk> <conv mask>"
     std::istringstream ss(line);
     std::string k;
     int64_t v;
-    if (ss >> k >> v) m->tuned_chunk[k] = v;
+    int mask;
+    if (ss >> k >> v >> mask) m->tuned[k] = {v, mask};
   }
 }
 
@@ -266,50 +353,58 @@ static void save_tune(MixedState *m) {
   const std::string f = tune_file();
   if (f.empty()) return;
   std::ofstream out(f);
-  for (auto &kv : m->tuned_chunk) out << kv.first << " " << kv.second << "\n";
+  for (auto &kv : m->tuned) out << kv.first << " " << kv.second.chunk << " " << kv.second.conv_mask << "\n";
 }
 
-// Pick the union-leaf chunk for this bucket by timing the candidates on the
-// plan's own leaves (first pass of a new bucket only).
-static int autotune_chunk(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_t st) {
+// Pick the union-leaf configuration for this bucket by timing the candidates
+// (leaf chunk x conv2 / conv3 kernel variant) on the plan's own leaves (first
+// pass of a new bucket only; each candidate is run once to size its scratch and
+// once timed).
+static int autotune(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_t st) {
   if (c->opt.leaf_chunk > 0 || pl.nleaf < 65536 || c->precision == BCTS_PREC_FP32_SIMT) return BCTS_OK;
   if (!m->tune_loaded) load_tune(m);
   const std::string key = std::to_string(c->precision) + ":" + std::to_string(leaf_bucket(pl.nleaf));
-  auto it = m->tuned_chunk.find(key);
-  if (it != m->tuned_chunk.end()) {
-    c->chunk_override = it->second;
+  auto it = m->tuned.find(key);
+  if (it != m->tuned.end()) {
+    c->chunk_override = it->second.chunk;
+    c->conv_mask = it->second.conv_mask;
     return BCTS_OK;
   }
-  const int64_t cands[] = {16384, 32768, 65536};
+  const int64_t chunks[] = {16384, 32768, 65536};
+  const int masks[] = {0, 1, 2, 3};  // conv2 (bit 0) / conv3 (bit 1) through TMA
   float best_ms = 1e30f;
-  int64_t best = 32768;
+  MixedState::Tuned best{32768, -1};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int rc = BCTS_OK;
-  for (int64_t cand : cands) {
-    c->chunk_override = cand;
-    // warm (sizes the scratch), then time
-    for (int rep = 0; rep < 2 && rc == BCTS_OK; ++rep) {
-      cudaEventRecord(e0, st);
-      rc = c->eval_nodes(static_cast<bcts_state *>(m->leaves.p), pl.nleaf, nullptr,
-                         static_cast<float *>(m->maxq_leaf.p), st, static_cast<uint8_t *>(m->nodeA_leaf.p));
-      cudaEventRecord(e1, st);
+  for (int64_t chunk : chunks) {
+    for (int mask : masks) {
+      c->chunk_override = chunk;
+      c->conv_mask = mask;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && rc == BCTS_OK; ++rep) {
+        cudaEventRecord(e0, st);
+        rc = c->eval_nodes(static_cast<bcts_state *>(m->leaves.p), pl.nleaf, nullptr,
+                           static_cast<float *>(m->maxq_leaf.p), st, static_cast<uint8_t *>(m->nodeA_leaf.p));
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (rc != BCTS_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = {chunk, mask};
+      }
     }
     if (rc != BCTS_OK) break;
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = cand;
-    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != BCTS_OK) return rc;
-  c->chunk_override = best;
-  m->tuned_chunk[key] = best;
+  c->chunk_override = best.chunk;
+  c->conv_mask = best.conv_mask;
+  m->tuned[key] = best;
   save_tune(m);
   return BCTS_OK;
 }
@@ -347,7 +442,12 @@ int Ctx::run_mixed(const bcts_state *, const bcts_state *h_roots, const int32_t 
       pl.nleaf += g.nleaf;
       g.zoff = pl.nz;
       pl.nz += int64_t(g.n) * ipow(g.A, g.d - 1);
-      if (g.d >= 3) pl.mid = std::max<int64_t>(pl.mid, int64_t(g.n) * ipow(g.A, g.d - 1));
+      // intermediate levels 2 .. d-1: every group's level i in one buffer (mid[i & 1])
+      for (int lv = 2; lv < g.d; ++lv) {
+        g.mid_off[lv] = pl.mid_fill[lv];
+        pl.mid_fill[lv] += int64_t(g.n) * ipow(g.A, lv);
+        pl.mid = std::max<int64_t>(pl.mid, pl.mid_fill[lv]);
+      }
     }
     if (pl.nleaf > 0x7FFFFFFFLL) return fail(BCTS_EINVAL, "batched search too large: more than 2^31 - 1 leaves");
     key << g.A << "x" << g.d << "x" << g.n << ";";
@@ -362,7 +462,7 @@ int Ctx::run_mixed(const bcts_state *, const bcts_state *h_roots, const int32_t 
   if ((rc = mixed_ensure(this, m, pl)) != BCTS_OK) return rc;
   char *hs = static_cast<char *>(m->host.p);
   for (int i = 0; i < n; ++i) std::memcpy(hs + size_t(i) * kStateBytes, h_roots + pl.order[i], kStateBytes);
-  if ((rc = autotune_chunk(this, m, pl, stream)) != BCTS_OK) return rc;
+  if ((rc = autotune(this, m, pl, stream)) != BCTS_OK) return rc;
   if (m->seen.size() >= kMaxSeen) m->seen.clear();
   const int times_seen = m->seen[pl.key]++;
   auto git = m->graphs.find(pl.key);
@@ -451,16 +551,19 @@ extern "C" int bcts_search_mixed(bcts_ctx *ctx, const bcts_state *roots, const i
   if (n < 0 || (n > 0 && (!roots || !depths || !actions || !out_action || !out_values)))
     return c->fail(BCTS_EINVAL, "bcts_search_mixed: invalid argument");
   if (n == 0) return BCTS_OK;
+  const int saved_mask = c->conv_mask;
   int rc = c->run_mixed(nullptr, roots, depths, actions, n, nullptr, nullptr);
   if (rc != BCTS_OK) {
     cudaStreamSynchronize(c->stream);
     c->chunk_override = 0;
+    c->conv_mask = saved_mask;
     return rc;
   }
   int herr = 0;
   BCTS_CUDA_TRY(cudaStreamSynchronize(c->stream), c->err);
   BCTS_CUDA_TRY(cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), c->err);
   c->chunk_override = 0;
+  c->conv_mask = saved_mask;
   if (herr != 0) {
     cudaMemset(c->d_err, 0, sizeof(int));
     return c->fail(BCTS_EDEVICE, "a kernel reported error code " + std::to_string(herr));

@@ -44,26 +44,46 @@ __device__ __forceinline__ float key_value(uint32_t k) {
 // (Alg. 1's leaf term; Eq. 1's max over a_1..a_d for root action s mod A).
 // Short segments: one warp per segment, four coalesced loads of each array in
 // flight per lane.
+// One segment by one warp.
+__device__ __forceinline__ void segment_max_warp(const float *__restrict__ r, const float *__restrict__ q,
+                                                 int64_t seg_len, float gamma_pow, uint32_t *__restrict__ out,
+                                                 int lane) {
+  float best = -INFINITY;
+  int64_t i = lane;
+  for (; i + 96 < seg_len; i += 128) {
+    const float r0 = __ldg(r + i), r1 = __ldg(r + i + 32), r2 = __ldg(r + i + 64), r3 = __ldg(r + i + 96);
+    const float q0 = __ldg(q + i), q1 = __ldg(q + i + 32), q2 = __ldg(q + i + 64), q3 = __ldg(q + i + 96);
+    best = fmaxf(fmaxf(best, fmaxf(r0 + gamma_pow * q0, r1 + gamma_pow * q1)),
+                 fmaxf(r2 + gamma_pow * q2, r3 + gamma_pow * q3));
+  }
+  for (; i < seg_len; i += 32) best = fmaxf(best, __ldg(r + i) + gamma_pow * __ldg(q + i));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (lane == 0) *out = order_key(best);
+}
+
 __global__ void __launch_bounds__(256) segment_max_warp_kernel(const float *__restrict__ R,
                                                                const float *__restrict__ maxq, int64_t n_seg,
                                                                int64_t seg_len, float gamma_pow,
                                                                uint32_t *__restrict__ V) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = int64_t(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t s = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n_seg; s += nwarps) {
-    const float *r = R + s * seg_len, *q = maxq + s * seg_len;
-    float best = -INFINITY;
-    int64_t i = lane;
-    for (; i + 96 < seg_len; i += 128) {
-      const float r0 = __ldg(r + i), r1 = __ldg(r + i + 32), r2 = __ldg(r + i + 64), r3 = __ldg(r + i + 96);
-      const float q0 = __ldg(q + i), q1 = __ldg(q + i + 32), q2 = __ldg(q + i + 64), q3 = __ldg(q + i + 96);
-      best = fmaxf(fmaxf(best, fmaxf(r0 + gamma_pow * q0, r1 + gamma_pow * q1)),
-                   fmaxf(r2 + gamma_pow * q2, r3 + gamma_pow * q3));
-    }
-    for (; i < seg_len; i += 32) best = fmaxf(best, __ldg(r + i) + gamma_pow * __ldg(q + i));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (lane == 0) V[s] = order_key(best);
+  for (int64_t s = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n_seg; s += nwarps)
+    segment_max_warp(R + s * seg_len, maxq + s * seg_len, seg_len, gamma_pow, V + s, lane);
+}
+
+// The segments of several independent searches (the batched form's (A, d)
+// groups) in one launch: group k's segments are seg_end[k - 1] .. seg_end[k] - 1.
+__global__ void __launch_bounds__(256) segment_max_list_kernel(const __grid_constant__ BackupList L) {
+  const int lane = threadIdx.x & 31;
+  const int64_t total = L.seg_end[L.n - 1];
+  const int64_t nwarps = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t s = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); s < total; s += nwarps) {
+    int k = 0;
+    while (k < L.n - 1 && s >= L.seg_end[k]) ++k;
+    const int64_t ls = s - (k ? L.seg_end[k - 1] : 0), len = L.seg_len[k];
+    segment_max_warp(L.R[k] + ls * len, L.maxq[k] + ls * len, len, L.gamma_d[k],
+                     reinterpret_cast<uint32_t *>(L.V[k]) + ls, lane);
   }
 }
 
@@ -129,14 +149,11 @@ __device__ __forceinline__ void warp_argmax_lowest(float &v, int &idx) {
 // host computed for A^d - A^(d-1) and A^(d-1) leaves), corrected values (Eq. 3,
 // scaled by c) and the action (Eq. 4).  V holds the segment maxima as order
 // keys; `values` may alias V (each lane reads its own key before it writes).
-__global__ void __launch_bounds__(256) finalize_kernel(const float *__restrict__ q0, const float *__restrict__ maxq1,
-                                                       const float *__restrict__ r1, const uint32_t *V, int n,
-                                                       int A, int depth, int A_stride, float gamma, float gamma_d,
-                                                       float corr, int32_t *__restrict__ action, float *values,
-                                                       int q_stride, int exact_gev, float gev_e, float gev_o) {
-  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= n) return;  // whole warps leave together
+__device__ __forceinline__ void finalize_root(const float *__restrict__ q0, const float *__restrict__ maxq1,
+                                              const float *__restrict__ r1, const uint32_t *V, int64_t i, int A,
+                                              int depth, int A_stride, float gamma, float gamma_d, float corr,
+                                              int32_t *__restrict__ action, float *values, int q_stride,
+                                              int exact_gev, float gev_e, float gev_o, int lane) {
   const bool on = lane < A;
   const float q = on ? q0[size_t(i) * q_stride + lane] : -INFINITY;
   float bq = q;
@@ -171,6 +188,29 @@ __global__ void __launch_bounds__(256) finalize_kernel(const float *__restrict__
   int best = on ? lane : 64;
   warp_argmax_lowest(v, best);
   if (lane == 0) action[i] = best;
+}
+
+__global__ void __launch_bounds__(256) finalize_kernel(const float *__restrict__ q0, const float *__restrict__ maxq1,
+                                                       const float *__restrict__ r1, const uint32_t *V, int n,
+                                                       int A, int depth, int A_stride, float gamma, float gamma_d,
+                                                       float corr, int32_t *__restrict__ action, float *values,
+                                                       int q_stride, int exact_gev, float gev_e, float gev_o) {
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (i >= n) return;  // whole warps leave together
+  finalize_root(q0, maxq1, r1, V, i, A, depth, A_stride, gamma, gamma_d, corr, action, values, q_stride, exact_gev,
+                gev_e, gev_o, threadIdx.x & 31);
+}
+
+// The roots of several groups in one launch: group k's roots are
+// root_end[k - 1] .. root_end[k] - 1, each with its own A, d and arrays.
+__global__ void __launch_bounds__(256) finalize_list_kernel(const __grid_constant__ BackupList L) {
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (i >= L.root_end[L.n - 1]) return;
+  int k = 0;
+  while (k < L.n - 1 && i >= L.root_end[k]) ++k;
+  finalize_root(L.q0[k], L.maxq1[k], L.r1[k], reinterpret_cast<const uint32_t *>(L.V[k]),
+                i - (k ? L.root_end[k - 1] : 0), L.A[k], L.depth[k], L.A_stride, L.gamma, L.gamma_d[k], L.corr,
+                L.action[k], L.values[k], L.q_stride, L.exact_gev, L.gev_e[k], L.gev_o[k], threadIdx.x & 31);
 }
 
 }  // namespace
@@ -276,6 +316,29 @@ int launch_finalize(const float *q0, const float *maxq1, const float *r1, const 
   finalize_kernel<<<unsigned((int64_t(n) * 32 + 255) / 256), 256, 0, st>>>(
       q0, maxq1, r1, reinterpret_cast<const uint32_t *>(V), n, A, depth, A_stride, gamma, gamma_d, corr, action,
       values, q_stride > 0 ? q_stride : A, exact_gev, gev_e, gev_o);
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
+
+int launch_backup_list(BackupList &L, cudaStream_t st) {
+  if (L.n <= 0) return BCTS_OK;
+  ProfScope ps(K_BACKUP, st);
+  for (int k = 0; k < L.n; ++k) {
+    if (L.A[k] > 32 || L.A_stride > 32 || (L.depth[k] >= 1 && L.seg_len[k] >= 2 * kSegPart)) return BCTS_EINVAL;
+    L.gev_e[k] = L.gev_o[k] = 0.f;
+    if (L.exact_gev && L.depth[k] >= 1) {
+      const double n_o = std::pow(double(L.A[k]), double(L.depth[k] - 1));
+      const double n_e = std::pow(double(L.A[k]), double(L.depth[k])) - n_o;
+      L.gev_e[k] = float(gev_shift_host(n_e));
+      L.gev_o[k] = float(gev_shift_host(n_o));
+    }
+  }
+  const int64_t segs = L.seg_end[L.n - 1];
+  if (segs > 0) {
+    const int64_t blocks = (segs + 7) / 8, cap = int64_t(num_sms_backup()) * 8;
+    segment_max_list_kernel<<<unsigned(blocks < cap ? blocks : cap), 256, 0, st>>>(L);
+  }
+  const int64_t roots = L.root_end[L.n - 1];
+  finalize_list_kernel<<<unsigned((roots * 32 + 255) / 256), 256, 0, st>>>(L);
   return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
 }
 

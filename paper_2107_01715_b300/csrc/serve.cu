@@ -1,15 +1,15 @@
 // serve.cu -- serving form: continuous batching of decision requests.
 //
-// bcts_submit queues a request (root, d, A) and returns a ticket at once.  Two
+// bcts_submit queues a request (root, d, A) and returns a ticket at once.  Three
 // worker threads, each with its own stream and buffers (a context sharing the
 // owner's weights), repeatedly take as many queued requests as the pass limit
 // and the admission budget allow and run them as one batched search pass (the
 // mixed form: every Q-network evaluation of the pass in one batch).  Requests
-// that arrive while a pass is on the GPU wait only for the next free worker,
-// so two passes overlap on the device.  A request is admitted while the frame
-// bytes of its leaves (A^d stacks of 28,224 bytes) fit in what the budget has
-// left; a request larger than the whole budget runs alone.  bcts_poll returns
-// a request's result as soon as its pass has finished.
+// that arrive while passes are on the GPU wait only for the next free worker,
+// so up to three passes overlap on the device.  A request is admitted while the
+// device bytes its part of a pass occupies (request_cost) fit in what the
+// budget has left; a request larger than the whole budget runs alone.
+// bcts_poll returns a request's result as soon as its pass has finished.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -29,7 +29,8 @@ struct ServeRequest {
   int status = BCTS_PENDING;
   int32_t action = -1;
   std::vector<float> values;
-  size_t cost = 0;
+  size_t cost = 0;    // device bytes it occupies in a pass (request_cost)
+  size_t leaves = 0;  // A^d
 };
 
 struct ServeState {
@@ -43,8 +44,8 @@ struct ServeState {
   size_t budget = 0, inflight = 0;
   int max_batch = 64;
   int busy_workers = 0;
-  size_t queued_cost = 0;  // sum of the queued requests' costs
-  static constexpr int kWorkers = 2;
+  size_t queued_leaves = 0;  // leaves of the queued requests
+  static constexpr int kWorkers = 3;
   std::thread worker[kWorkers];
   Ctx *wctx[kWorkers] = {};
 };
@@ -54,10 +55,20 @@ namespace {
 constexpr auto kWindow = std::chrono::microseconds(2000);
 constexpr size_t kFullPassLeaves = size_t(1) << 20;  // about 1M leaves keep all SMs busy
 
+// Device bytes one request occupies in a batched pass (mixed.cu's buffers): its
+// node levels (80-byte state + FP32 R each; intermediate levels ping-pong), per
+// leaf its max Q, action count and parent index, the FP32 partial conv1 map of
+// each of its leaves' parents (51,200 bytes), and its root's and depth-1 nodes'
+// values.  The Q-network's activation maps of a leaf chunk are a per-worker
+// constant, not charged per request.
 size_t request_cost(int A, int d) {
-  size_t leaves = 1;
-  for (int i = 0; i < d; ++i) leaves *= size_t(A);
-  return leaves * size_t(kFrameBytes);
+  size_t lvl[kMaxDepth + 2] = {1};
+  for (int i = 1; i <= d; ++i) lvl[i] = lvl[i - 1] * size_t(A);
+  size_t bytes = size_t(kStateBytes) + 3 * size_t(A) * 4 + 16;  // root, q0 / V / values
+  if (d >= 1) bytes += lvl[1] * (kStateBytes + 4 + 4 + 1);       // depth 1: state, r, max Q, A
+  for (int i = 2; i < d; ++i) bytes += lvl[i] * (kStateBytes + 4);
+  if (d >= 2) bytes += lvl[d] * (kStateBytes + 4 + 4 + 1 + 4) + lvl[d - 1] * size_t(kP1) * kC1 * 4;
+  return bytes;
 }
 
 // A context that shares `o`'s weights and owns its own stream and buffers.
@@ -109,7 +120,7 @@ void worker_loop(ServeState *s, int w) {
       // small passes; an idle device starts at once
       const auto until = std::chrono::steady_clock::now() + kWindow;
       while (!s->stop && s->busy_workers > 0 && int(s->queue.size()) < s->max_batch &&
-             s->queued_cost < kFullPassLeaves * size_t(kFrameBytes)) {
+             s->queued_leaves < kFullPassLeaves) {
         if (s->cv_work.wait_until(lk, until) == std::cv_status::timeout) break;
       }
       if (s->queue.empty()) continue;
@@ -121,7 +132,7 @@ void worker_loop(ServeState *s, int w) {
         const bool fits = s->inflight + cost + r.cost <= s->budget;
         if (!fits && !(batch.empty() && s->inflight == 0)) break;
         cost += r.cost;
-        s->queued_cost -= r.cost;
+        s->queued_leaves -= r.leaves;
         batch.push_back(s->queue.front());
         s->queue.pop_front();
       }
@@ -243,7 +254,9 @@ extern "C" int bcts_submit(bcts_ctx *ctx, const bcts_state *root, int d, int A, 
     r.d = d;
     r.A = A;
     r.cost = bcts::request_cost(A, d);
-    s->queued_cost += r.cost;
+    r.leaves = 1;
+    for (int i = 0; i < d; ++i) r.leaves *= size_t(A);
+    s->queued_leaves += r.leaves;
     s->queue.push_back(t);
     *out_ticket = t;
   }

@@ -35,7 +35,7 @@ def _wait(bcts, ctx, ticket, A):
     return a, v
 
 
-@pytest.mark.parametrize("budget", [0, 16 << 20])
+@pytest.mark.parametrize("budget", [0, 2 << 20])
 def test_served_results_equal_alone(dev, budget):
     torch, bcts = dev
     W = inputs.qnet_weights(18)
