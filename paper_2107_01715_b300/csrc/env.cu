@@ -182,19 +182,24 @@ constexpr int kRenderGroup = 8;
 __device__ __forceinline__ void render_group(const uint4 *__restrict__ states, uint64_t b0, uint64_t step,
                                              uint64_t n, bool newest, uint4 *__restrict__ frames) {
   const uint32_t jc = threadIdx.x;
+  // the word writers' object cells, loaded before the background stores so that the
+  // load latency overlaps them
+  const int k = int(jc >> 4), obj = int(jc >> 2) & 3, r = int(jc & 3);
+  const uint64_t bw = b0 + k * step;
+  const bool writer = jc < kRenderGroup * 16 && bw < n;  // (slot, object, sprite row)
+  uint4 P = make_uint4(0u, 0u, 0u, 0u);
+  if (writer) P = __ldg(newest ? states + bw * 5 + 3 : states + (bw >> 2) * 5 + (bw & 3));
   if (jc < kChunksPerSlot) {
 #pragma unroll
-    for (int k = 0; k < kRenderGroup; ++k) {
-      const uint64_t b = b0 + k * step;
+    for (int g = 0; g < kRenderGroup; ++g) {
+      const uint64_t b = b0 + g * step;
       if (b < n) frames[b * kChunksPerSlot + jc] = make_uint4(0u, 0u, 0u, 0u);
     }
   }
   __syncthreads();
-  if (jc < kRenderGroup * 16) {  // (slot, object, sprite row)
-    const int k = int(jc >> 4), obj = int(jc >> 2) & 3, r = int(jc & 3);
-    const uint64_t b = b0 + k * step;
-    if (b < n) {
-      const uint4 P = __ldg(newest ? states + b * 5 + 3 : states + (b >> 2) * 5 + (b & 3));
+  if (writer) {
+    const uint64_t b = bw;
+    {
       int ox[4], oy[4];
       unpack_slot(P, ox, oy);
       const int y = 4 * oy[obj] + r, cx = ox[obj];

@@ -42,7 +42,7 @@ __device__ __forceinline__ float key_value(uint32_t k) {
 
 // V[s] = max over the seg_len consecutive leaves of segment s of R + gamma^d maxq
 // (Alg. 1's leaf term; Eq. 1's max over a_1..a_d for root action s mod A).
-// Short segments: one warp per segment, four coalesced loads of each array in
+// Short segments: one warp per segment, eight coalesced loads of each array in
 // flight per lane.
 // One segment by one warp.
 __device__ __forceinline__ void segment_max_warp(const float *__restrict__ r, const float *__restrict__ q,
@@ -50,11 +50,15 @@ __device__ __forceinline__ void segment_max_warp(const float *__restrict__ r, co
                                                  int lane) {
   float best = -INFINITY;
   int64_t i = lane;
-  for (; i + 96 < seg_len; i += 128) {
-    const float r0 = __ldg(r + i), r1 = __ldg(r + i + 32), r2 = __ldg(r + i + 64), r3 = __ldg(r + i + 96);
-    const float q0 = __ldg(q + i), q1 = __ldg(q + i + 32), q2 = __ldg(q + i + 64), q3 = __ldg(q + i + 96);
-    best = fmaxf(fmaxf(best, fmaxf(r0 + gamma_pow * q0, r1 + gamma_pow * q1)),
-                 fmaxf(r2 + gamma_pow * q2, r3 + gamma_pow * q3));
+  for (; i + 224 < seg_len; i += 256) {  // eight loads of each array in flight per lane
+    float rv[8], qv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      rv[k] = __ldg(r + i + 32 * k);
+      qv[k] = __ldg(q + i + 32 * k);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) best = fmaxf(best, rv[k] + gamma_pow * qv[k]);
   }
   for (; i < seg_len; i += 32) best = fmaxf(best, __ldg(r + i) + gamma_pow * __ldg(q + i));
 #pragma unroll
@@ -87,7 +91,8 @@ __global__ void __launch_bounds__(256) segment_max_list_kernel(const __grid_cons
   }
 }
 
-// Long segments: each block reduces kSegPart consecutive leaves of one segment
+// Segments of kSegPart leaves or more: each block reduces kSegPart consecutive
+// leaves of one segment
 // (eight loads of each array in flight per thread) and folds its maximum into the
 // segment's key with atomicMax; V is zero-filled first.
 constexpr int kSegThreads = 256, kSegPerThread = 16, kSegPart = kSegThreads * kSegPerThread;
@@ -262,7 +267,7 @@ int launch_segment_max(const float *R, const float *maxq, int64_t n_seg, int64_t
   if (n_seg <= 0) return BCTS_OK;
   ProfScope ps(K_BACKUP, st);
   uint32_t *key = reinterpret_cast<uint32_t *>(V);
-  if (seg_len >= 2 * kSegPart) {
+  if (seg_len >= kSegPart) {
     const int64_t parts = (seg_len + kSegPart - 1) / kSegPart;
     if (n_seg * parts > 0x7FFFFFFFLL) return BCTS_EINVAL;
     if (cudaMemsetAsync(key, 0, size_t(n_seg) * sizeof(uint32_t), st) != cudaSuccess) return BCTS_ECUDA;
