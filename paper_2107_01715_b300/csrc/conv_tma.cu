@@ -38,6 +38,7 @@
 #include "kernels.cuh"
 #include "pack.cuh"
 #include "tc_ptx.cuh"
+#include "tma_host.cuh"
 
 namespace bcts {
 namespace tc {
@@ -104,19 +105,6 @@ struct ConvTmaParams {
   int num_tiles;
   int *d_err;
 };
-
-// Bounded wait that ignores the abort flag: used at teardown, to let copies and
-// MMAs that were issued complete before the CTA releases its shared memory.
-__device__ __forceinline__ void wait_bar_drain(uint32_t bar, uint32_t parity, int *d_err) {
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity)) {
-    __nanosleep(64);
-    if (clock64() - t0 > kWaitCycles) {
-      if (d_err) atomicCAS(d_err, 0, 5);
-      return;
-    }
-  }
-}
 
 template <int LAYER, int MODE>
 __global__ void __launch_bounds__(TmaCfg<LAYER, MODE>::THREADS, 1)
@@ -390,19 +378,6 @@ __global__ void __launch_bounds__(TmaCfg<LAYER, MODE>::THREADS, 1)
 // ---------------------------------------------------------------------------
 // Host side: tensor maps and launch
 // ---------------------------------------------------------------------------
-using EncodeIm2col = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const int *, const int *, cuuint32_t, cuuint32_t,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-struct Encoders {
-  EncodeIm2col im2col = nullptr;
-  EncodeTiled tiled = nullptr;
-};
-
 const Encoders &encoders() {
   static Encoders e;
   static std::once_flag once;

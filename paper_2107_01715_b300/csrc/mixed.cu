@@ -359,19 +359,33 @@ static void save_tune(MixedState *m) {
 // Pick the union-leaf configuration for this bucket by timing the candidates
 // (leaf chunk x conv2 / conv3 kernel variant) on the plan's own leaves (first
 // pass of a new bucket only; each candidate is run once to size its scratch and
-// once timed).
+// once timed).  The candidate kernels sum every output's products in the same
+// order as the precision's default ones (conv2 through windows or not, as the
+// default; conv3 through any of its three kernels), so a root's result does not
+// depend on the bucket its pass falls into.  A mask fixed through
+// BCTS_CONV_KERNELS is kept; only the chunk is tuned then.
 static int autotune(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_t st) {
   if (c->opt.leaf_chunk > 0 || pl.nleaf < 65536 || c->precision == BCTS_PREC_FP32_SIMT) return BCTS_OK;
   if (!m->tune_loaded) load_tune(m);
-  const std::string key = std::to_string(c->precision) + ":" + std::to_string(leaf_bucket(pl.nleaf));
+  const int dm = c->conv_mask_fixed ? c->conv_mask : tc_default_conv_mask(c->precision);
+  const std::string key = std::to_string(c->precision) + ":" + std::to_string(leaf_bucket(pl.nleaf)) +
+                          (c->conv_mask_fixed ? ":m" + std::to_string(dm) : std::string());
   auto it = m->tuned.find(key);
-  if (it != m->tuned.end()) {
+  if (it != m->tuned.end() && (it->second.conv_mask & 4) == (dm & 4)) {
     c->chunk_override = it->second.chunk;
     c->conv_mask = it->second.conv_mask;
     return BCTS_OK;
   }
   const int64_t chunks[] = {16384, 32768, 65536};
-  const int masks[] = {0, 1, 2, 3};  // conv2 (bit 0) / conv3 (bit 1) through TMA
+  // conv2 / conv3 kernels: bits 0 / 1 TMA im2col, bits 2 / 3 shared-memory windows
+  std::vector<int> masks;
+  if (c->conv_mask_fixed) {
+    masks.push_back(dm);
+  } else {
+    for (int c2 : {0, 1})
+      for (int c3 : {0, 2, 8})
+        if (!(dm & 4) || c2 == 0) masks.push_back(((dm & 4) ? 4 : c2) | c3);
+  }
   float best_ms = 1e30f;
   MixedState::Tuned best{32768, -1};
   cudaEvent_t e0, e1;

@@ -1163,18 +1163,19 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
     a.out_lo = o_lo;
     a.n = n;
     a.d_err = d_err;
-    return launch_conv_tma(l + 1, MODE, a, st);
+    return (conv_tma_mask >> (l + 1)) & 1 ? launch_conv_win(l + 1, MODE, a, st) : launch_conv_tma(l + 1, MODE, a, st);
   };
-  // conv2 / conv3: TMA im2col-fed (conv_tma.cu) or cp.async-gathered (tc_gemm),
-  // chosen per layer by conv_tma_mask (bit 0 conv2, bit 1 conv3)
-  if (conv_tma_mask & 1) {
+  // conv2 / conv3: window-fed (conv_win.cu), TMA im2col-fed (conv_tma.cu) or
+  // cp.async-gathered (tc_gemm), chosen per layer by conv_tma_mask (bits 2 / 3
+  // window, bits 0 / 1 im2col, for conv2 / conv3)
+  if (conv_tma_mask & 5) {
     rc = conv(1, a1, a1l, a2, a2l);
   } else {
     layer(1, a1, a1l, a2, a2l);
     rc = tc::launch<2, MODE, false>(p, (long long)n * kP2, K_CONV2, st);
   }
   if (rc != BCTS_OK) return rc;
-  if (conv_tma_mask & 2) {
+  if (conv_tma_mask & 10) {
     rc = conv(2, a2, a2l, a3, a3l);
   } else {
     layer(2, a2, a2l, a3, a3l);
@@ -1189,9 +1190,11 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
 
 int tc_default_conv_mask(int precision) {
   // measured per layer on B300 at the Atari-scale workload (CUDA events, same
-  // call): TMA im2col wins for conv3 in the FP32-class split and E4M3 modes,
-  // the cp.async gather everywhere else
-  return precision == BCTS_PREC_BF16 ? 0 : 2;
+  // call): BF16 reads conv2 and conv3 from shared-memory windows (conv_win.cu);
+  // the FP32-class split and E4M3 modes take conv3 through TMA im2col and conv2
+  // through the cp.async gather (their window variants, whose padded rows cost
+  // 23-65 % more MMAs, measured slower)
+  return precision == BCTS_PREC_BF16 ? 12 : 2;
 }
 
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,

@@ -4,6 +4,7 @@
 // C-ABI entry points that run them.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -872,6 +873,13 @@ extern "C" int bcts_create(const bcts_env_desc *env, const float *w, int A, int 
   c->precision = c->opt.precision;
   c->tc_fused_render = (c->opt.flags & BCTS_FLAG_FRAMES) == 0;
   c->exact_gev = (c->opt.flags & BCTS_FLAG_EXACT_GEV) != 0;
+  if (const char *cm = std::getenv("BCTS_CONV_KERNELS")) {  // conv2 / conv3 kernel variants, bits as conv_mask
+    const int m = std::atoi(cm);
+    if (m >= 0 && m <= 15) {
+      c->conv_mask = m;
+      c->conv_mask_fixed = true;
+    }
+  }
   if (c->precision < BCTS_PREC_FP32 || c->precision > BCTS_PREC_FP32_SIMT) {
     delete c;
     set_thread_error("bcts_create: unknown precision");

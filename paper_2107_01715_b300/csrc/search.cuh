@@ -77,6 +77,7 @@ struct Ctx {
   Profiler *prof = nullptr;
   int64_t chunk_override = 0;    // leaf chunk chosen by the batched form's autotuner
   int conv_mask = -1;            // conv2/conv3 kernel variants of the leaf Q-network (-1: per-precision default)
+  bool conv_mask_fixed = false;  // conv_mask set through BCTS_CONV_KERNELS (the batched form's tuner keeps it)
   uint64_t buf_generation = 1;   // bumped whenever a device buffer moves
 
   ~Ctx();

@@ -187,6 +187,19 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
   return true;
 }
 
+// Bounded wait that ignores the abort flag: used at teardown, to let copies and
+// MMAs that were issued complete before the CTA releases its shared memory.
+__device__ __forceinline__ void wait_bar_drain(uint32_t bar, uint32_t parity, int *d_err) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    __nanosleep(64);
+    if (clock64() - t0 > kWaitCycles) {
+      if (d_err) atomicCAS(d_err, 0, 5);
+      return;
+    }
+  }
+}
+
 // ---- TMA (cp.async.bulk.tensor) ------------------------------------------
 // Arrive on `bar` and add `bytes` to the transaction count its phase waits for.
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
@@ -201,6 +214,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *map, int x
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
           dst),
       "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// Tiled 4D load of one box at (c0, c1, c2, c3) (c0 innermost, in elements).
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+          dst),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
       : "memory");
 }
 // im2col load from a 4D NHWC tensor: pixels traversed from (w, h, n) through the
