@@ -242,7 +242,7 @@ static int mixed_enqueue(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_
         const int64_t cnt = int64_t(g.n) * ipow(g.A, i);
         const bcts_state *cur = level_src(g, i).first;
         float *z = static_cast<float *>(m->zbuf.p) + size_t(g.zoff) * kP1 * kC1;
-        const int64_t chunk = c->chunk_nodes();
+        const int64_t chunk = c->chunk_nodes(cnt);
         for (int64_t off = 0; off < cnt; off += chunk) {
           const int64_t k = cnt - off < chunk ? cnt - off : chunk;
           if ((rc = tc_conv1_partial(c->tc, cur + off, k, z + size_t(off) * kP1 * kC1, st, c->d_err)) != BCTS_OK)
@@ -376,7 +376,7 @@ static int autotune(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_t st)
     c->conv_mask = it->second.conv_mask;
     return BCTS_OK;
   }
-  const int64_t chunks[] = {16384, 32768, 65536};
+  const int64_t chunks[] = {32768, 65536, 0};  // 0: the automatic pass size (Ctx::chunk_nodes)
   // conv2 / conv3 kernels: bits 0 / 1 TMA im2col, bits 2 / 3 shared-memory windows
   std::vector<int> masks;
   if (c->conv_mask_fixed) {

@@ -108,7 +108,7 @@ int Ctx::run_search_pruned(const bcts_state *d_roots, int n, int keep, int32_t *
     const float *zmap = nullptr;
     if (use_z) {
       if ((rc = ensure(z_buf, size_t(G * S) * kP1 * kC1 * 4)) != BCTS_OK) return rc;
-      const int64_t chunk = chunk_nodes();
+      const int64_t chunk = chunk_nodes(G * S);
       for (int64_t off = 0; off < G * S; off += chunk) {
         const int64_t k = G * S - off < chunk ? G * S - off : chunk;
         if ((rc = tc_conv1_partial(tc, par + off, k, static_cast<float *>(z_buf.p) + size_t(off) * kP1 * kC1, st,

@@ -84,7 +84,9 @@ struct Ctx {
   int fail(int code, const std::string &msg);
   int ensure(DevBuf &b, size_t bytes);
   int ensure_host(HostBuf &b, size_t bytes);
-  int64_t chunk_nodes() const;
+  // nodes per Q-network pass when `count` nodes are to be scored (0: the largest pass)
+  int64_t chunk_nodes(int64_t count = 0) const;
+  size_t dev_mem = 0;  // device memory (bytes), for the pass size
   int eval_nodes(const bcts_state *states, int64_t count, float *q, float *maxq, cudaStream_t st,
                  const uint8_t *node_A = nullptr, const float *zmap = nullptr, uint32_t zbranch = 0,
                  const uint32_t *zparent = nullptr);

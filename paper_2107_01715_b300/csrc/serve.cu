@@ -88,6 +88,7 @@ Ctx *clone_ctx(const Ctx *o) {
   c->tc = o->tc;
   c->tc_ref = o->tc_ref;
   c->conv_mask = o->conv_mask;
+  c->dev_mem = o->dev_mem;
   c->conv_mask_fixed = o->conv_mask_fixed;
   c->tc_fused_render = o->tc_fused_render;
   c->exact_gev = o->exact_gev;
