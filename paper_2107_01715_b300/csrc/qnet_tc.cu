@@ -400,6 +400,10 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
       // read neighbouring pixels.  The next stages' pixel words are loaded into
       // registers before this stage is converted and stored.
       constexpr int NW = FP8 ? 4 : 2;  // 32-bit pixel words per 16-byte chunk
+      // E4M3 layer 6: the K block's first slot (weight channel 2) is zero, the
+      // second (channel 3) live: the row's two threads take two live chunks (kernel
+      // row pairs 2 half, 2 half + 1) and two zero chunks each, not one slot each
+      constexpr bool BAL = FP8 && LAYER == 6;
       const int row = pt >> 1, half = pt & 1;
       auto live_of = [&](int kb) {
         const int sl = FP8 ? 2 * (C::KB0 + kb) + half - C::CH0 : kb;
@@ -407,7 +411,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
       };
       auto load_stage = [&](int t, int kb, uint32_t(&w)[4][NW]) {
         const uint32_t m0 = uint32_t(t / NT) * 128u;
-        const int sl = FP8 ? 2 * (C::KB0 + kb) + half - C::CH0 : kb;  // A slot
+        const int sl = BAL ? 0 : (FP8 ? 2 * (C::KB0 + kb) + half - C::CH0 : kb);  // A slot
         const bool live = sl >= 0 && sl < C::NCH;
         const int sc = live ? sl : 0;
         uint32_t m = m0 + uint32_t(row);
@@ -420,10 +424,10 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           if (FP8) {
-            const uint8_t *src = frame + 2 * j * 84;
+            const uint8_t *src = frame + 2 * (BAL ? 2 * half + (j & 1) : j) * 84;
 #pragma unroll
             for (int k = 0; k < NW; ++k) w[j][k] = 0u;
-            if (live) {
+            if (BAL ? j < 2 : live) {
               w[j][0] = __ldg(reinterpret_cast<const uint32_t *>(src));
               w[j][1] = __ldg(reinterpret_cast<const uint32_t *>(src + 4));
               w[j][NW > 2 ? 2 : 0] = __ldg(reinterpret_cast<const uint32_t *>(src + 84));
@@ -453,19 +457,21 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
         const int s = g % S;
         if (!wait_bar(empty_bar(s), uint32_t((g / S) & 1) ^ 1u, abort_flag, p.d_err, 1)) return false;
         const uint32_t sA = sA_of(s);
-        const bool live = live_of(q.kb);
+        const bool live = BAL || live_of(q.kb);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           uint4 v = make_uint4(0u, 0u, 0u, 0u);
           if (FP8) {
-            if (live) {
+            if (BAL ? j < 2 : live) {
               const uint32_t w4[4] = {w[j][0], w[j][1], w[j][NW > 2 ? 2 : 0], w[j][NW > 3 ? 3 : 0]};
               v = pixels16_to_e4m3(w4);
             }
           } else {
             v = pixels8_to_bf16(w[j][0], w[j][1]);
           }
-          st_shared16(sA + sw128_off(row, 4 * half + j), v);
+          // BAL: live chunks 4 + 2 half + j (j < 2), zero chunks 2 half + j - 2
+          const int chunk = BAL ? (j < 2 ? 4 + 2 * half + j : 2 * half + j - 2) : 4 * half + j;
+          st_shared16(sA + sw128_off(row, chunk), v);
         }
         fence_proxy_async();
         mbar_arrive(full_bar(s));
