@@ -703,8 +703,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
       // layer 6: the warp's 32 rows of their parents' partial maps (FP32, 32
       // columns = 128 bytes a row), loaded before the wait so that the latency
       // overlaps the MMAs, and coalesced: load i of lane l is the 16-byte piece
-      // l % 8 of row l / 8 + 4 i; the pieces pass through the staging rows to
-      // their owners
+      // l % 8 of row l / 8 + 4 i
       float4 zr[LAYER == 6 ? 8 : 1];
       if constexpr (LAYER == 6) {
         uint32_t m = uint32_t(t / NT) * 128u + uint32_t(q * 32 + lane);
@@ -722,14 +721,85 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
       if (!wait_bar(tfull_bar(acc), uint32_t((it / NA) & 1), abort_flag, p.d_err, 4)) break;
       tc_fence_after();
       if constexpr (LAYER == 6) {
-        __syncwarp();
+        // The accumulator rows (FP32; split mode: the sum of its two halves) pass
+        // through the staging rows once; lane l then takes columns 4 (l % 8) .. + 3
+        // of rows l / 8 + 4 i, the layout its parent-map pieces were loaded in,
+        // adds them (the map holds the bias), applies the ReLU, rounds and stores
+        // to the NHWC map: consecutive lanes write consecutive bytes.
+        const uint32_t mw0 = uint32_t(t / NT) * 128u + uint32_t(q * 32);
+        const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * C::ACC_N);
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-          *reinterpret_cast<float4 *>(stg + ((lane >> 3) + 4 * i) * kStgRow + (lane & 7) * 16) = zr[i];
-        __syncwarp();
+        for (int j = 0; j < BN / 16; ++j) {
+          uint32_t r[16];
+          tmem_ld16(tbase + uint32_t(j * 16), r);
+          float v[16];
+          if (C::B_CAT) {
+            uint32_t r2[16];  // the A_hi * B_lo half
+            tmem_ld16(tbase + uint32_t(BN + j * 16), r2);
+            tmem_wait_ld();
 #pragma unroll
-        for (int k = 0; k < 8; ++k) zr[k] = *reinterpret_cast<const float4 *>(stg + lane * kStgRow + k * 16);
+            for (int e = 0; e < 8; ++e) {
+              const float2 x = add2(make_float2(__uint_as_float(r[2 * e]), __uint_as_float(r[2 * e + 1])),
+                                    make_float2(__uint_as_float(r2[2 * e]), __uint_as_float(r2[2 * e + 1])));
+              v[2 * e] = x.x;
+              v[2 * e + 1] = x.y;
+            }
+          } else {
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            *reinterpret_cast<float4 *>(stg + lane * kStgRow + j * 64 + e * 16) =
+                make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        }
+        tc_fence_before();
         __syncwarp();
+        if (lane == 0) mbar_arrive(tempty_bar(acc));  // the accumulator is in the staging rows
+        const int pc = lane & 7;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int rr = (lane >> 3) + 4 * i;
+          float4 a = *reinterpret_cast<const float4 *>(stg + rr * kStgRow + pc * 16);
+          float2 lo2 = make_float2(a.x, a.y), hi2 = make_float2(a.z, a.w);
+          if (FP8) {  // per-column weight x input scale of the E4M3 product
+            const float4 s4 = *reinterpret_cast<const float4 *>(scale_s + 4 * pc);
+            lo2 = mul2(lo2, make_float2(s4.x, s4.y));
+            hi2 = mul2(hi2, make_float2(s4.z, s4.w));
+          }
+          lo2 = add2(lo2, make_float2(zr[i].x, zr[i].y));
+          hi2 = add2(hi2, make_float2(zr[i].z, zr[i].w));
+          const uint32_t m = mw0 + uint32_t(rr);
+          if (m >= p.M) continue;
+          if constexpr (FP8) {
+            const float2 inv = make_float2(p.out_inv_scale, p.out_inv_scale);
+            *reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(p.out_hi) + size_t(m) * BN + pc * 4) =
+                relu_e4m3x4(mul2(lo2, inv), mul2(hi2, inv));
+          } else if constexpr (SPLIT) {
+            // hi = bf16(relu(v)), lo = bf16(relu(v) - hi)
+            uint32_t hw[2], lw[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float2 y = h ? hi2 : lo2;
+              const float2 x = make_float2(fmaxf(y.x, 0.f), fmaxf(y.y, 0.f));
+              const __nv_bfloat162 hb = __floats2bfloat162_rn(x.x, x.y);
+              hw[h] = *reinterpret_cast<const uint32_t *>(&hb);
+              const float2 d = fma2(__bfloat1622float2(hb), make_float2(-1.f, -1.f), x);  // exact, one rounding
+              const __nv_bfloat162 lb = __floats2bfloat162_rn(d.x, d.y);
+              lw[h] = *reinterpret_cast<const uint32_t *>(&lb);
+            }
+            *reinterpret_cast<uint2 *>(static_cast<uint8_t *>(p.out_hi) + size_t(m) * BN * 2 + pc * 8) =
+                make_uint2(hw[0], hw[1]);
+            *reinterpret_cast<uint2 *>(static_cast<uint8_t *>(p.out_lo) + size_t(m) * BN * 2 + pc * 8) =
+                make_uint2(lw[0], lw[1]);
+          } else {
+            *reinterpret_cast<uint2 *>(static_cast<uint8_t *>(p.out_hi) + size_t(m) * BN * 2 + pc * 8) =
+                make_uint2(relu_bf16x2(lo2), relu_bf16x2(hi2));
+          }
+        }
+        __syncwarp();  // the staging rows are read before the next tile writes them
+        continue;
       }
       const uint32_t mw0 = uint32_t(t / NT) * 128u + uint32_t(q * 32);
       const int n0 = (t % NT) * BN;
@@ -770,11 +840,6 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
           } else {
             v[2 * e] = add2(v[2 * e], c0);
             v[2 * e + 1] = add2(v[2 * e + 1], c1);
-          }
-          if constexpr (LAYER == 6) {  // + the parent's partial map (it holds the bias)
-            const float4 z4 = zr[j * 4 + e];
-            v[2 * e] = add2(v[2 * e], make_float2(z4.x, z4.y));
-            v[2 * e + 1] = add2(v[2 * e + 1], make_float2(z4.z, z4.w));
           }
         }
         if constexpr (LAYER == 5) {  // partial map: FP32, no ReLU
