@@ -400,18 +400,28 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
       // read neighbouring pixels.  The next stages' pixel words are loaded into
       // registers before this stage is converted and stored.
       constexpr int NW = FP8 ? 4 : 2;  // 32-bit pixel words per 16-byte chunk
-      // E4M3 layer 6: the K block's first slot (weight channel 2) is zero, the
-      // second (channel 3) live: the row's two threads take two live chunks (kernel
-      // row pairs 2 half, 2 half + 1) and two zero chunks each, not one slot each
-      constexpr bool BAL = FP8 && LAYER == 6;
+      // E4M3 K blocks hold two slots; where only one is live (layer 6: channel 3
+      // beside a zero channel 2; layer 5's second block: channel 2 beside a zero
+      // channel 3) the row's two threads take two live chunks (kernel row pairs
+      // 2 half, 2 half + 1) and two zero chunks each, not one slot each
       const int row = pt >> 1, half = pt & 1;
+      // for K block kb: exactly one live slot? its slot index and first chunk
+      auto bal_of = [&](int kb, int &lsl, int &lbase) {
+        const int s0 = 2 * (C::KB0 + kb) - C::CH0, s1 = s0 + 1;
+        const bool l0 = s0 >= 0 && s0 < C::NCH, l1 = s1 >= 0 && s1 < C::NCH;
+        lsl = l0 ? s0 : s1;
+        lbase = l0 ? 0 : 4;
+        return FP8 && l0 != l1;
+      };
       auto live_of = [&](int kb) {
         const int sl = FP8 ? 2 * (C::KB0 + kb) + half - C::CH0 : kb;
         return sl >= 0 && sl < C::NCH;
       };
       auto load_stage = [&](int t, int kb, uint32_t(&w)[4][NW]) {
         const uint32_t m0 = uint32_t(t / NT) * 128u;
-        const int sl = BAL ? 0 : (FP8 ? 2 * (C::KB0 + kb) + half - C::CH0 : kb);  // A slot
+        int lsl, lbase;
+        const bool BAL = bal_of(kb, lsl, lbase);
+        const int sl = BAL ? lsl : (FP8 ? 2 * (C::KB0 + kb) + half - C::CH0 : kb);  // A slot
         const bool live = sl >= 0 && sl < C::NCH;
         const int sc = live ? sl : 0;
         uint32_t m = m0 + uint32_t(row);
@@ -457,6 +467,8 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
         const int s = g % S;
         if (!wait_bar(empty_bar(s), uint32_t((g / S) & 1) ^ 1u, abort_flag, p.d_err, 1)) return false;
         const uint32_t sA = sA_of(s);
+        int lsl, lbase;
+        const bool BAL = bal_of(q.kb, lsl, lbase);
         const bool live = BAL || live_of(q.kb);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -469,8 +481,8 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
           } else {
             v = pixels8_to_bf16(w[j][0], w[j][1]);
           }
-          // BAL: live chunks 4 + 2 half + j (j < 2), zero chunks 2 half + j - 2
-          const int chunk = BAL ? (j < 2 ? 4 + 2 * half + j : 2 * half + j - 2) : 4 * half + j;
+          // BAL: live chunks lbase + 2 half + j (j < 2), zero chunks in the other half
+          const int chunk = BAL ? (j < 2 ? lbase + 2 * half + j : (4 - lbase) + 2 * half + j - 2) : 4 * half + j;
           st_shared16(sA + sw128_off(row, chunk), v);
         }
         fence_proxy_async();
