@@ -277,40 +277,50 @@ __global__ void __launch_bounds__(WinCfg<LAYER, MODE>::THREADS, 1)
         const uint32_t d = tmem + uint32_t(acc * C::ACC_N);
         const uint32_t w = win0 + uint32_t(s * C::WIN_BYTES);
         const int row_off = LAYER == 2 ? (t * 128) % G::PW : 0;  // tile start within its window line
-        for (int sb = 0; sb < C::NSUB; ++sb) {
+        // The descriptors of one tile differ only in their start-address field
+        // (bits 0-13: address / 16): one base for the window (at the tile's first
+        // row) and one for the weights, plus offsets that are constants once the
+        // loops are unrolled, so the issuing thread spends a few instructions per MMA.
+        // Any 32-byte step of a window row takes the start address only (see the top
+        // of the file).
+        const uint64_t wdesc = swz_desc(w, C::ROWB) + uint64_t(uint32_t(row_off * C::ROWB) >> 4);
+        auto a_off = [&](int sb) {  // window offset (in 16 bytes) of sub-block sb's first row
           const int tap = sb / G::NSLAB, sl = sb % G::NSLAB;
-          const int row0 = row_off + (tap / G::TW) * G::PW + tap % G::TW;
-          const uint32_t a_hi = w + uint32_t(sl * C::SLAB + row0 * C::ROWB);
-          uint32_t bsub;
-          int b = 0;
-          if constexpr (C::B_RES) {
-            bsub = res + uint32_t(sb * C::B_SUB);
-          } else {
-            b = gb % BSTM;
+          return uint64_t(uint32_t(sl * C::SLAB + ((tap / G::TW) * G::PW + tap % G::TW) * C::ROWB) >> 4);
+        };
+        constexpr uint64_t kLoOff = uint64_t(uint32_t(G::NSLAB * C::SLAB) >> 4);  // the lo slabs (split)
+        if constexpr (C::B_RES) {
+          const uint64_t bdesc = swz_desc(res, C::ROWB);
+#pragma unroll
+          for (int sb = 0; sb < C::NSUB; ++sb) {
+#pragma unroll
+            for (int kk = 0; kk < C::ROWB / 32; ++kk) {  // 32 bytes of K per instruction
+              const uint32_t acc_flag = (sb != 0 || kk != 0) ? 1u : 0u;
+              const uint64_t a = wdesc + a_off(sb) + uint64_t(2 * kk);
+              const uint64_t bd = bdesc + uint64_t(uint32_t(sb * C::B_SUB) >> 4) + uint64_t(2 * kk);
+              if (FP8)
+                mma_f8(d, a, bd, idesc_n, acc_flag);
+              else
+                mma_bf16(d, a, bd, idesc_n, acc_flag);
+            }
+          }
+        } else {
+          for (int sb = 0; sb < C::NSUB; ++sb) {
+            const int b = gb % BSTM;
             if (!wait_bar(bfull_bar(b), uint32_t((gb / BSTM) & 1), abort_flag, p.d_err, 3)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            bsub = bring + uint32_t(b * C::B_SUB);
-          }
+            const uint64_t bdesc = swz_desc(bring + uint32_t(b * C::B_SUB), C::ROWB);
+            const uint64_t a0 = wdesc + a_off(sb);
 #pragma unroll
-          for (int kk = 0; kk < C::ROWB / 32; ++kk) {  // 32 bytes of K per instruction
-            const uint32_t acc_flag = (sb != 0 || kk != 0) ? 1u : 0u;
-            // any 32-byte step of a window row: start address only (see the top of the file)
-            const uint64_t a = swz_desc(a_hi + uint32_t(32 * kk), C::ROWB);
-            const uint64_t bd = swz_desc(bsub, C::ROWB) + uint64_t(2 * kk);
-            if (FP8) {
-              mma_f8(d, a, bd, idesc_n, acc_flag);
-            } else if (SPLIT) {
-              mma_bf16(d, a, bd, idesc_wide, acc_flag);  // [A_hi B_hi | A_hi B_lo]
-              const uint32_t a_lo = a_hi + uint32_t(G::NSLAB * C::SLAB);
-              mma_bf16(d, swz_desc(a_lo + uint32_t(32 * kk), C::ROWB), bd, idesc_n, 1u);  // + A_lo B_hi
-            } else {
-              mma_bf16(d, a, bd, idesc_n, acc_flag);
+            for (int kk = 0; kk < C::ROWB / 32; ++kk) {
+              const uint32_t acc_flag = (sb != 0 || kk != 0) ? 1u : 0u;
+              const uint64_t bd = bdesc + uint64_t(2 * kk);
+              mma_bf16(d, a0 + uint64_t(2 * kk), bd, idesc_wide, acc_flag);          // [A_hi B_hi | A_hi B_lo]
+              mma_bf16(d, a0 + kLoOff + uint64_t(2 * kk), bd, idesc_n, 1u);          // + A_lo B_hi
             }
-          }
-          if constexpr (!C::B_RES) {
             mma_commit(bempty_bar(b));  // the weight stage is free once these MMAs have read it
             ++gb;
           }
