@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(TmaCfg<LAYER, MODE>::THREADS, 1)
       constexpr uint32_t idesc_wide = idesc_bf16(2 * BN);  // [hi; lo] weight rows side by side
       bool ok = true;
       if (C::B_RES) ok = wait_bar(wready_bar, 0, abort_flag, p.d_err, 6);
+      const uint64_t stage_desc = swz_desc(stage0, C::ROWB), res_desc = swz_desc(res, C::ROWB);
       int g = 0, it = 0;
       for (int t = T0; t < TE && ok; ++t, ++it) {
         const int acc = it % NA;
@@ -230,21 +231,24 @@ __global__ void __launch_bounds__(TmaCfg<LAYER, MODE>::THREADS, 1)
             break;
           }
           tc_fence_after();
+          // the descriptors differ only in their start-address field (address / 16)
+          const uint64_t sd = stage_desc + uint64_t(uint32_t(s * C::STAGE_BYTES) >> 4);
 #pragma unroll
           for (int j = 0; j < C::PPS; ++j) {
             const int pos = ks * C::PPS + j;
-            const uint32_t sA = stage0 + uint32_t(s * C::STAGE_BYTES + j * C::POS_BYTES);
-            const uint32_t sB = C::B_RES ? res + uint32_t(pos * C::B_SUB) : sA + uint32_t(C::NA_SUB * C::A_SUB);
+            const uint64_t aj = sd + uint64_t(uint32_t(j * C::POS_BYTES) >> 4);
+            const uint64_t bj = C::B_RES ? res_desc + uint64_t(uint32_t(pos * C::B_SUB) >> 4)
+                                         : aj + uint64_t(uint32_t(C::NA_SUB * C::A_SUB) >> 4);
 #pragma unroll
             for (int kk = 0; kk < C::ROWB / 32; ++kk) {  // 32 bytes of K per instruction
               const uint32_t acc_flag = (pos != 0 || kk != 0) ? 1u : 0u;
-              const uint64_t a = swz_desc(sA, C::ROWB) + uint64_t(2 * kk);
-              const uint64_t b = swz_desc(sB, C::ROWB) + uint64_t(2 * kk);
+              const uint64_t a = aj + uint64_t(2 * kk);
+              const uint64_t b = bj + uint64_t(2 * kk);
               if (FP8) {
                 mma_f8(d, a, b, idesc_n, acc_flag);
               } else if (SPLIT) {
                 mma_bf16(d, a, b, idesc_wide, acc_flag);  // [A_hi B_hi | A_hi B_lo]
-                mma_bf16(d, swz_desc(sA + C::A_SUB, C::ROWB) + uint64_t(2 * kk), b, idesc_n, 1u);  // + A_lo B_hi
+                mma_bf16(d, a + uint64_t(uint32_t(C::A_SUB) >> 4), b, idesc_n, 1u);  // + A_lo B_hi
               } else {
                 mma_bf16(d, a, b, idesc_n, acc_flag);
               }

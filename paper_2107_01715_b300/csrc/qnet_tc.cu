@@ -601,6 +601,7 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
     if (lane == 0) {
       constexpr uint32_t idesc_wide = idesc_bf16(C::B_CAT ? 2 * BN : BN);  // [hi; lo] weight rows
       constexpr uint32_t idesc_n = FP8 ? idesc_e4m3(BN) : idesc_bf16(BN);
+      const uint64_t stage_desc = sw128_desc(stage0), res_desc = sw128_desc(res);
       int g = 0, it = 0;
       bool ok = true;
       if (C::B_RES) ok = wait_bar(wready_bar, 0, abort_flag, p.d_err, 6);
@@ -635,25 +636,27 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
           for (int kk = 0; kk < C::KPS; ++kk) {
           const int kb = ks * C::KPS + kk;
           if (kb >= KB) break;
-          const uint32_t sA = sub_of(s, kk);
-          const uint32_t sAlo = sA + C::A_BYTES;
-          const uint32_t sB = C::B_RES ? res + uint32_t(kb) * (C::B_ROWS * 128) : sB_of(s, kk);
-          const uint32_t sBlo = sB + C::B_BYTES;
+          // descriptors differ only in their start-address field (address / 16):
+          // offsets from the stage area's and the resident weights' descriptors
+          const uint64_t ad = stage_desc + uint64_t((uint32_t(s) * C::STAGE_BYTES + uint32_t(kk) * C::SUB_BYTES) >> 4);
+          const uint64_t bd = C::B_RES ? res_desc + uint64_t((uint32_t(kb) * (C::B_ROWS * 128)) >> 4)
+                                       : ad + uint64_t(uint32_t(C::A_BYTES * (C::A_LO ? 2 : 1)) >> 4);
+          constexpr uint64_t kAlo = uint64_t(uint32_t(C::A_BYTES) >> 4), kBlo = uint64_t(uint32_t(C::B_BYTES) >> 4);
 #pragma unroll
           for (int j = 0; j < 4; ++j) {  // K = 16 bf16 / 32 E4M3 = 32 bytes per instruction
             const uint32_t first = (kb != 0 || j != 0) ? 1u : 0u;
-            const uint64_t a = sw128_desc(sA) + uint64_t(2 * j);
-            const uint64_t b = sw128_desc(sB) + uint64_t(2 * j);
+            const uint64_t a = ad + uint64_t(2 * j);
+            const uint64_t b = bd + uint64_t(2 * j);
             if (FP8) {
               mma_f8(d, a, b, idesc_n, first);
             } else if (C::B_CAT) {
               mma_bf16(d, a, b, idesc_wide, first);  // [A_hi B_hi | A_hi B_lo]
-              if (C::A_LO) mma_bf16(d, sw128_desc(sAlo) + uint64_t(2 * j), b, idesc_n, 1u);  // + A_lo B_hi
+              if (C::A_LO) mma_bf16(d, a + kAlo, b, idesc_n, 1u);  // + A_lo B_hi
             } else {
               mma_bf16(d, a, b, idesc_n, first);
               if (SPLIT) {
-                mma_bf16(d, a, sw128_desc(sBlo) + uint64_t(2 * j), idesc_n, 1u);
-                if (C::A_LO) mma_bf16(d, sw128_desc(sAlo) + uint64_t(2 * j), b, idesc_n, 1u);
+                mma_bf16(d, a, b + kBlo, idesc_n, 1u);
+                if (C::A_LO) mma_bf16(d, a + kAlo, b, idesc_n, 1u);
               }
             }
           }
