@@ -39,7 +39,8 @@
 //             32 bytes of K per instruction) into rotating FP32 accumulators;
 //   warps 2-5 epilogue: tcgen05.ld, bias (FP8: per-column scale), ReLU, round to
 //             bf16 (split: plus the remainder) or E4M3, and the kept rows to the
-//             NHWC output through shared-memory staging.
+//             NHWC output (BF16 / E4M3 straight from registers, the split mode's
+//             hi and lo rows through shared-memory staging).
 // Precision modes as elsewhere: 0 BF16, 1 FP32-class split (A_hi B_hi + A_hi
 // B_lo + A_lo B_hi), 2 FP8 E4M3 with per-channel scales.  Every wait is bounded;
 // on a time-out the kernel records an error code, stops issuing, waits for its
@@ -371,7 +372,22 @@ __global__ void __launch_bounds__(WinCfg<LAYER, MODE>::THREADS, 1)
       tc_fence_after();
       const uint32_t pr0 = uint32_t(t) * 128u + uint32_t(q * 32);
       const uint32_t tbase = tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * C::ACC_N);
-      constexpr int OW32 = FP8 ? BN / 4 : BN / 2;  // 32-bit words of this thread's output row
+      // this thread's row (accumulator lane pr0 + lane): its NHWC output row, if it
+      // is inside the output grid.  BF16 / E4M3: the row's bytes are written
+      // straight from registers, so shared memory serves the MMAs' operand reads
+      // (measured: conv3 E4M3 0.75 -> 0.63 ms); the split mode's hi and lo rows go
+      // through the staging rows (direct stores measured slower there)
+      size_t orow = ~size_t(0);
+      {
+        const uint32_t pr = pr0 + uint32_t(lane);
+        const uint32_t node = pr / uint32_t(G::PP), px = pr - node * uint32_t(G::PP);
+        const uint32_t oy = px / uint32_t(G::PW), ox = px - oy * uint32_t(G::PW);
+        if (node < p.n && oy < uint32_t(G::OW) && ox < uint32_t(G::OW))
+          orow = (size_t(node) * G::P + oy * G::OW + ox) * ROWB_OUT;
+      }
+      uint8_t *ohi = static_cast<uint8_t *>(p.out_hi) + (orow == ~size_t(0) ? 0 : orow);
+      const bool live = orow != ~size_t(0);
+      constexpr int OW32 = BN / 2;  // split: 32-bit words of this thread's lo row
       uint32_t olo[SPLIT ? OW32 : 1];
 #pragma unroll
       for (int j = 0; j < BN / 16; ++j) {
@@ -411,9 +427,9 @@ __global__ void __launch_bounds__(WinCfg<LAYER, MODE>::THREADS, 1)
           uint32_t w[4];
 #pragma unroll
           for (int h = 0; h < 4; ++h) w[h] = relu_e4m3x4(mul2(v[2 * h], inv), mul2(v[2 * h + 1], inv));
-          *reinterpret_cast<uint4 *>(stg + lane * kStgRowW + j * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+          if (live) *reinterpret_cast<uint4 *>(ohi + j * 16) = make_uint4(w[0], w[1], w[2], w[3]);
         } else {
-          uint32_t hh[8];
+          uint32_t hh[8], ll[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             if constexpr (SPLIT) {
@@ -423,17 +439,24 @@ __global__ void __launch_bounds__(WinCfg<LAYER, MODE>::THREADS, 1)
               hh[e] = *reinterpret_cast<const uint32_t *>(&h);
               const float2 dd = fma2(__bfloat1622float2(h), make_float2(-1.f, -1.f), x);  // exact, one rounding
               const __nv_bfloat162 l = __floats2bfloat162_rn(dd.x, dd.y);
-              olo[j * 8 + e] = *reinterpret_cast<const uint32_t *>(&l);
+              ll[e] = *reinterpret_cast<const uint32_t *>(&l);
             } else {
               hh[e] = relu_bf16x2(v[e]);
             }
           }
-          *reinterpret_cast<uint4 *>(stg + lane * kStgRowW + j * 32) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
-          *reinterpret_cast<uint4 *>(stg + lane * kStgRowW + j * 32 + 16) = make_uint4(hh[4], hh[5], hh[6], hh[7]);
+          if constexpr (SPLIT) {
+            *reinterpret_cast<uint4 *>(stg + lane * kStgRowW + j * 32) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+            *reinterpret_cast<uint4 *>(stg + lane * kStgRowW + j * 32 + 16) = make_uint4(hh[4], hh[5], hh[6], hh[7]);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) olo[j * 8 + e] = ll[e];
+          } else if (live) {
+            *reinterpret_cast<uint4 *>(ohi + j * 32) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+            *reinterpret_cast<uint4 *>(ohi + j * 32 + 16) = make_uint4(hh[4], hh[5], hh[6], hh[7]);
+          }
         }
       }
-      flush(static_cast<uint8_t *>(p.out_hi), pr0);
       if constexpr (SPLIT) {
+        flush(static_cast<uint8_t *>(p.out_hi), pr0);
 #pragma unroll
         for (int i = 0; i < OW32 / 4; ++i)
           *reinterpret_cast<uint4 *>(stg + lane * kStgRowW + i * 16) =

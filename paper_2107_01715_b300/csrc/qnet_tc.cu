@@ -1280,10 +1280,11 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
 int tc_default_conv_mask(int precision) {
   // measured per layer on B300 at the Atari-scale workload (CUDA events, same
   // call): BF16 reads conv2 and conv3 from shared-memory windows (conv_win.cu);
-  // the FP32-class split and E4M3 modes take conv3 through TMA im2col and conv2
-  // through the cp.async gather (their window variants, whose padded rows cost
-  // 23-65 % more MMAs, measured slower)
-  return precision == BCTS_PREC_BF16 ? 12 : 2;
+  // E4M3 reads conv2 from windows and takes conv3 through TMA im2col; the
+  // FP32-class split mode takes conv3 through TMA im2col and conv2 through the
+  // cp.async gather (its window variants, whose padded rows cost 23-65 % more
+  // MMAs, measured slower)
+  return precision == BCTS_PREC_BF16 ? 12 : (precision == BCTS_PREC_FP8 ? 6 : 2);
 }
 
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
