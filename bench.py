@@ -76,8 +76,8 @@ ALG_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 0, "conv1_leaf": 0,
 # d = 3 (launches over 23,328 leaves; traffic grows in proportion to the nodes a launch
 # processes).  A class whose kernel changed after its capture has no entry here.
 TRAFFIC_PER_NODE = {"fp32/conv1_leaf": 53939.0, "bf16/conv1_leaf": 27170.0, "fp8/conv1_leaf": 13745.0,
-                    "fp32/conv2": 70866.0, "bf16/conv2": 34848.0, "fp8/conv2": 16944.0,
-                    "fp32/conv3": 31900.0, "fp32/fc1": 14578.0}
+                    "fp32/conv2": 70871.0, "bf16/conv2": 34762.0, "fp8/conv2": 16775.0,
+                    "fp32/conv3": 31903.0, "fp32/fc1": 14562.0}
 
 
 def layer_model(cls, precision, A):
