@@ -667,14 +667,23 @@ PRECISION_TOL = {"fp32": 1e-4, "bf16": 2e-2, "fp8": 8e-2}
 
 def working_set_gb(n, A, d, precision):
     """DRAM bytes one search streams through besides the weights: the two deepest node
-    levels (80-byte states + R), the parents' FP32 partial conv1 maps and one leaf
-    chunk's activation maps (32,768 leaves)."""
+    levels (80-byte states + R), the parents' FP32 partial conv1 maps and one
+    Q-network pass's activation maps (the library's pass: the whole level when its
+    maps fit in 1/16 of the device memory, else equal passes of that size)."""
     e = {"fp32": 4, "bf16": 2, "fp8": 1}.get(precision, 4)
     leaves = n * A ** d
     parents = n * A ** max(d - 1, 0)
-    chunk = min(leaves, 32768)
+    per_leaf = (400 * 32 + 81 * 64 + 49 * 64) * e + 512 * 4
+    try:
+        import torch
+        mem = torch.cuda.get_device_properties(0).total_memory if torch.cuda.is_available() else 0
+    except Exception:
+        mem = 0
+    cap = max(32768, int((mem or 288e9) / 16) // per_leaf)
+    passes = -(-leaves // cap)
+    chunk = -(-leaves // passes)
     return (84 * (leaves + parents) + parents * 400 * 32 * 4 +
-            chunk * ((400 * 32 + 81 * 64 + 49 * 64) * e + 512 * 4)) / 1e9
+            chunk * per_leaf) / 1e9
 
 
 def report_vs_oracle(bcts, W, wl):

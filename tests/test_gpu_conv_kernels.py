@@ -71,8 +71,8 @@ def test_qnet_variants_match_oracle(oracle_lib, dev, monkeypatch, precision, n):
 
 @pytest.mark.parametrize("precision,mask", [("fp32", 12), ("fp32", 4), ("bf16", 12), ("bf16", 3), ("fp8", 12)])
 def test_atari_scale_search_with_variant(dev, monkeypatch, precision, mask):
-    """All 32 Atari-scale roots (A = 18, d = 3: 186,624 leaves in chunks of 32,768, so
-    each launch spans thousands of tiles) against the stored FP64 oracle values."""
+    """All 32 Atari-scale roots (A = 18, d = 3: 186,624 leaves in one Q-network pass,
+    so each launch spans about 146,000 tiles) against the stored FP64 oracle values."""
     torch, bcts = dev
     import json
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_atari32_a18_d3.json")
