@@ -23,9 +23,12 @@
 // hi = bf16(x), lo = bf16(x - hi) and the product is hi*hi + hi*lo + lo*hi
 // (three MMAs; two for conv1, whose integer pixels are exact in bf16),
 // accumulated in FP32.  FC2 and the max over actions run in FP32 on CUDA cores
-// (9,216 MACs per node, 0.1 % of the network).  The leaves' conv1 runs here
-// only when their parents' partial maps are not kept; otherwise it is the
-// streaming pass of leaf_conv1.cu.
+// (9,216 MACs per node, 0.1 % of the network).  The leaves' conv1 is, on the
+// default path, the streaming pass of leaf_conv1.cu over the sprite tables; on
+// the frame path it runs here as layers 5 (the parents' partial maps from their
+// older frames) and 6 (each leaf's newest frame plus its parent's map).  conv2
+// and conv3 may instead run in the TMA im2col kernel (conv_tma.cu) or the
+// shared-memory window kernel (conv_win.cu), chosen per precision.
 //
 // Every wait is bounded: a wait that runs out sets the context's device error
 // word and an abort flag, every role leaves its loop, in-flight copies and MMAs
