@@ -76,8 +76,13 @@ ALG_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 0, "conv1_leaf": 0,
 # d = 3 (launches over 23,328 leaves; traffic grows in proportion to the nodes a launch
 # processes).  A class whose kernel changed after its capture has no entry here.
 TRAFFIC_PER_NODE = {"fp32/conv1_leaf": 53939.0, "bf16/conv1_leaf": 27170.0, "fp8/conv1_leaf": 13745.0,
-                    "fp32/conv2": 70871.0, "bf16/conv2": 34762.0, "fp8/conv2": 16775.0,
+                    "fp32/conv2": 70771.0, "bf16/conv2": 34762.0, "fp8/conv2": 16775.0,
                     "fp32/conv3": 31903.0, "fp32/fc1": 14562.0}
+# Output rows each precision's default kernel computes per output row it keeps: the
+# window and tap-pair kernels run on a grid padded to the input's width and height
+# (conv2: 100 rows per 81, conv3: 81 per 49), and the tap-pair tiles keep 127 of 128.
+EXEC_PAD = {"fp32/conv2": 100 / 81 * 128 / 127, "bf16/conv2": 100 / 81, "bf16/conv3": 81 / 49,
+            "fp8/conv2": 100 / 81}
 
 
 def layer_model(cls, precision, A):
@@ -87,7 +92,8 @@ def layer_model(cls, precision, A):
     the partial conv1 map of a parent is FP32 and each of its A children reads it, so a
     leaf's share is 1/A of it; the fc1 output is FP32.  Weights stay resident in shared
     memory (read once per CTA).  The split mode executes 2 bf16 MMAs per conv1 MAC
-    (pixels are exact in bf16) and 3 per MAC elsewhere."""
+    (pixels are exact in bf16) and 3 per MAC elsewhere, times the padding of the
+    default kernel's output grid (EXEC_PAD)."""
     e = {"fp32": 4, "bf16": 2, "fp8": 1}.get(precision, 4)
     c1, c2, c3, f1 = 400 * 32, 81 * 64, 49 * 64, 512
     rw = {"conv1": (80, c1 * e), "conv1_partial": (80, c1 * 4), "conv1_leaf": (80 + c1 * 4 / A, c1 * e),
@@ -95,6 +101,7 @@ def layer_model(cls, precision, A):
           "fc2": (f1 * 4, 4)}.get(cls, (0, 0))
     macs = ALG_MACS.get(cls, A * 512 if cls == "fc2" else 0)
     mma = (2 if cls.startswith("conv1") else 3) if precision == "fp32" else 1
+    mma *= EXEC_PAD.get(f"{precision}/{cls}", 1.0)
     return macs, mma, rw[0], rw[1]
 
 

@@ -127,11 +127,13 @@ BCTS_API size_t bcts_qnet_numel(int A);
  *                  0 = vanilla tree search (Eq. 2), 1 = Eq. 3 as printed
  *   opt          : NULL = defaults
  *   out          : receives the context
- * Environment: BCTS_CONV_KERNELS = m (0..15), read here, fixes the kernels of the
- *   leaf Q-network's conv2 / conv3 (tensor-core precisions): bit 2 / bit 3 the
- *   shared-memory window kernels, else bit 0 / bit 1 the TMA im2col kernels,
- *   else the cp.async gather; unset = the precision's measured default.  Every
- *   variant computes the same layer; they differ in speed and rounding order.
+ * Environment: BCTS_CONV_KERNELS = m (0..31), read here, fixes the kernels of the
+ *   leaf Q-network's conv2 / conv3 (tensor-core precisions): bit 4 conv2 through
+ *   the tap-pair kernel (weights in tensor memory; BF16 and FP32-class), else
+ *   bit 2 / bit 3 the shared-memory window kernels, else bit 0 / bit 1 the TMA
+ *   im2col kernels, else the cp.async gather; unset = the precision's measured
+ *   default.  Every variant computes the same layer; they differ in speed and
+ *   rounding order.
  * Errors: BCTS_EINVAL (bad A, d, gamma, NULL weights/out), BCTS_ENOMEM, BCTS_ECUDA.
  */
 BCTS_API int bcts_create(const bcts_env_desc *env, const float *qnet_weights, int A, int d, float gamma,

@@ -53,35 +53,12 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "pack.cuh"
+#include "conv_win.cuh"
 #include "tc_ptx.cuh"
 #include "tma_host.cuh"
 
 namespace bcts {
 namespace tc {
-
-template <int LAYER>
-struct WinGeo;
-template <>
-struct WinGeo<2> {  // space-to-depth view of [20][20][32]: [10][10] x (dy, dx, c)
-  static constexpr int PW = 10, PP = 100;  // padded grid width, padded rows per node
-  static constexpr int OW = 9, P = 81;     // output side, output pixels per node
-  static constexpr int TW = 2, NTAP = 4;   // filter side and taps over super-pixels
-  static constexpr int NSLAB = 2;          // window slabs per row (dy)
-  static constexpr int LINES = 15;         // window lines of PW rows loaded per tile
-  static constexpr int WROWS = LINES * PW; // 150 >= 9 (tile start in its line) + 128 + 11 (largest shift)
-  __host__ __device__ static constexpr int wx(int tap, int slab) {  // first K of (tap, slab) in (ky, kx, c)
-    return ((2 * (tap / 2) + slab) * 4 + 2 * (tap % 2)) * 32;
-  }
-};
-template <>
-struct WinGeo<3> {  // [9][9][64]
-  static constexpr int PW = 9, PP = 81;
-  static constexpr int OW = 7, P = 49;
-  static constexpr int TW = 3, NTAP = 9;
-  static constexpr int NSLAB = 1;
-  static constexpr int WROWS = 148;        // 128 + 20 (largest shift)
-  __host__ __device__ static constexpr int wx(int tap, int) { return tap * 64; }
-};
 
 constexpr int kStgRowW = 144;  // epilogue staging row (128 output bytes + 16 to spread the banks)
 
@@ -480,33 +457,10 @@ __global__ void __launch_bounds__(WinCfg<LAYER, MODE>::THREADS, 1)
 // ---------------------------------------------------------------------------
 // Host side: tensor maps and launch
 // ---------------------------------------------------------------------------
-// The input window map.  conv2: 4D view (channels (dx, c), x2, dy, node*10 + y2)
-// of the NHWC [n][20][20][32] map, box = 15 lines of 10 super-pixels of one dy.
-// conv3: [n*81][64] rows, box = 148 rows.  Rows past the end read as zeros.
+// The input window map (conv_win.cuh).
 template <int LAYER, int MODE>
 int encode_window(CUtensorMap *m, const void *base, int64_t n) {
-  using C = WinCfg<LAYER, MODE>;
-  using G = WinGeo<LAYER>;
-  const Encoders &e = encoders();
-  if (!e.tiled) return BCTS_ECUDA;
-  const CUtensorMapDataType dt = C::FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  CUresult r;
-  if constexpr (LAYER == 2) {
-    const cuuint64_t dims[4] = {64, 10, 2, cuuint64_t(n) * 10};
-    const cuuint64_t strides[3] = {cuuint64_t(64 * C::EB), cuuint64_t(640 * C::EB), cuuint64_t(1280 * C::EB)};
-    const cuuint32_t box[4] = {64, 10, 1, cuuint32_t(G::LINES)};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    r = e.tiled(m, dt, 4, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                swizzle_for(C::ROWB), CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  } else {
-    const cuuint64_t dims[2] = {64, cuuint64_t(n) * G::PP};
-    const cuuint64_t strides[1] = {cuuint64_t(64 * C::EB)};
-    const cuuint32_t box[2] = {64, cuuint32_t(G::WROWS)};
-    const cuuint32_t estr[2] = {1, 1};
-    r = e.tiled(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                swizzle_for(C::ROWB), CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  }
-  return r == CUDA_SUCCESS ? BCTS_OK : BCTS_ECUDA;
+  return encode_window_map<LAYER>(m, base, n, WinCfg<LAYER, MODE>::FP8);
 }
 
 // Weights [64][kpad] (K-major): one box = 64 rows x 64 consecutive K.

@@ -91,8 +91,9 @@ struct FrameSrc {
 int tc_conv1_zmap_frames(const TcWeights *w, const FrameSrc &fs, int64_t n, float *z, cudaStream_t st, int *d_err);
 // conv_tma_mask: conv2 (bit 0) / conv3 (bit 1) through the TMA im2col kernel of
 // conv_tma.cu, conv2 (bit 2) / conv3 (bit 3) through the window kernel of
-// conv_win.cu (before bits 0 / 1), else the cp.async-gathered tc_gemm; -1 = this
-// precision's default.
+// conv_win.cu (before bits 0 / 1), conv2 through the tap-pair kernel of
+// conv_pair.cu (bit 4, before all others; BF16 and FP32-class only), else the
+// cp.async-gathered tc_gemm; -1 = this precision's default.
 // fs (frames and states NULL): conv1 from rendered frames (see FrameSrc).
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,
                     float *maxq, void *scratch, cudaStream_t stream, int *d_err, const uint8_t *node_A = nullptr,
@@ -116,6 +117,10 @@ int launch_conv_tma(int layer, int mode, const ConvTmaArgs &a, cudaStream_t st);
 // the input map in shared memory (stride-1 form; conv2 on its space-to-depth
 // view).  Same arguments and outputs.
 int launch_conv_win(int layer, int mode, const ConvTmaArgs &a, cudaStream_t st);
+// conv_pair.cu: conv2 with its weights resident in tensor memory and two filter
+// taps of the space-to-depth view per M = 128, N = 128 instruction.  mode 0 BF16
+// or 1 FP32-class split (E4M3: BCTS_EINVAL).  Same arguments and outputs.
+int launch_conv_pair(int mode, const ConvTmaArgs &a, cudaStream_t st);
 // leaf_conv1.cu: conv1 of n leaves (states) from their parents' partial maps, as
 // ReLU(Z + the newest slot's term).  mode: 0 BF16, 1 FP32-class split (bf16 hi +
 // lo), 2 E4M3 scaled by out_scale.  T [4 objects][2][2][32] and W3 [64][32]: the

@@ -360,10 +360,17 @@ static void save_tune(MixedState *m) {
 // (leaf chunk x conv2 / conv3 kernel variant) on the plan's own leaves (first
 // pass of a new bucket only; each candidate is run once to size its scratch and
 // once timed).  The candidate kernels sum every output's products in the same
-// order as the precision's default ones (conv2 through windows or not, as the
-// default; conv3 through any of its three kernels), so a root's result does not
-// depend on the bucket its pass falls into.  A mask fixed through
-// BCTS_CONV_KERNELS is kept; only the chunk is tuned then.
+// order as the precision's default ones (conv2 through the same one of its
+// three summation orders as the default; conv3 through any of its three
+// kernels), so a root's result does not depend on the bucket its pass falls
+// into.  A mask fixed through BCTS_CONV_KERNELS is kept; only the chunk is tuned
+// then.
+// conv2's summation order under a kernel mask: 0 im2col rows (cp.async gather or
+// TMA im2col), 1 shared-memory windows, 2 tap pairs (E4M3 has no tap-pair kernel).
+static int conv2_order(int mask, int precision) {
+  if ((mask & 16) && precision != BCTS_PREC_FP8) return 2;
+  return (mask & 4) ? 1 : 0;
+}
 static int autotune(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_t st) {
   if (c->opt.leaf_chunk > 0 || pl.nleaf < 65536 || c->precision == BCTS_PREC_FP32_SIMT) return BCTS_OK;
   if (!m->tune_loaded) load_tune(m);
@@ -371,20 +378,22 @@ static int autotune(Ctx *c, MixedState *m, const MixedPlan &pl, cudaStream_t st)
   const std::string key = std::to_string(c->precision) + ":" + std::to_string(leaf_bucket(pl.nleaf)) +
                           (c->conv_mask_fixed ? ":m" + std::to_string(dm) : std::string());
   auto it = m->tuned.find(key);
-  if (it != m->tuned.end() && (it->second.conv_mask & 4) == (dm & 4)) {
+  const int order = conv2_order(dm, c->precision);
+  if (it != m->tuned.end() && conv2_order(it->second.conv_mask, c->precision) == order) {
     c->chunk_override = it->second.chunk;
     c->conv_mask = it->second.conv_mask;
     return BCTS_OK;
   }
   const int64_t chunks[] = {32768, 65536, 0};  // 0: the automatic pass size (Ctx::chunk_nodes)
-  // conv2 / conv3 kernels: bits 0 / 1 TMA im2col, bits 2 / 3 shared-memory windows
+  // conv2 / conv3 kernels: bits 0 / 1 TMA im2col, bits 2 / 3 shared-memory
+  // windows, bit 4 conv2 tap pairs
   std::vector<int> masks;
   if (c->conv_mask_fixed) {
     masks.push_back(dm);
   } else {
-    for (int c2 : {0, 1})
-      for (int c3 : {0, 2, 8})
-        if (!(dm & 4) || c2 == 0) masks.push_back(((dm & 4) ? 4 : c2) | c3);
+    const std::vector<int> c2s = order == 2 ? std::vector<int>{16} : (order == 1 ? std::vector<int>{4} : std::vector<int>{0, 1});
+    for (int c2 : c2s)
+      for (int c3 : {0, 2, 8}) masks.push_back(c2 | c3);
   }
   float best_ms = 1e30f;
   MixedState::Tuned best{32768, -1};

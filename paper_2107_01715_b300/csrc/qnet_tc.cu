@@ -1241,6 +1241,7 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
   }
   if (rc != BCTS_OK) return rc;
   // conv2 and conv3: TMA-fed implicit GEMMs (conv_tma.cu)
+  const bool pair2 = (conv_tma_mask & 16) && MODE != 2;  // E4M3 has no tap-pair kernel
   auto conv = [&](int l, const void *in, const void *in_lo, void *o, void *o_lo) {
     ConvTmaArgs a{};
     a.in_hi = in;
@@ -1255,12 +1256,14 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
     a.out_lo = o_lo;
     a.n = n;
     a.d_err = d_err;
+    if (l == 1 && pair2) return launch_conv_pair(MODE, a, st);
     return (conv_tma_mask >> (l + 1)) & 1 ? launch_conv_win(l + 1, MODE, a, st) : launch_conv_tma(l + 1, MODE, a, st);
   };
-  // conv2 / conv3: window-fed (conv_win.cu), TMA im2col-fed (conv_tma.cu) or
-  // cp.async-gathered (tc_gemm), chosen per layer by conv_tma_mask (bits 2 / 3
-  // window, bits 0 / 1 im2col, for conv2 / conv3)
-  if (conv_tma_mask & 5) {
+  // conv2 / conv3: tap-pair (conv_pair.cu, conv2 only), window-fed (conv_win.cu),
+  // TMA im2col-fed (conv_tma.cu) or cp.async-gathered (tc_gemm), chosen per layer
+  // by conv_tma_mask (bit 4 tap pair; bits 2 / 3 window, bits 0 / 1 im2col, for
+  // conv2 / conv3)
+  if ((conv_tma_mask & 5) || pair2) {
     rc = conv(1, a1, a1l, a2, a2l);
   } else {
     layer(1, a1, a1l, a2, a2l);
@@ -1284,10 +1287,11 @@ int tc_default_conv_mask(int precision) {
   // measured per layer on B300 at the Atari-scale workload (CUDA events, same
   // call): BF16 reads conv2 and conv3 from shared-memory windows (conv_win.cu);
   // E4M3 reads conv2 from windows and takes conv3 through TMA im2col; the
-  // FP32-class split mode takes conv3 through TMA im2col and conv2 through the
-  // cp.async gather (its window variants, whose padded rows cost 23-65 % more
-  // MMAs, measured slower)
-  return precision == BCTS_PREC_BF16 ? 12 : (precision == BCTS_PREC_FP8 ? 6 : 2);
+  // FP32-class split mode takes conv2 through tap pairs (conv_pair.cu: 2.30 ms
+  // against 3.22 ms for the cp.async gather, the best of the pixel-major
+  // kernels) and conv3 through TMA im2col (its window variant, whose padded rows
+  // cost 65 % more MMAs, measured slower)
+  return precision == BCTS_PREC_BF16 ? 12 : (precision == BCTS_PREC_FP8 ? 6 : 18);
 }
 
 int tc_qnet_forward(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n, float *q,

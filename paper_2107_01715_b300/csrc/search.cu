@@ -887,7 +887,7 @@ extern "C" int bcts_create(const bcts_env_desc *env, const float *w, int A, int 
   c->exact_gev = (c->opt.flags & BCTS_FLAG_EXACT_GEV) != 0;
   if (const char *cm = std::getenv("BCTS_CONV_KERNELS")) {  // conv2 / conv3 kernel variants, bits as conv_mask
     const int m = std::atoi(cm);
-    if (m >= 0 && m <= 15) {
+    if (m >= 0 && m <= 31) {
       c->conv_mask = m;
       c->conv_mask_fixed = true;
     }

@@ -1,11 +1,12 @@
 """GPU parity of every conv2 / conv3 kernel variant of the leaf Q-network (cp.async
-gather, TMA im2col, shared-memory window), selected per context with the
-BCTS_CONV_KERNELS mask, against the FP64 oracle and against each other.
+gather, TMA im2col, shared-memory window, conv2 tap pairs), selected per context
+with the BCTS_CONV_KERNELS mask, against the FP64 oracle and against each other.
 
 The window kernels pad the output grid (conv2: 100 rows per node on the
 space-to-depth view, conv3: 81) and read every filter tap as a row-shifted view
 of one window: node counts below are chosen so that tiles straddle nodes and the
-last tile is ragged (n * 100 and n * 81 not multiples of 128)."""
+last tile is ragged (n * 100 and n * 81 not multiples of 128; the tap-pair
+kernel's tiles advance by 127 rows)."""
 import os
 
 import numpy as np
@@ -16,8 +17,9 @@ from tests._util import TOL, check_actions, pi_o_decided, value_close
 
 pytestmark = pytest.mark.gpu
 
-# bits 0 / 1: conv2 / conv3 through TMA im2col; bits 2 / 3: through windows
-MASKS = [0, 3, 4, 8, 12, 6, 9]
+# bits 0 / 1: conv2 / conv3 through TMA im2col; bits 2 / 3: through windows;
+# bit 4: conv2 through tap pairs (BF16, FP32-class; E4M3 ignores it)
+MASKS = [0, 3, 4, 8, 12, 6, 9, 16, 18, 24]
 
 
 @pytest.fixture(scope="module")
@@ -69,7 +71,8 @@ def test_qnet_variants_match_oracle(oracle_lib, dev, monkeypatch, precision, n):
         assert d.max() <= agree, (mask, d.max())
 
 
-@pytest.mark.parametrize("precision,mask", [("fp32", 12), ("fp32", 4), ("bf16", 12), ("bf16", 3), ("fp8", 12)])
+@pytest.mark.parametrize("precision,mask", [("fp32", 12), ("fp32", 4), ("fp32", 18), ("bf16", 12), ("bf16", 3),
+                                            ("bf16", 24), ("fp8", 12)])
 def test_atari_scale_search_with_variant(dev, monkeypatch, precision, mask):
     """All 32 Atari-scale roots (A = 18, d = 3: 186,624 leaves in one Q-network pass,
     so each launch spans about 146,000 tiles) against the stored FP64 oracle values."""
@@ -87,7 +90,7 @@ def test_atari_scale_search_with_variant(dev, monkeypatch, precision, mask):
     check_actions(act, ref, tol / 2 if precision != "fp32" else tol)
 
 
-@pytest.mark.parametrize("mask", [4, 12])
+@pytest.mark.parametrize("mask", [4, 12, 16])
 def test_ragged_chunks_with_windows(oracle_lib, dev, monkeypatch, mask):
     """Leaf chunks of 40 leaves (a window's tiles end inside a node at every chunk
     end) in every precision, against the oracle's search."""

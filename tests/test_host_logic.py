@@ -60,14 +60,16 @@ def test_roofline_picks_the_binding_resource(bench):
     assert macs == 0 and rd + wr == pytest.approx(80 + 51200 / 18 + 51200)
     r = bench.roofline_for("conv1_leaf", "fp32", 18, 1000, 1.0, 1, pk, "measured")
     assert r["bound"] == "hbm" and r["achieved"] == pytest.approx((rd + wr) * 1000 / 1e-3 / 1e9)
-    # conv2 in split mode: 3 MMAs per MAC -> tensor-bound; achieved and frac count the
-    # method's own FLOPs (2 x MACs), executed_frac the 3 executed MMAs per MAC
+    # conv2 in split mode: 3 MMAs per MAC on the tap-pair kernel's padded grid (100 rows
+    # per 81 kept, 127 kept of each 128-row tile) -> tensor-bound; achieved and frac count
+    # the method's own FLOPs (2 x MACs), executed_frac the executed MMAs
     r = bench.roofline_for("conv2", "fp32", 18, 1000, 1.0, 1, pk, "measured")
     assert r["bound"] == "tensor"
     assert r["achieved"] == pytest.approx(2 * 81 * 64 * 512 * 1000 / 1e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / 1000.0)
-    assert r["executed_frac"] == pytest.approx(3 * r["frac"])
+    assert r["executed_frac"] == pytest.approx(3 * 100 / 81 * 128 / 127 * r["frac"])
     # E4M3 doubles the tensor peak; the plain FP32 network is ALU-bound
     r8 = bench.roofline_for("conv2", "fp8", 18, 1000, 1.0, 1, pk, "measured")
-    assert r8["min_time_ms"]["tensor_or_alu_executed"] == pytest.approx(1e3 * 2 * 81 * 64 * 512 * 1000 / 2000e12)
+    assert r8["min_time_ms"]["tensor_or_alu_executed"] == pytest.approx(
+        1e3 * 2 * 81 * 64 * 512 * 1000 * (100 / 81) / 2000e12)
     assert bench.roofline_for("conv2", "fp32_simt", 18, 10 ** 6, 1.0, 1, pk, "measured")["bound"] == "alu"
