@@ -77,7 +77,7 @@ ALG_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 0, "conv1_leaf": 0,
 # processes).  A class whose kernel changed after its capture has no entry here.
 TRAFFIC_PER_NODE = {"fp32/conv1_leaf": 53939.0, "bf16/conv1_leaf": 27170.0, "fp8/conv1_leaf": 13745.0,
                     "fp32/conv2": 70771.0, "bf16/conv2": 34762.0, "fp8/conv2": 16775.0,
-                    "fp32/conv3": 31903.0, "fp32/fc1": 14562.0}
+                    "fp32/conv3": 31903.0}
 # Output rows each precision's default kernel computes per output row it keeps: the
 # window and tap-pair kernels run on a grid padded to the input's width and height
 # (conv2: 100 rows per 81, conv3: 81 per 49), and the tap-pair tiles keep 127 of 128.
@@ -90,15 +90,17 @@ def layer_model(cls, precision, A):
     executed per MAC, algorithmic DRAM bytes read, written).  Activation maps are bf16
     (2 bytes), bf16 hi + lo in the FP32-class split mode (4 bytes), E4M3 in FP8 (1 byte);
     the partial conv1 map of a parent is FP32 and each of its A children reads it, so a
-    leaf's share is 1/A of it; the fc1 output is FP32.  Weights stay resident in shared
+    leaf's share is 1/A of it; the fc1 output is FP32 (in the split mode, whose fc1
+    epilogue folds fc2 in, two halves' partial Q-values: 2 x 18 FP32).  Weights stay resident in shared
     memory (read once per CTA).  The split mode executes 2 bf16 MMAs per conv1 MAC
     (pixels are exact in bf16) and 3 per MAC elsewhere, times the padding of the
     default kernel's output grid (EXEC_PAD)."""
     e = {"fp32": 4, "bf16": 2, "fp8": 1}.get(precision, 4)
     c1, c2, c3, f1 = 400 * 32, 81 * 64, 49 * 64, 512
+    fc1_out = 2 * 18 * 4 if precision == "fp32" else f1 * 4
     rw = {"conv1": (80, c1 * e), "conv1_partial": (80, c1 * 4), "conv1_leaf": (80 + c1 * 4 / A, c1 * e),
-          "conv2": (c1 * e, c2 * e), "conv3": (c2 * e, c3 * e), "fc1": (c3 * e, f1 * 4),
-          "fc2": (f1 * 4, 4)}.get(cls, (0, 0))
+          "conv2": (c1 * e, c2 * e), "conv3": (c2 * e, c3 * e), "fc1": (c3 * e, fc1_out),
+          "fc2": (fc1_out, 4)}.get(cls, (0, 0))
     macs = ALG_MACS.get(cls, A * 512 if cls == "fc2" else 0)
     mma = (2 if cls.startswith("conv1") else 3) if precision == "fp32" else 1
     mma *= EXEC_PAD.get(f"{precision}/{cls}", 1.0)

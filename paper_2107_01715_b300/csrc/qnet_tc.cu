@@ -195,6 +195,11 @@ struct GemmParams {
   const float *zmap;
   const uint32_t *zparent;
   uint32_t zleaf0, zbranch;
+  // layer 4 (fc1) with fc2 folded into its epilogue: fc2 weights [fA][512] FP32;
+  // partial Q-values of each row's 256-column half, qpart[row][half][kMaxA]
+  const float *w2;
+  int fA;
+  float *qpart;
   int num_tiles;
   int *d_err;
 };
@@ -826,7 +831,16 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
       // in registers until the hi rows are written
       constexpr int OW = LAYER == 4 ? 1 : (FP8 ? BN / 4 : BN / 2);
       uint32_t olo[SPLIT && LAYER != 4 ? OW : 1];
+      // fc1 in the split mode: this row's fc2 partial sums over the tile's 256
+      // columns (BF16 / E4M3, whose fc1 MMAs are shorter than this arithmetic,
+      // write the FP32 map for fc2_max_kernel instead)
+      constexpr bool FOLD = LAYER == 4 && SPLIT;
+      float qs[FOLD ? kMaxA : 1];
 #pragma unroll
+      for (int a = 0; a < (FOLD ? kMaxA : 1); ++a) qs[a] = 0.f;
+      // then the 16 chunks stay a rolled loop: unrolled, the fc2 sums and the
+      // chunks' loads overlapped beyond the 128 registers of this 13-warp CTA
+#pragma unroll(FOLD ? 1 : BN / 16)
       for (int j = 0; j < BN / 16; ++j) {
         uint32_t r[16];
         tmem_ld16(tbase + uint32_t(j * 16), r);
@@ -865,6 +879,27 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
           for (int e = 0; e < 4; ++e)
             *reinterpret_cast<float4 *>(stg + lane * kStgRow + j * 64 + e * 16) =
                 make_float4(v[2 * e].x, v[2 * e].y, v[2 * e + 1].x, v[2 * e + 1].y);
+        } else if constexpr (FOLD) {
+          // h = ReLU(v) for these 16 columns, folded straight into fc2: qs[a] +=
+          // h . W2[a][n0 + 16 j ..] (every lane reads the same weights: broadcast)
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = make_float2(fmaxf(v[e].x, 0.f), fmaxf(v[e].y, 0.f));
+#pragma unroll
+          for (int a = 0; a < kMaxA; ++a) {
+            if (a < p.fA) {
+              const float4 *wr = reinterpret_cast<const float4 *>(p.w2 + size_t(a) * G::NTOT + n0 + j * 16);
+              float acc_a = qs[a];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float4 w4 = __ldg(wr + k);
+                acc_a = fmaf(v[2 * k].x, w4.x, acc_a);
+                acc_a = fmaf(v[2 * k].y, w4.y, acc_a);
+                acc_a = fmaf(v[2 * k + 1].x, w4.z, acc_a);
+                acc_a = fmaf(v[2 * k + 1].y, w4.w, acc_a);
+              }
+              qs[a] = acc_a;
+            }
+          }
         } else if constexpr (LAYER == 4) {
 #pragma unroll
           for (int e = 0; e < 4; ++e)
@@ -897,6 +932,15 @@ __global__ void __launch_bounds__(Cfg<LAYER, MODE>::THREADS, 1) tc_gemm(const Ge
           }
           *reinterpret_cast<uint4 *>(stg + lane * kStgRow + j * 32) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
           *reinterpret_cast<uint4 *>(stg + lane * kStgRow + j * 32 + 16) = make_uint4(hh[4], hh[5], hh[6], hh[7]);
+        }
+      }
+      if constexpr (FOLD) {
+        const uint32_t m = mw0 + uint32_t(lane);
+        if (m < p.M) {
+          float *dst = p.qpart + (size_t(m) * NT + size_t(t % NT)) * kMaxA;
+#pragma unroll
+          for (int a = 0; a < kMaxA; ++a)
+            if (a < p.fA) dst[a] = qs[a];
         }
       }
       if constexpr (LAYER != 4) {
@@ -1183,6 +1227,33 @@ void set_frames(tc::GemmParams &p, const FrameSrc &f) {
   p.node0 = f.node0;
 }
 
+// fc2 after fc1's epilogue: q[node][a] = (partial of fc1 columns 0-255 +
+// partial of columns 256-511) + b2[a], and the max over the node's first node_A
+// actions (the batched form; else all A), the outputs launch_fc2_max gives.
+__global__ void fc2_combine_kernel(const float *__restrict__ qpart, const float *__restrict__ b2, int A, int64_t n,
+                                   float *__restrict__ q, float *__restrict__ maxq,
+                                   const uint8_t *__restrict__ node_A) {
+  const int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (node >= n) return;
+  const float *p0 = qpart + node * (2 * kMaxA);
+  const int An = node_A ? int(node_A[node]) : A;
+  float best = -INFINITY;
+  for (int a = 0; a < A; ++a) {
+    const float v = (p0[a] + p0[kMaxA + a]) + __ldg(b2 + a);
+    if (q) q[node * A + a] = v;
+    if (a < An) best = fmaxf(best, v);
+  }
+  if (maxq) maxq[node] = best;
+}
+
+int launch_fc2_combine(const float *qpart, const float *b2, int A, int64_t n, float *q, float *maxq,
+                       cudaStream_t st, const uint8_t *node_A) {
+  if (n <= 0) return BCTS_OK;
+  ProfScope ps(K_FC2, st);
+  fc2_combine_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(qpart, b2, A, n, q, maxq, node_A);
+  return cudaGetLastError() == cudaSuccess ? BCTS_OK : BCTS_ECUDA;
+}
+
 template <int MODE>
 int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts_state *states, int64_t n,
                     float *q, float *maxq, void *scratch, cudaStream_t st, int *d_err, const uint8_t *node_A,
@@ -1277,6 +1348,19 @@ int tc_forward_impl(const TcWeights *w, int A, const uint8_t *frames, const bcts
     rc = tc::launch<3, MODE, false>(p, (long long)n * kP3, K_CONV3, st);
   }
   if (rc != BCTS_OK) return rc;
+  if constexpr (SPLIT) {
+    // fc1 with fc2 folded into its epilogue: each row's partial Q-values per
+    // 256-column half (in the space of the FP32 fc1 map, which is not written),
+    // then bias + the two halves and the max (measured: fc1 + fc2 1.38 against
+    // 1.48 ms per Atari-scale search; in BF16 / E4M3 the fold costs more than
+    // the FP32 map it saves)
+    layer(3, a3, a3l, nullptr, nullptr);
+    p.w2 = w->f2w;
+    p.fA = A;
+    p.qpart = h;
+    if ((rc = tc::launch<4, MODE, false>(p, (long long)n, K_FC1, st)) != BCTS_OK) return rc;
+    return launch_fc2_combine(h, w->f2b, A, n, q, maxq, st, node_A);
+  }
   layer(3, a3, a3l, h, nullptr);  // FP32 output for FC2
   if ((rc = tc::launch<4, MODE, false>(p, (long long)n, K_FC1, st)) != BCTS_OK) return rc;
   return launch_fc2_max(h, w->f2w, w->f2b, A, n, q, maxq, st, node_A);
