@@ -77,7 +77,7 @@ ALG_MACS = {"conv1": 400 * 32 * 256, "conv1_partial": 0, "conv1_leaf": 0,
 # processes).  A class whose kernel changed after its capture has no entry here.
 TRAFFIC_PER_NODE = {"fp32/conv1_leaf": 53939.0, "bf16/conv1_leaf": 27170.0, "fp8/conv1_leaf": 13745.0,
                     "fp32/conv2": 70771.0, "bf16/conv2": 34762.0, "fp8/conv2": 16775.0,
-                    "fp32/conv3": 31903.0}
+                    "fp32/conv3": 31903.0, "fp32/fc1": 13443.0}
 # Output rows each precision's default kernel computes per output row it keeps: the
 # window and tap-pair kernels run on a grid padded to the input's width and height
 # (conv2: 100 rows per 81, conv3: 81 per 49), and the tap-pair tiles keep 127 of 128.
